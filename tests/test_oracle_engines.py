@@ -1,0 +1,167 @@
+"""Pins of the oracle's engines, seeding and jumps against things other than
+the oracle itself: NumPy's SeedSequence / PCG64DXSM run as black boxes, jump
+identities with two independent jump constructions (Sec. 4.4), and
+statistics.  Philox4x32-10 is pinned bit-for-bit against cuRAND in the GPU
+suite (tests/test_gpu_engines.py); on the CPU only its structural properties
+are checked here."""
+import ctypes
+
+import numpy as np
+import pytest
+from numpy.random import PCG64DXSM, SeedSequence
+
+
+def _rng():
+    return np.random.default_rng(20240601)
+
+
+# ------------------------------------------------------------------ seeding
+def test_seedseq_matches_numpy(orc):
+    """Sec. 2.3: seed + spawn key -> 128-bit pool -> state words; reading =
+    NumPy SeedSequence semantics.  2000 random (seed, key) pairs plus edges."""
+    rng = _rng()
+    seeds = [0, 1, 2 ** 32 - 1, 2 ** 32, 2 ** 64 - 1] + [int(x) for x in rng.integers(0, 2 ** 63, 1000)]
+    keys = [None, 0, 1, 2 ** 32, 2 ** 64 - 1] + [int(x) for x in rng.integers(0, 2 ** 40, 1000)]
+    for i, seed in enumerate(seeds):
+        key = keys[i % len(keys)]
+        ss = SeedSequence(seed) if key is None else SeedSequence(seed, spawn_key=(key,))
+        ref = ss.generate_state(12, np.uint32)
+        got = orc.seedseq_generate(orc.seedseq_entropy(seed, key), 12)
+        assert np.array_equal(ref, got), (seed, key)
+
+
+def test_xoshiro_seed_is_seedseq_words(orc):
+    for seed, key in [(12345, None), (2024, None), (7, 1), (99, None)]:
+        g = orc.gen("xoshiro256pp", seed, key)
+        ss = SeedSequence(seed) if key is None else SeedSequence(seed, spawn_key=(key,))
+        assert orc.state_words(g) == [int(x) for x in ss.generate_state(4, np.uint64)]
+
+
+# ------------------------------------------------------------------ PCG64
+@pytest.mark.parametrize("seed,key", [(0, None), (2024, None), (12345, 3), (2 ** 63 + 11, None)])
+def test_pcg64dxsm_matches_numpy(orc, seed, key):
+    """Sec. 2.2 / Sec. 5.1: pcg64 is validated against NumPy.  Seeded state,
+    increment and the first 100k words must be identical."""
+    ss = SeedSequence(seed) if key is None else SeedSequence(seed, spawn_key=(key,))
+    bg = PCG64DXSM(ss)
+    g = orc.gen("pcg64dxsm", seed, key)
+    s = orc.state_words(g)
+    st = bg.state["state"]
+    assert st["state"] == (s[0] << 64 | s[1]) and st["inc"] == (s[2] << 64 | s[3])
+    assert np.array_equal(bg.random_raw(100_000), orc.next_words(g, 100_000))
+
+
+def test_pcg64dxsm_advance_matches_numpy(orc):
+    """Sec. 2.3: PCG64 advance by an arbitrary delta (LCG skip-ahead)."""
+    rng = _rng()
+    for _ in range(50):
+        delta = int(rng.integers(0, 2 ** 62)) << 66 | int(rng.integers(0, 2 ** 62))
+        bg = PCG64DXSM(SeedSequence(5))
+        g = orc.gen("pcg64dxsm", 5)
+        bg.advance(delta)
+        orc.lib().or_jump(ctypes.byref(g), (delta >> 64) & (2 ** 64 - 1), delta & (2 ** 64 - 1))
+        assert np.array_equal(bg.random_raw(8), orc.next_words(g, 8))
+
+
+# ------------------------------------------------------------------ xoshiro
+def test_xoshiro_charpoly_primitive_shape(orc):
+    """T^N = p_N(T) needs the degree-256 characteristic polynomial
+    (Cayley-Hamilton, Sec. 4.4).  Pins: degree 256, constant term 1, and
+    x^(2^256 - 1) = 1 mod p (period 2^256 - 1, Table "engines")."""
+    p = orc.xoshiro_charpoly()
+    assert p.bit_length() - 1 == 256 and (p & 1) == 1
+
+    def mulmod(a, b):
+        r = 0
+        while b:
+            if b & 1:
+                r ^= a
+            b >>= 1
+            a <<= 1
+            if (a >> 256) & 1:
+                a ^= p
+        return r
+
+    def powmod(e):
+        r, base = 1, 2
+        while e:
+            if e & 1:
+                r = mulmod(r, base)
+            base = mulmod(base, base)
+            e >>= 1
+        return r
+
+    assert powmod(2 ** 256 - 1) == 1
+    # the period is not a proper divisor (prime factors of 2^256-1 up to the
+    # Fermat primes): x^((2^256-1)/q) != 1
+    for q in (3, 5, 17, 257, 641, 65537, 274177, 6700417):
+        assert powmod((2 ** 256 - 1) // q) != 1
+
+
+def test_xoshiro_jump_equals_steps(orc):
+    """jump(N) == N single steps, N <= 4096 plus random N, for both jump
+    constructions (polynomial and matrix)."""
+    g = orc.gen("xoshiro256pp", 12345)
+    s0 = orc.state_words(g)
+    words = orc.next_words(g, 4100)
+    rng = _rng()
+    Ns = [0, 1, 2, 3, 63, 64, 255, 256, 257, 1000, 4095] + [int(x) for x in rng.integers(0, 4096, 6)]
+    for N in Ns:
+        for method in ("poly", "matrix"):
+            s = orc.xoshiro_jump(s0, N, method)
+            h = orc.Gen()
+            orc.lib().or_gen_set(ctypes.byref(h), 1, np.array(s, np.uint64).ctypes.data_as(ctypes.c_void_p))
+            assert int(orc.next_words(h, 1)[0]) == int(words[N]), (N, method)
+
+
+def test_xoshiro_jump_composition_and_methods_agree(orc):
+    """jump(a) o jump(b) == jump(a+b); T^(2^k) by matrix squaring == by the
+    jump polynomial for k in {32, 64, 96, 128, 192} (Sec. 2.3)."""
+    s0 = orc.state_words(orc.gen("xoshiro256pp", 99))
+    rng = _rng()
+    for _ in range(4):
+        a = int(rng.integers(0, 2 ** 63)) * 3 + 1
+        b = int(rng.integers(0, 2 ** 63)) << 40
+        assert orc.xoshiro_jump(orc.xoshiro_jump(s0, a), b) == orc.xoshiro_jump(s0, a + b)
+    for k in (32, 64, 96, 128, 192):
+        assert orc.xoshiro_jump(s0, 2 ** k, "poly") == orc.xoshiro_jump(s0, 2 ** k, "matrix")
+
+
+def test_xoshiro_bit_balance(orc):
+    """Statistics: each of the 64 bit positions is 1 with probability 1/2."""
+    g = orc.gen("xoshiro256pp", 2024)
+    w = orc.next_words(g, 1 << 18)
+    bits = np.unpackbits(w.view(np.uint8)).reshape(-1, 64).mean(axis=0)
+    sigma = 0.5 / np.sqrt(len(w))
+    assert np.all(np.abs(bits - 0.5) < 6 * sigma)
+
+
+def test_seek_matches_sequential(orc):
+    for eng in ("xoshiro256pp", "pcg64dxsm", "philox4x32_10"):
+        g = orc.gen(eng, 31337)
+        w = orc.next_words(g, 3000)
+        for p in (0, 1, 2, 777, 2999):
+            h = orc.gen(eng, 31337, pos=p)
+            assert int(orc.next_words(h, 1)[0]) == int(w[p]), (eng, p)
+
+
+# ------------------------------------------------------------------ Philox
+def test_philox_structure(orc):
+    """Counter-based: word p is half (p mod 2) of block counter + p/2; the
+    counter is a 128-bit integer (carry across the 32-bit lanes); different
+    keys give unrelated blocks; output bits are balanced."""
+    g = orc.gen("philox4x32_10", 2024)
+    ctr = g.s[0] | (g.s[1] << 64)
+    key = g.s[2]
+    w = orc.next_words(g, 64)
+    for b in range(32):
+        c = ctr + b
+        o = orc.philox([(c >> (32 * i)) & 0xFFFFFFFF for i in range(4)], [key & 0xFFFFFFFF, key >> 32])
+        assert int(w[2 * b]) == o[0] | (o[1] << 32) and int(w[2 * b + 1]) == o[2] | (o[3] << 32)
+    # carry propagation across 32-bit lanes
+    a = orc.philox([0xFFFFFFFF, 0, 0, 0], [1, 2])
+    b = orc.philox([0, 1, 0, 0], [1, 2])
+    assert a != b
+    outs = np.array([orc.philox([i, 0, 0, 0], [5, 6]) for i in range(4096)], np.uint32)
+    bits = np.unpackbits(outs.view(np.uint8)).mean()
+    assert abs(bits - 0.5) < 6 * 0.5 / np.sqrt(outs.size * 32)
