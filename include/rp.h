@@ -1,0 +1,135 @@
+/* rp.h -- C ABI of the GB300 bulk-fill library (librp.so).
+ *
+ * Bulk filling of a device array with n variates from one seeded engine
+ * stream, after Randompack (arXiv 2605.05099): engines of Sec. 2.2
+ * (xoshiro256++, PCG64-DXSM; Philox4x32-10 in place of the paper's
+ * Philox-4x64), seeding and stream control of Sec. 2.3, the distribution
+ * algorithms of Sec. 3 and the validation ideas of Sec. 5.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Status: 0 (RP_OK) on success, a negative RP_ERR_* code otherwise; the
+ *   message of the last failure on the calling host thread is returned by
+ *   rp_last_error() (mirrors the per-RNG last-error string of Sec. 2.1).
+ *   No entry point aborts, traps or prints.
+ * - Stream model: a stream is an engine state seeded from (seed, spawn key)
+ *   (Sec. 2.3); `stream` is the spawn key, or RP_NO_STREAM for none.  Word p
+ *   of a stream is the p-th 64-bit engine output after seeding.  `pos` is
+ *   read as the first word to use and, on success, set to the next unused
+ *   word: a fill consumes exactly the words its variates used, so two fills
+ *   in a row give the same values as one fill of the combined length.
+ * - Memory: `d_*` pointers are device memory owned by the caller; `h_*`
+ *   pointers are host memory owned by the caller.  Output pointers must be
+ *   8-byte aligned.  The library owns only immutable tables and an internal
+ *   scratch pool (tile status words) that grows on demand.
+ * - Streams: `cuda_stream` is a cudaStream_t (NULL = legacy default stream).
+ *   Fill calls enqueue their kernels on it and return after they have
+ *   completed (the call synchronises that stream once at the end to read
+ *   the consumed-word count and the device status word).
+ * - Threading: calls from several host threads are serialised internally.
+ * - n = 0 is a valid no-op that leaves *pos unchanged (Sec. 5.1, zero
+ *   lengths must work).
+ */
+#ifndef RP_H
+#define RP_H
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  RP_XOSHIRO256PP = 1,   /* Blackman & Vigna 2019, 4 x 64-bit state */
+  RP_PCG64DXSM = 2,      /* O'Neill 2019, 128-bit LCG + DXSM output */
+  RP_PHILOX4X32_10 = 3   /* Salmon et al. 2011, 128-bit counter, 64-bit key */
+} rp_engine;
+
+typedef int rp_status;
+#define RP_OK 0
+#define RP_ERR_NULL (-1)      /* a required pointer is NULL */
+#define RP_ERR_PARAM (-2)     /* invalid distribution parameter or size */
+#define RP_ERR_ENGINE (-3)    /* unknown engine id */
+#define RP_ERR_CUDA (-4)      /* CUDA runtime error (message has details) */
+#define RP_ERR_TIMEOUT (-5)   /* a bounded device wait ran out */
+#define RP_ERR_NOMEM (-6)     /* scratch allocation failed */
+#define RP_ERR_INTERNAL (-7)  /* device-side consistency check failed */
+#define RP_ERR_SEED (-8)      /* seeding produced an all-zero xoshiro state */
+
+#define RP_NO_STREAM UINT64_MAX
+
+/* ---------------------------------------------------------------------
+ * Fills.  Common arguments:
+ *   engine  rp_engine id
+ *   seed    user seed (Sec. 2.3 seeding: seed + spawn key hashed into a
+ *           128-bit pool; NumPy SeedSequence semantics)
+ *   stream  spawn key, or RP_NO_STREAM
+ *   pos     in: first stream word to use; out: next unused word (host ptr)
+ *   n       number of variates
+ *   d_out   device array of n elements
+ * ------------------------------------------------------------------- */
+
+/* Raw 64-bit words (Table "discrete": uint64 with b = 0; raw bitstream). */
+rp_status rp_fill_u64(rp_engine engine, uint64_t seed, uint64_t stream, uint64_t* pos,
+                      size_t n, uint64_t* d_out, void* cuda_stream);
+
+/* U[0,1) doubles with 53-bit resolution: floor(u / 2^11) * 2^-53 (Sec. 3.1,
+ * method 1), one word per variate, bit-exact. */
+rp_status rp_fill_uniform(rp_engine engine, uint64_t seed, uint64_t stream, uint64_t* pos,
+                          size_t n, double* d_out, void* cuda_stream);
+
+/* Unbiased integers in [0, m) by Lemire's multiply-and-reject (Sec. 3.2):
+ * one word per attempt, reject while low64(u m) < 2^64 mod m, output
+ * high64(u m).  m = 0 gives the full 64-bit range (raw words). */
+rp_status rp_fill_bounded(rp_engine engine, uint64_t seed, uint64_t stream, uint64_t* pos,
+                          size_t n, uint64_t m, uint64_t* d_out, void* cuda_stream);
+
+/* Standard normal by the 256-strip ziggurat (Sec. 3.1): low byte = strip,
+ * bit 8 = sign, bits 9-60 = magnitude r, x = +-RN(r w_i); fast accept when
+ * r < k_i; wedge test y < exp(-x^2/2); tail beyond R by Marsaglia's 1964
+ * method.  Accept decisions are exact (correctly rounded exp/log). */
+rp_status rp_fill_normal(rp_engine engine, uint64_t seed, uint64_t stream, uint64_t* pos,
+                         size_t n, double* d_out, void* cuda_stream);
+
+/* Standard exponential by the 256-strip ziggurat (Sec. 3.1): bits 8-60 =
+ * magnitude; memoryless tail R - log(1 - U). */
+rp_status rp_fill_exp(rp_engine engine, uint64_t seed, uint64_t stream, uint64_t* pos,
+                      size_t n, double* d_out, void* cuda_stream);
+
+/* Gamma(alpha, 1) by Marsaglia & Tsang (Sec. 3.1, gamma); alpha < 1 by the
+ * boost Gamma(alpha+1) U^(1/alpha).  alpha > 0. */
+rp_status rp_fill_gamma(rp_engine engine, uint64_t seed, uint64_t stream, uint64_t* pos,
+                        size_t n, double alpha, double* d_out, void* cuda_stream);
+
+/* Beta(a, b) = X / (X + Y), X ~ Gamma(a) drawn before Y ~ Gamma(b)
+ * (Table "continuous", beta).  a, b > 0. */
+rp_status rp_fill_beta(rp_engine engine, uint64_t seed, uint64_t stream, uint64_t* pos,
+                       size_t n, double a, double b, double* d_out, void* cuda_stream);
+
+/* ---------------------------------------------------------------------
+ * Seeding and stream control (Sec. 2.3), host only.
+ * ------------------------------------------------------------------- */
+/* Engine state words from (seed, spawn key): xoshiro s0..s3; PCG64 state
+ * hi, state lo, inc hi, inc lo; Philox counter lo, counter hi, key.
+ * words must hold 4 entries; *nw receives the count used. */
+rp_status rp_seed_state(rp_engine engine, uint64_t seed, uint64_t stream, uint64_t* words, int* nw);
+
+/* Advance state words (layout as above) by delta = delta_hi 2^64 + delta_lo
+ * words: GF(2) jump polynomial for xoshiro (Sec. 4.4), LCG skip-ahead for
+ * PCG64 (Sec. 2.3), counter offset for Philox. */
+rp_status rp_jump_state(rp_engine engine, uint64_t* words, uint64_t delta_hi, uint64_t delta_lo);
+
+/* Message of the last failed call on this host thread ("" if none). */
+const char* rp_last_error(void);
+
+/* Library version string. */
+const char* rp_version(void);
+
+/* Ziggurat tables used by the kernels (which: 0 normal, 1 exponential):
+ * k[256], w[256], f[256] and R.  For inspection and tests. */
+rp_status rp_ziggurat_tables(int which, uint64_t* k, double* w, double* f, double* R);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,180 @@
+"""Python binding of librp, the GB300 bulk-fill library (C ABI in include/rp.h).
+
+Argument marshalling only: every fill runs in the CUDA kernels of librp.so.
+PyTorch supplies device memory and the current CUDA stream.  There is no CPU
+fallback; a missing or unloadable library raises immediately.
+
+    import torch, paper_2605_05099_gb300 as rp
+    x = torch.empty(1 << 20, dtype=torch.float64, device="cuda")
+    pos = rp.rp_fill_normal(rp.XOSHIRO256PP, 12345, rp.NO_STREAM, 0, x)
+"""
+import ctypes
+import os
+
+import torch
+
+XOSHIRO256PP, PCG64DXSM, PHILOX4X32_10 = 1, 2, 3
+ENGINES = {"xoshiro256pp": XOSHIRO256PP, "pcg64dxsm": PCG64DXSM, "philox4x32_10": PHILOX4X32_10}
+NO_STREAM = (1 << 64) - 1
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "librp.so")
+
+STATUS = {0: "RP_OK", -1: "RP_ERR_NULL", -2: "RP_ERR_PARAM", -3: "RP_ERR_ENGINE", -4: "RP_ERR_CUDA",
+          -5: "RP_ERR_TIMEOUT", -6: "RP_ERR_NOMEM", -7: "RP_ERR_INTERNAL", -8: "RP_ERR_SEED"}
+
+
+class RPError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def lib():
+    """Load librp.so (building it first when the sources are newer)."""
+    global _lib
+    if _lib is None:
+        from . import build as _build
+        _build.build()
+        L = ctypes.CDLL(LIB_PATH)
+        u64, i32, dbl, sz, vp = ctypes.c_uint64, ctypes.c_int, ctypes.c_double, ctypes.c_size_t, ctypes.c_void_p
+        pu64 = ctypes.POINTER(u64)
+        sig = {
+            "rp_fill_u64": [i32, u64, u64, pu64, sz, vp, vp],
+            "rp_fill_uniform": [i32, u64, u64, pu64, sz, vp, vp],
+            "rp_fill_bounded": [i32, u64, u64, pu64, sz, u64, vp, vp],
+            "rp_fill_normal": [i32, u64, u64, pu64, sz, vp, vp],
+            "rp_fill_exp": [i32, u64, u64, pu64, sz, vp, vp],
+            "rp_fill_gamma": [i32, u64, u64, pu64, sz, dbl, vp, vp],
+            "rp_fill_beta": [i32, u64, u64, pu64, sz, dbl, dbl, vp, vp],
+            "rp_seed_state": [i32, u64, u64, pu64, ctypes.POINTER(i32)],
+            "rp_jump_state": [i32, pu64, u64, u64],
+            "rp_ziggurat_tables": [i32, pu64, ctypes.POINTER(dbl), ctypes.POINTER(dbl), ctypes.POINTER(dbl)],
+        }
+        for name, args in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = i32
+        L.rp_last_error.restype = ctypes.c_char_p
+        L.rp_last_error.argtypes = []
+        L.rp_version.restype = ctypes.c_char_p
+        L.rp_version.argtypes = []
+        _lib = L
+    return _lib
+
+
+def _check(rc):
+    if rc != 0:
+        raise RPError(rc, lib().rp_last_error().decode())
+
+
+def _engine(e):
+    return ENGINES[e] if isinstance(e, str) else int(e)
+
+
+def _stream_handle(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _out(out, dtype):
+    if not isinstance(out, torch.Tensor) or not out.is_cuda:
+        raise TypeError("out must be a CUDA tensor")
+    if out.dtype != dtype or not out.is_contiguous():
+        raise TypeError(f"out must be a contiguous {dtype} tensor")
+    return ctypes.c_void_p(out.data_ptr()), out.numel()
+
+
+def _fill(fn, engine, seed, stream, pos, out, dtype, extra=(), cuda_stream=None):
+    p, n = _out(out, dtype)
+    cpos = ctypes.c_uint64(pos)
+    _check(fn(_engine(engine), seed, stream, ctypes.byref(cpos), n, *extra, p, _stream_handle(cuda_stream)))
+    return cpos.value
+
+
+# ---- fills: same names and argument order as the C ABI; `out` is a CUDA
+# tensor of n elements; the return value is the new stream position.
+def rp_fill_u64(engine, seed, stream, pos, out, cuda_stream=None):
+    return _fill(lib().rp_fill_u64, engine, seed, stream, pos, out, torch.uint64, cuda_stream=cuda_stream)
+
+
+def rp_fill_uniform(engine, seed, stream, pos, out, cuda_stream=None):
+    return _fill(lib().rp_fill_uniform, engine, seed, stream, pos, out, torch.float64, cuda_stream=cuda_stream)
+
+
+def rp_fill_bounded(engine, seed, stream, pos, m, out, cuda_stream=None):
+    return _fill(lib().rp_fill_bounded, engine, seed, stream, pos, out, torch.uint64, (m,), cuda_stream)
+
+
+def rp_fill_normal(engine, seed, stream, pos, out, cuda_stream=None):
+    return _fill(lib().rp_fill_normal, engine, seed, stream, pos, out, torch.float64, cuda_stream=cuda_stream)
+
+
+def rp_fill_exp(engine, seed, stream, pos, out, cuda_stream=None):
+    return _fill(lib().rp_fill_exp, engine, seed, stream, pos, out, torch.float64, cuda_stream=cuda_stream)
+
+
+def rp_fill_gamma(engine, seed, stream, pos, alpha, out, cuda_stream=None):
+    return _fill(lib().rp_fill_gamma, engine, seed, stream, pos, out, torch.float64, (float(alpha),), cuda_stream)
+
+
+def rp_fill_beta(engine, seed, stream, pos, a, b, out, cuda_stream=None):
+    return _fill(lib().rp_fill_beta, engine, seed, stream, pos, out, torch.float64, (float(a), float(b)),
+                 cuda_stream)
+
+
+def rp_seed_state(engine, seed, stream=NO_STREAM):
+    w = (ctypes.c_uint64 * 4)()
+    nw = ctypes.c_int()
+    _check(lib().rp_seed_state(_engine(engine), seed, stream, w, ctypes.byref(nw)))
+    return [int(x) for x in w[: nw.value]]
+
+
+def rp_jump_state(engine, words, delta):
+    w = (ctypes.c_uint64 * 4)(*(list(words) + [0] * (4 - len(words))))
+    _check(lib().rp_jump_state(_engine(engine), w, (delta >> 64) & (2 ** 64 - 1), delta & (2 ** 64 - 1)))
+    return [int(x) for x in w[: len(words)]]
+
+
+def rp_ziggurat_tables(which):
+    k = (ctypes.c_uint64 * 256)()
+    w = (ctypes.c_double * 256)()
+    f = (ctypes.c_double * 256)()
+    R = ctypes.c_double()
+    _check(lib().rp_ziggurat_tables(which, k, w, f, ctypes.byref(R)))
+    return list(k), list(w), list(f), R.value
+
+
+def rp_last_error():
+    return lib().rp_last_error().decode()
+
+
+def rp_version():
+    return lib().rp_version().decode()
+
+
+# ---- convenience: allocate and fill
+_DIST_DTYPE = {"u64": torch.uint64, "uniform": torch.float64, "bounded": torch.uint64, "normal": torch.float64,
+               "exp": torch.float64, "gamma": torch.float64, "beta": torch.float64}
+
+
+def fill(dist, n, engine="xoshiro256pp", seed=0, stream=NO_STREAM, pos=0, params=(), out=None, cuda_stream=None):
+    """Allocate (unless `out` is given) and fill n variates; returns (out, new_pos)."""
+    if out is None:
+        out = torch.empty(n, dtype=_DIST_DTYPE[dist], device="cuda")
+    f = {"u64": rp_fill_u64, "uniform": rp_fill_uniform, "normal": rp_fill_normal, "exp": rp_fill_exp}
+    if dist in f:
+        newpos = f[dist](engine, seed, stream, pos, out, cuda_stream)
+    elif dist == "bounded":
+        newpos = rp_fill_bounded(engine, seed, stream, pos, params[0], out, cuda_stream)
+    elif dist == "gamma":
+        newpos = rp_fill_gamma(engine, seed, stream, pos, params[0], out, cuda_stream)
+    elif dist == "beta":
+        newpos = rp_fill_beta(engine, seed, stream, pos, params[0], params[1], out, cuda_stream)
+    else:
+        raise ValueError(dist)
+    return out, newpos

@@ -1,0 +1,275 @@
+// Device building blocks of librp: engines with jump-ahead, exact integer
+// conversions, double-double elementary functions for rare exact decisions,
+// and the ziggurat tables.  sm_103a only.
+#pragma once
+#include <cstdint>
+
+#include "rp_internal.h"
+
+namespace rp {
+
+typedef unsigned long long u64;
+typedef unsigned __int128 u128;
+
+// ------------------------------------------------------------------ bits
+__device__ __forceinline__ u64 rotl64(u64 x, int k) { return (x << k) | (x >> (64 - k)); }
+
+// 53-bit uniform floor(u / 2^11) 2^-53 assembled from integer operations
+// (exact: the value has at most 53 significant bits), Sec. 3.1 method 1.
+__device__ __forceinline__ double u53_bits(u64 u) {
+  u64 v = u >> 11;
+  if (v == 0) return 0.0;
+  int lz = __clzll(v);                       // >= 11
+  u64 mt = v << (lz - 11);                   // in [2^52, 2^53)
+  return __longlong_as_double((long long)((((u64)(1032 - lz)) << 52) + mt));
+}
+
+// Exact RN(r * w) for 0 <= r < 2^53 and w = wm 2^we with wm in [2^52, 2^53),
+// using integer multiplies only (the FP64 pipe of this GPU is ~40x slower
+// than its integer pipes).  msh = wm << 11, wtz = trailing zeros of wm.
+__device__ __forceinline__ double mul_rn_int(u64 r, u64 msh, int wtz, int we) {
+  if (r == 0) return 0.0;
+  int lz = __clzll(r);
+  u64 rn = r << lz;                          // top bit 63
+  u64 hi = __umul64hi(rn, msh);              // r wm 2^(lz+11) = hi 2^64 + lo
+  int tzr = __ffsll((long long)r) - 1;
+  bool lo_nz = (tzr + lz + wtz + 11) < 64;   // lo != 0
+  int top = (int)(hi >> 63);
+  int sh = 10 + top;
+  u64 mt = hi >> sh;                         // 53-bit significand (truncated)
+  u64 rem = hi & ((1ull << sh) - 1);
+  u64 half = 1ull << (sh - 1);
+  bool up = (rem > half) || (rem == half && (lo_nz || (mt & 1)));
+  mt += up ? 1 : 0;                          // a carry into bit 53 bumps the exponent below
+  int q = sh + 53 - lz + we;                 // value = mt 2^q
+  return __longlong_as_double((long long)((((u64)(q + 1074)) << 52) + mt));
+}
+
+// ------------------------------------------------------------------ double-double
+struct dd { double hi, lo; };
+
+__device__ __forceinline__ dd dd_two_sum(double a, double b) {
+  double s = __dadd_rn(a, b);
+  double bb = __dsub_rn(s, a);
+  double e = __dadd_rn(__dsub_rn(a, __dsub_rn(s, bb)), __dsub_rn(b, bb));
+  return {s, e};
+}
+__device__ __forceinline__ dd dd_quick(double a, double b) {
+  double s = __dadd_rn(a, b);
+  return {s, __dsub_rn(b, __dsub_rn(s, a))};
+}
+__device__ __forceinline__ dd dd_prod(double a, double b) {
+  double p = __dmul_rn(a, b);
+  return {p, __fma_rn(a, b, -p)};
+}
+__device__ __forceinline__ dd dd_addx(dd a, dd b) {
+  dd s = dd_two_sum(a.hi, b.hi);
+  dd t = dd_two_sum(a.lo, b.lo);
+  s.lo = __dadd_rn(s.lo, t.hi);
+  s = dd_quick(s.hi, s.lo);
+  s.lo = __dadd_rn(s.lo, t.lo);
+  return dd_quick(s.hi, s.lo);
+}
+__device__ __forceinline__ dd dd_mulx(dd a, dd b) {
+  dd p = dd_prod(a.hi, b.hi);
+  p.lo = __dadd_rn(p.lo, __dadd_rn(__dmul_rn(a.hi, b.lo), __dmul_rn(a.lo, b.hi)));
+  return dd_quick(p.hi, p.lo);
+}
+__device__ __forceinline__ dd dd_scale_inv(dd a, double k) {  // a / k, k a small integer
+  double q = __ddiv_rn(a.hi, k);
+  dd p = dd_prod(q, k);
+  double r = __ddiv_rn(__dadd_rn(__dsub_rn(__dsub_rn(a.hi, p.hi), p.lo), a.lo), k);
+  return dd_quick(q, r);
+}
+
+// exp(x) to ~2^-100 relative: x = k ln2 + r (ln 2 in three parts), exp(r) =
+// exp(r/256)^256 with a degree-11 Taylor polynomial, then 2^k.
+__device__ dd dd_exp_dev(double x) {
+  const double L1 = 0x1.62e42fefa39efp-1, L2 = 0x1.abc9e3b39803fp-56, L3 = 0x1.7b57a079a1934p-111;
+  const double INV_LN2 = 0x1.71547652b82fep+0;
+  double k = rint(__dmul_rn(x, INV_LN2));
+  dd a = dd_prod(k, L1);
+  dd r = dd_addx({x, 0.0}, {-a.hi, -a.lo});
+  dd b = dd_prod(k, L2);
+  r = dd_addx(r, {-b.hi, -b.lo});
+  r = dd_addx(r, {-__dmul_rn(k, L3), 0.0});
+  r.hi = ldexp(r.hi, -8);
+  r.lo = ldexp(r.lo, -8);
+  dd p = {1.0, 0.0};
+  for (int j = 11; j >= 1; --j) p = dd_addx({1.0, 0.0}, dd_scale_inv(dd_mulx(r, p), (double)j));
+  for (int j = 0; j < 8; ++j) p = dd_mulx(p, p);
+  int ki = (int)k;
+  return {ldexp(p.hi, ki), ldexp(p.lo, ki)};
+}
+
+// log(y), y > 0, by one Newton step on exp from the libm value.
+__device__ dd dd_log_dev(double y) {
+  double y0 = log(y);
+  dd e = dd_exp_dev(-y0);
+  dd z = dd_addx(dd_mulx(e, {y, 0.0}), {-1.0, 0.0});
+  dd zz = dd_mulx(z, z);
+  z = dd_addx(z, {-0.5 * zz.hi, -0.5 * zz.lo});
+  return dd_addx({y0, 0.0}, z);
+}
+
+// Correctly rounded exp / log via the normalised double-double value.
+__device__ __forceinline__ double cr_exp_dev(double x) {
+  if (x == 0.0) return 1.0;
+  if (x < -708.0) return exp(x);
+  return dd_exp_dev(x).hi;
+}
+__device__ __forceinline__ double cr_log_dev(double y) {
+  if (y == 1.0) return 0.0;
+  if (y == 0.0) return -__longlong_as_double(0x7ff0000000000000ll);
+  return dd_log_dev(y).hi;
+}
+
+// Exact decision y < RN(exp(t)): CUDA exp (max error a few ulp) decides
+// unless y lies within 2^-48 relative of it; then the correctly rounded value
+// decides.
+__device__ __forceinline__ bool lt_cr_exp(double y, double t) {
+  double e = exp(t);
+  double m = __dmul_rn(e, 0x1.0p-48);
+  if (y < __dsub_rn(e, m)) return true;
+  if (y > __dadd_rn(e, m)) return false;
+  return y < cr_exp_dev(t);
+}
+
+// ------------------------------------------------------------------ ziggurat tables
+struct ZigDev {
+  u64 k[256];
+  u64 msh[256];     // significand of w_i shifted to bit 63
+  double f[256];
+  int we[256];      // w_i = (msh >> 11) 2^we
+  int wtz[256];     // trailing zeros of the significand
+  double R;
+};
+
+// ------------------------------------------------------------------ engines
+// GF(2) matrix-vector product with a nibble table: out = XOR over the 64
+// four-bit chunks c of the input of tab[c][chunk value] (32-byte entries).
+__device__ __forceinline__ void gf2_apply(const ulonglong4_32a* __restrict__ tab, u64& s0, u64& s1, u64& s2, u64& s3) {
+  u64 a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+  u64 in[4] = {s0, s1, s2, s3};
+#pragma unroll
+  for (int w = 0; w < 4; ++w) {
+    u64 x = in[w];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      int v = (int)((x >> (4 * q)) & 15u);
+      const ulonglong2* e = (const ulonglong2*)(tab + ((w * 16 + q) * 16 + v));
+      ulonglong2 t0 = __ldg(e), t1 = __ldg(e + 1);
+      a0 ^= t0.x; a1 ^= t0.y; a2 ^= t1.x; a3 ^= t1.y;
+    }
+  }
+  s0 = a0; s1 = a1; s2 = a2; s3 = a3;
+}
+
+// xoshiro256++ (Blackman & Vigna): output from the current state, then the
+// linear transition.  Jumps by precomputed GF(2) matrices T^(2^j).
+struct XoshiroDev {
+  u64 s0, s1, s2, s3;
+  __device__ __forceinline__ u64 next() {
+    u64 r = rotl64(s0 + s3, 23) + s0;
+    u64 t = s1 << 17;
+    s2 ^= s0; s3 ^= s1; s1 ^= s2; s0 ^= s3; s2 ^= t; s3 = rotl64(s3, 45);
+    return r;
+  }
+  __device__ void init(const EngineArgs& a, u64 off) {
+    s0 = a.s[0]; s1 = a.s[1]; s2 = a.s[2]; s3 = a.s[3];
+    const ulonglong4_32a* tab = (const ulonglong4_32a*)a.gf2_pow;
+    while (off) {
+      int j = __ffsll((long long)off) - 1;
+      gf2_apply(tab + (size_t)j * 1024, s0, s1, s2, s3);
+      off &= off - 1;
+    }
+  }
+  __device__ __forceinline__ void advance(const EngineArgs& a) {
+    gf2_apply((const ulonglong4_32a*)a.gf2_stride, s0, s1, s2, s3);
+  }
+};
+
+// PCG64-DXSM (O'Neill): DXSM output of the current state, then the LCG step
+// with the 64-bit multiplier.  Jumps by affine powers (A, G): s <- A s + G inc.
+struct PcgDev {
+  u128 st, inc;
+  __device__ __forceinline__ u64 next() {
+    u64 hi = (u64)(st >> 64), lo = (u64)st | 1ull;
+    hi ^= hi >> 32;
+    hi *= 0xda942042e4dd58b5ull;
+    hi ^= hi >> 48;
+    hi *= lo;
+    st = st * (u128)0xda942042e4dd58b5ull + inc;
+    return hi;
+  }
+  __device__ void init(const EngineArgs& a, u64 off) {
+    st = ((u128)a.s[0] << 64) | a.s[1];
+    inc = ((u128)a.s[2] << 64) | a.s[3];
+    while (off) {
+      int j = __ffsll((long long)off) - 1;
+      const u64* p = a.pcg_pow + 4 * j;
+      u128 A = ((u128)p[0] << 64) | p[1], G = ((u128)p[2] << 64) | p[3];
+      st = A * st + G * inc;
+      off &= off - 1;
+    }
+  }
+  __device__ __forceinline__ void advance(const EngineArgs& a) {
+    u128 A = ((u128)a.pcg_stride[0] << 64) | a.pcg_stride[1];
+    u128 G = ((u128)a.pcg_stride[2] << 64) | a.pcg_stride[3];
+    st = A * st + G * inc;
+  }
+};
+
+// Philox4x32-10 (Salmon et al.): word i of the stream is half (i & 1) of
+// block (counter + i/2); the block's 32-bit lanes x0..x3 give x0|x1<<32 and
+// x2|x3<<32.
+struct PhiloxDev {
+  u64 c_lo, c_hi;
+  unsigned k0, k1;
+  u64 idx;         // next word index relative to the seeded counter
+  u64 buf;
+  __device__ __forceinline__ void block(u64 b, u64& w0, u64& w1) const {
+    u128 c = (((u128)c_hi << 64) | c_lo) + (u128)b;
+    unsigned x0 = (unsigned)c, x1 = (unsigned)(c >> 32), x2 = (unsigned)(c >> 64), x3 = (unsigned)(c >> 96);
+    unsigned ka = k0, kb = k1;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+      unsigned h0 = __umulhi(0xD2511F53u, x0), l0 = 0xD2511F53u * x0;
+      unsigned h1 = __umulhi(0xCD9E8D57u, x2), l1 = 0xCD9E8D57u * x2;
+      unsigned y0 = h1 ^ x1 ^ ka, y2 = h0 ^ x3 ^ kb;
+      x0 = y0; x1 = l1; x2 = y2; x3 = l0;
+      ka += 0x9E3779B9u; kb += 0xBB67AE85u;
+    }
+    w0 = (u64)x0 | ((u64)x1 << 32);
+    w1 = (u64)x2 | ((u64)x3 << 32);
+  }
+  __device__ __forceinline__ u64 next() {
+    u64 r;
+    if ((idx & 1) == 0) {
+      u64 w0, w1;
+      block(idx >> 1, w0, w1);
+      buf = w1;
+      r = w0;
+    } else {
+      r = buf;
+    }
+    ++idx;
+    return r;
+  }
+  __device__ void init(const EngineArgs& a, u64 off) {
+    c_lo = a.s[0]; c_hi = a.s[1];
+    k0 = (unsigned)a.s[2]; k1 = (unsigned)(a.s[2] >> 32);
+    idx = a.word0 + off;
+    if (idx & 1) {  // starting on the odd half: fetch it
+      u64 w0;
+      block(idx >> 1, w0, buf);
+    }
+  }
+  __device__ __forceinline__ void advance(const EngineArgs& a) {
+    u64 start = idx;  // callers advance a saved chunk-start copy
+    idx = start + a.stride;
+    if (idx & 1) { u64 w0; block(idx >> 1, w0, buf); }
+  }
+};
+
+}  // namespace rp

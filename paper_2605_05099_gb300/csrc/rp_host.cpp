@@ -1,0 +1,564 @@
+// Host side of librp: argument checks, seeding and stream control
+// (Randompack Sec. 2.3), jump tables, scratch management and the C ABI
+// declared in include/rp.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/rp.h"
+#include "rp_internal.h"
+
+namespace rp {
+struct ZigDev;
+int upload_zig(const void* host2);
+}  // namespace rp
+
+namespace {
+
+typedef unsigned long long u64;
+typedef unsigned __int128 u128;
+
+thread_local std::string g_err;
+std::mutex g_mu;
+
+rp_status fail(rp_status code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+
+rp_status cuda_fail(int e, const char* where) {
+  return fail(RP_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString((cudaError_t)e));
+}
+
+// ---------------------------------------------------------------- seeding
+// Seed and spawn key are hashed into a pool of four 32-bit words, then
+// hashed out to the requested number of state words (Sec. 2.3; NumPy
+// SeedSequence semantics, O'Neill's seed_seq design).
+struct SeedSeq {
+  static constexpr uint32_t kA = 0x43b0d7e5u, kMA = 0x931e8875u, kB = 0x8b51f9ddu, kMB = 0x58f38dedu;
+  static constexpr uint32_t kL = 0xca01f9ddu, kR = 0x4973f715u;
+  uint32_t pool[4];
+
+  explicit SeedSeq(const std::vector<uint32_t>& ent) {
+    uint32_t hc = kA;
+    auto hash = [&hc](uint32_t v) {
+      v ^= hc;
+      hc *= kMA;
+      v *= hc;
+      return v ^ (v >> 16);
+    };
+    auto mix = [](uint32_t x, uint32_t y) {
+      uint32_t r = kL * x - kR * y;
+      return r ^ (r >> 16);
+    };
+    for (int i = 0; i < 4; ++i) pool[i] = hash(i < (int)ent.size() ? ent[i] : 0u);
+    for (int s = 0; s < 4; ++s)
+      for (int d = 0; d < 4; ++d)
+        if (s != d) pool[d] = mix(pool[d], hash(pool[s]));
+    for (size_t s = 4; s < ent.size(); ++s)
+      for (int d = 0; d < 4; ++d) pool[d] = mix(pool[d], hash(ent[s]));
+  }
+  void words64(u64* out, int n) const {
+    uint32_t hc = kB;
+    for (int i = 0; i < 2 * n; ++i) {
+      uint32_t v = pool[i & 3] ^ hc;
+      hc *= kMB;
+      v *= hc;
+      v ^= v >> 16;
+      if (i & 1) out[i / 2] |= (u64)v << 32;
+      else out[i / 2] = v;
+    }
+  }
+};
+
+void append_u32(std::vector<uint32_t>& v, u64 x) {
+  v.push_back((uint32_t)x);
+  if (x >> 32) v.push_back((uint32_t)(x >> 32));
+}
+
+void seed_words(u64 seed, u64 stream, u64* out, int n) {
+  std::vector<uint32_t> ent;
+  append_u32(ent, seed);
+  if (stream != RP_NO_STREAM) {
+    while (ent.size() < 4) ent.push_back(0);
+    append_u32(ent, stream);
+  }
+  SeedSeq(ent).words64(out, n);
+}
+
+// ---------------------------------------------------------------- xoshiro GF(2)
+// 256x256 matrices over GF(2), column j = image of basis vector e_j.
+struct Mat {
+  u64 c[256][4];
+};
+
+void xo_step(u64 s[4]) {
+  u64 t = s[1] << 17;
+  s[2] ^= s[0];
+  s[3] ^= s[1];
+  s[1] ^= s[2];
+  s[0] ^= s[3];
+  s[2] ^= t;
+  s[3] = (s[3] << 45) | (s[3] >> 19);
+}
+
+void mat_vec(const Mat& M, const u64 v[4], u64 r[4]) {
+  u64 a[4] = {0, 0, 0, 0};
+  for (int w = 0; w < 4; ++w) {
+    u64 x = v[w];
+    while (x) {
+      int b = __builtin_ctzll(x);
+      const u64* col = M.c[64 * w + b];
+      a[0] ^= col[0]; a[1] ^= col[1]; a[2] ^= col[2]; a[3] ^= col[3];
+      x &= x - 1;
+    }
+  }
+  memcpy(r, a, sizeof(a));
+}
+
+void mat_mul(const Mat& A, const Mat& B, Mat& out) {  // out = A B
+  Mat tmp;
+  for (int j = 0; j < 256; ++j) mat_vec(A, B.c[j], tmp.c[j]);
+  out = tmp;
+}
+
+struct XoTables {
+  std::vector<Mat> pow;        // pow[j] = T^(2^j), j < 192
+  void* d_pow = nullptr;       // nibble tables of pow[0..63]
+  std::map<u64, void*> d_stride;
+};
+XoTables* g_xo = nullptr;
+
+void nibble_table(const Mat& M, std::vector<u64>& out) {  // 64 x 16 x 4 words
+  out.assign(64 * 16 * 4, 0);
+  for (int c = 0; c < 64; ++c)
+    for (int v = 0; v < 16; ++v)
+      for (int b = 0; b < 4; ++b)
+        if (v >> b & 1)
+          for (int k = 0; k < 4; ++k) out[(c * 16 + v) * 4 + k] ^= M.c[4 * c + b][k];
+}
+
+XoTables& xo() {
+  if (!g_xo) {
+    g_xo = new XoTables;
+    g_xo->pow.resize(192);
+    for (int j = 0; j < 256; ++j) {
+      u64 e[4] = {0, 0, 0, 0};
+      e[j >> 6] = 1ull << (j & 63);
+      xo_step(e);
+      memcpy(g_xo->pow[0].c[j], e, sizeof(e));
+    }
+    for (int j = 1; j < 192; ++j) mat_mul(g_xo->pow[j - 1], g_xo->pow[j - 1], g_xo->pow[j]);
+  }
+  return *g_xo;
+}
+
+void xo_jump(u64 s[4], u128 n) {
+  XoTables& X = xo();
+  for (int j = 0; j < 128 && n; ++j, n >>= 1)
+    if (n & 1) mat_vec(X.pow[j], s, s);
+}
+
+void xo_jump_limbs(u64 s[4], const u64* limbs, int nl) {  // N = sum limbs[i] 2^(64 i), N < 2^192
+  XoTables& X = xo();
+  for (int i = 0; i < nl && i < 3; ++i)
+    for (int b = 0; b < 64; ++b)
+      if (limbs[i] >> b & 1) mat_vec(X.pow[64 * i + b], s, s);
+}
+
+int xo_device_pow(void** out) {
+  XoTables& X = xo();
+  if (!X.d_pow) {
+    std::vector<u64> all(64 * 64 * 16 * 4), one;
+    for (int j = 0; j < 64; ++j) {
+      nibble_table(X.pow[j], one);
+      memcpy(&all[(size_t)j * one.size()], one.data(), one.size() * 8);
+    }
+    int e = (int)cudaMalloc(&X.d_pow, all.size() * 8);
+    if (e) { X.d_pow = nullptr; return e; }
+    e = (int)cudaMemcpy(X.d_pow, all.data(), all.size() * 8, cudaMemcpyHostToDevice);
+    if (e) return e;
+  }
+  *out = X.d_pow;
+  return 0;
+}
+
+int xo_device_stride(u64 D, void** out) {
+  XoTables& X = xo();
+  auto it = X.d_stride.find(D);
+  if (it == X.d_stride.end()) {
+    Mat M;
+    memset(&M, 0, sizeof(M));
+    for (int j = 0; j < 256; ++j) M.c[j][j >> 6] = 1ull << (j & 63);
+    for (int j = 0; j < 64; ++j)
+      if (D >> j & 1) mat_mul(X.pow[j], M, M);
+    std::vector<u64> tab;
+    nibble_table(M, tab);
+    void* d = nullptr;
+    int e = (int)cudaMalloc(&d, tab.size() * 8);
+    if (e) return e;
+    e = (int)cudaMemcpy(d, tab.data(), tab.size() * 8, cudaMemcpyHostToDevice);
+    if (e) return e;
+    it = X.d_stride.emplace(D, d).first;
+  }
+  *out = it->second;
+  return 0;
+}
+
+// ---------------------------------------------------------------- PCG64 affine powers
+constexpr u64 kPcgMult = 0xda942042e4dd58b5ull;
+struct Aff {
+  u128 A, G;  // x -> A x + G inc
+};
+Aff aff_pow2(int j) {  // 2^j steps
+  Aff r{(u128)kPcgMult, 1};
+  for (int i = 0; i < j; ++i) r = Aff{r.A * r.A, r.G * (r.A + 1)};
+  return r;
+}
+Aff aff_steps(u128 n) {
+  Aff acc{1, 0};
+  Aff cur{(u128)kPcgMult, 1};
+  while (n) {
+    if (n & 1) acc = Aff{acc.A * cur.A, acc.G * cur.A + cur.G};
+    cur = Aff{cur.A * cur.A, cur.G * (cur.A + 1)};
+    n >>= 1;
+  }
+  return acc;
+}
+u64* g_pcg_pow = nullptr;
+int pcg_device_pow(u64** out) {
+  if (!g_pcg_pow) {
+    std::vector<u64> h(64 * 4);
+    for (int j = 0; j < 64; ++j) {
+      Aff a = aff_pow2(j);
+      h[4 * j] = (u64)(a.A >> 64); h[4 * j + 1] = (u64)a.A;
+      h[4 * j + 2] = (u64)(a.G >> 64); h[4 * j + 3] = (u64)a.G;
+    }
+    int e = (int)cudaMalloc((void**)&g_pcg_pow, h.size() * 8);
+    if (e) { g_pcg_pow = nullptr; return e; }
+    e = (int)cudaMemcpy(g_pcg_pow, h.data(), h.size() * 8, cudaMemcpyHostToDevice);
+    if (e) return e;
+  }
+  *out = g_pcg_pow;
+  return 0;
+}
+
+// ---------------------------------------------------------------- engine states
+constexpr u128 kPcgMult128 = ((u128)0x2360ED051FC65DA4ull << 64) | 0x4385DF649FCCF645ull;
+
+rp_status seed_state(int engine, u64 seed, u64 stream, u64 s[4]) {
+  u64 w[4] = {0, 0, 0, 0};
+  if (engine == RP_XOSHIRO256PP) {
+    seed_words(seed, stream, w, 4);
+    if ((w[0] | w[1] | w[2] | w[3]) == 0) return fail(RP_ERR_SEED, "seeding gave an all-zero xoshiro256++ state");
+    memcpy(s, w, sizeof(w));
+  } else if (engine == RP_PCG64DXSM) {
+    seed_words(seed, stream, w, 4);
+    u128 initstate = ((u128)w[0] << 64) | w[1], initseq = ((u128)w[2] << 64) | w[3];
+    u128 inc = (initseq << 1) | 1u;
+    u128 st = inc + initstate;
+    st = st * kPcgMult128 + inc;
+    s[0] = (u64)(st >> 64); s[1] = (u64)st; s[2] = (u64)(inc >> 64); s[3] = (u64)inc;
+  } else if (engine == RP_PHILOX4X32_10) {
+    seed_words(seed, stream, w, 3);
+    s[0] = w[0]; s[1] = w[1]; s[2] = w[2]; s[3] = 0;
+  } else {
+    return fail(RP_ERR_ENGINE, "unknown engine id " + std::to_string(engine));
+  }
+  return RP_OK;
+}
+
+void jump_state(int engine, u64 s[4], u128 delta) {
+  if (engine == RP_XOSHIRO256PP) {
+    xo_jump(s, delta);
+  } else if (engine == RP_PCG64DXSM) {
+    Aff a = aff_steps(delta);
+    u128 st = ((u128)s[0] << 64) | s[1], inc = ((u128)s[2] << 64) | s[3];
+    st = a.A * st + a.G * inc;
+    s[0] = (u64)(st >> 64); s[1] = (u64)st;
+  } else {
+    u128 c = (((u128)s[1] << 64) | s[0]) + delta / 2;
+    // an odd delta cannot be expressed in the state words of a block engine;
+    // callers use the word offset instead (rp_fill_* take pos)
+    s[0] = (u64)c; s[1] = (u64)(c >> 64);
+  }
+}
+
+// ---------------------------------------------------------------- ziggurat upload
+#include "zig_tables.inc"
+
+struct ZigHost {
+  u64 k[256];
+  u64 msh[256];
+  double f[256];
+  int we[256];
+  int wtz[256];
+  double R;
+};
+
+void fill_zig(ZigHost& z, const unsigned long long* K, const double* W, const double* F, double R) {
+  for (int i = 0; i < 256; ++i) {
+    z.k[i] = K[i];
+    z.f[i] = F[i];
+    u64 bits;
+    memcpy(&bits, &W[i], 8);
+    int be = (int)((bits >> 52) & 0x7ff);
+    u64 m = (bits & ((1ull << 52) - 1)) | (1ull << 52);
+    z.msh[i] = m << 11;
+    z.we[i] = be - 1075;
+    z.wtz[i] = __builtin_ctzll(m);
+  }
+  z.R = R;
+}
+
+bool g_zig_ready = false;
+int ensure_zig() {
+  if (g_zig_ready) return 0;
+  ZigHost z[2];
+  fill_zig(z[0], RP_ZIG_N_K, RP_ZIG_N_W, RP_ZIG_N_F, RP_ZIG_N_R);
+  fill_zig(z[1], RP_ZIG_E_K, RP_ZIG_E_W, RP_ZIG_E_F, RP_ZIG_E_R);
+  int e = rp::upload_zig(z);
+  if (!e) g_zig_ready = true;
+  return e;
+}
+
+// ---------------------------------------------------------------- scratch
+struct Scratch {
+  unsigned long long* status = nullptr;
+  size_t cap = 0;
+  rp::Ctrl* ctrl = nullptr;
+  rp::Ctrl* h_ctrl = nullptr;  // pinned
+};
+Scratch g_scr;
+
+int ensure_scratch(size_t tiles) {
+  if (!g_scr.ctrl) {
+    int e = (int)cudaMalloc((void**)&g_scr.ctrl, sizeof(rp::Ctrl));
+    if (e) return e;
+    e = (int)cudaMallocHost((void**)&g_scr.h_ctrl, sizeof(rp::Ctrl));
+    if (e) return e;
+  }
+  if (tiles > g_scr.cap) {
+    if (g_scr.status) cudaFree(g_scr.status);
+    size_t cap = tiles < 4096 ? 4096 : tiles + tiles / 2;
+    int e = (int)cudaMalloc((void**)&g_scr.status, cap * 8);
+    if (e) { g_scr.status = nullptr; g_scr.cap = 0; return e; }
+    g_scr.cap = cap;
+  }
+  return 0;
+}
+
+int g_sms = 0;
+int sm_count() {
+  if (!g_sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (g_sms <= 0) g_sms = 1;
+  }
+  return g_sms;
+}
+
+std::map<std::pair<int, int>, int> g_occ;
+
+// expected words per variate (upper estimate used to size one launch)
+double words_per_variate(int dist, const rp::SampArgs& sp) {
+  switch (dist) {
+    case rp::D_BOUNDED: return sp.m ? 1.0 / (1.0 - (double)sp.thresh * 0x1.0p-64) : 1.0;
+    case rp::D_NORMAL: return 1.0235;
+    case rp::D_EXP: return 1.036;
+    default: return 1.0;
+  }
+}
+
+rp_status run_fill(int engine, u64 seed, u64 stream, u64* pos, size_t n, int dist, const rp::SampArgs& sp,
+                   void* d_out, void* cstream) {
+  if (!pos) return fail(RP_ERR_NULL, "pos is NULL");
+  if (n == 0) return RP_OK;
+  if (!d_out) return fail(RP_ERR_NULL, "output pointer is NULL");
+  if ((uintptr_t)d_out & 7) return fail(RP_ERR_PARAM, "output pointer must be 8-byte aligned");
+  if (engine < 1 || engine > 3) return fail(RP_ERR_ENGINE, "unknown engine id " + std::to_string(engine));
+  std::lock_guard<std::mutex> lk(g_mu);
+  u64 s[4] = {0, 0, 0, 0};
+  rp_status st = seed_state(engine, seed, stream, s);
+  if (st) return st;
+  int e = ensure_zig();
+  if (e) return cuda_fail(e, "ziggurat table upload");
+
+  rp::FillArgs a;
+  memset(&a, 0, sizeof(a));
+  a.eng.engine = engine;
+  a.dist = dist;
+  a.sp = sp;
+  rp::TileGeom tg = rp::tile_geom(engine, dist);
+  const u64 T = (u64)tg.tile_words;
+  auto key = std::make_pair(engine, dist);
+  if (!g_occ.count(key)) g_occ[key] = rp::occupancy_blocks(engine, dist);
+  int occ = g_occ[key] > 0 ? g_occ[key] : 1;
+  const bool trivial = (dist == rp::D_U64 || dist == rp::D_UNIFORM);
+
+  u64 cur = *pos;
+  size_t done = 0;
+  const size_t esz = 8;
+  for (int launch = 0; done < n; ++launch) {
+    if (launch > 64) return fail(RP_ERR_INTERNAL, "too many continuation launches");
+    size_t left = n - done;
+    double wpv = words_per_variate(dist, sp);
+    double need = (double)left * wpv + 8.0 * std::sqrt((double)left * (wpv > 1.0 ? wpv : 1.0)) + 64.0;
+    u64 tiles = trivial ? (left + T - 1) / T : (u64)(need / (double)T) + 2;
+    u64 grid = std::min<u64>(tiles, (u64)sm_count() * occ);
+    // engine at word `cur`
+    u64 s0[4];
+    memcpy(s0, s, sizeof(s0));
+    a.eng.word0 = 0;
+    if (engine == RP_PHILOX4X32_10) {
+      a.eng.word0 = cur;
+    } else {
+      jump_state(engine, s0, (u128)cur);
+    }
+    memcpy(a.eng.s, s0, sizeof(s0));
+    a.eng.stride = grid * T;
+    if (engine == RP_XOSHIRO256PP) {
+      e = xo_device_pow((void**)&a.eng.gf2_pow);
+      if (!e) e = xo_device_stride(a.eng.stride, (void**)&a.eng.gf2_stride);
+      if (e) return cuda_fail(e, "jump tables");
+    } else if (engine == RP_PCG64DXSM) {
+      e = pcg_device_pow((u64**)&a.eng.pcg_pow);
+      if (e) return cuda_fail(e, "jump tables");
+      Aff d = aff_steps((u128)a.eng.stride);
+      a.eng.pcg_stride[0] = (u64)(d.A >> 64); a.eng.pcg_stride[1] = (u64)d.A;
+      a.eng.pcg_stride[2] = (u64)(d.G >> 64); a.eng.pcg_stride[3] = (u64)d.G;
+    }
+    a.n = left;
+    a.n_tiles = tiles;
+    a.out = (char*)d_out + done * esz;
+    if (!trivial) {
+      e = ensure_scratch(tiles);
+      if (e) return fail(RP_ERR_NOMEM, std::string("scratch allocation: ") + cudaGetErrorString((cudaError_t)e));
+      a.tile_status = g_scr.status;
+      a.ctrl = g_scr.ctrl;
+      rp::Ctrl c0;
+      memset(&c0, 0, sizeof(c0));
+      c0.done_tile = ~0ull;
+      e = (int)cudaMemsetAsync(g_scr.status, 0, tiles * 8, (cudaStream_t)cstream);
+      if (!e) e = (int)cudaMemcpyAsync(g_scr.ctrl, &c0, sizeof(c0), cudaMemcpyHostToDevice, (cudaStream_t)cstream);
+      if (e) return cuda_fail(e, "scratch reset");
+    }
+    e = rp::launch_fill(a, (int)grid, cstream);
+    if (e) return cuda_fail(e, "kernel launch");
+    if (trivial) {
+      e = (int)cudaStreamSynchronize((cudaStream_t)cstream);
+      if (e) return cuda_fail(e, "fill");
+      done = n;
+      cur += left;
+      break;
+    }
+    e = (int)cudaMemcpyAsync(g_scr.h_ctrl, g_scr.ctrl, sizeof(rp::Ctrl), cudaMemcpyDeviceToHost, (cudaStream_t)cstream);
+    if (!e) e = (int)cudaStreamSynchronize((cudaStream_t)cstream);
+    if (e) return cuda_fail(e, "fill");
+    const rp::Ctrl& c = *g_scr.h_ctrl;
+    if (c.err) {
+      char buf[160];
+      snprintf(buf, sizeof buf, "device check failed (bits 0x%x, tile %llu)", c.err, (unsigned long long)c.err_info);
+      return fail(c.err & rp::E_TIMEOUT ? RP_ERR_TIMEOUT : RP_ERR_INTERNAL, buf);
+    }
+    if (c.done_tile != ~0ull) {
+      cur += c.next_pos;
+      done = n;
+    } else {
+      if (c.total == 0 && c.next_pos == 0) return fail(RP_ERR_INTERNAL, "launch produced no output");
+      done += c.total;
+      cur += c.next_pos;
+    }
+  }
+  *pos = cur;
+  return RP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* rp_last_error(void) { return g_err.c_str(); }
+const char* rp_version(void) { return "rp 0.1 (sm_103a)"; }
+
+rp_status rp_fill_u64(rp_engine engine, uint64_t seed, uint64_t stream, uint64_t* pos, size_t n, uint64_t* d_out,
+                      void* cuda_stream) {
+  rp::SampArgs sp{};
+  return run_fill(engine, seed, stream, (u64*)pos, n, rp::D_U64, sp, d_out, cuda_stream);
+}
+
+rp_status rp_fill_uniform(rp_engine engine, uint64_t seed, uint64_t stream, uint64_t* pos, size_t n, double* d_out,
+                          void* cuda_stream) {
+  rp::SampArgs sp{};
+  return run_fill(engine, seed, stream, (u64*)pos, n, rp::D_UNIFORM, sp, d_out, cuda_stream);
+}
+
+rp_status rp_fill_bounded(rp_engine engine, uint64_t seed, uint64_t stream, uint64_t* pos, size_t n, uint64_t m,
+                          uint64_t* d_out, void* cuda_stream) {
+  rp::SampArgs sp{};
+  sp.m = m;
+  if (m == 0) return run_fill(engine, seed, stream, (u64*)pos, n, rp::D_U64, sp, d_out, cuda_stream);
+  sp.thresh = (0 - m) % m;
+  return run_fill(engine, seed, stream, (u64*)pos, n, rp::D_BOUNDED, sp, d_out, cuda_stream);
+}
+
+rp_status rp_fill_normal(rp_engine engine, uint64_t seed, uint64_t stream, uint64_t* pos, size_t n, double* d_out,
+                         void* cuda_stream) {
+  rp::SampArgs sp{};
+  return run_fill(engine, seed, stream, (u64*)pos, n, rp::D_NORMAL, sp, d_out, cuda_stream);
+}
+
+rp_status rp_fill_exp(rp_engine engine, uint64_t seed, uint64_t stream, uint64_t* pos, size_t n, double* d_out,
+                      void* cuda_stream) {
+  rp::SampArgs sp{};
+  return run_fill(engine, seed, stream, (u64*)pos, n, rp::D_EXP, sp, d_out, cuda_stream);
+}
+
+rp_status rp_fill_gamma(rp_engine, uint64_t, uint64_t, uint64_t*, size_t, double, double*, void*) {
+  return fail(RP_ERR_PARAM, "gamma fill not built yet");
+}
+
+rp_status rp_fill_beta(rp_engine, uint64_t, uint64_t, uint64_t*, size_t, double, double, double*, void*) {
+  return fail(RP_ERR_PARAM, "beta fill not built yet");
+}
+
+rp_status rp_seed_state(rp_engine engine, uint64_t seed, uint64_t stream, uint64_t* words, int* nw) {
+  if (!words || !nw) return fail(RP_ERR_NULL, "words/nw is NULL");
+  u64 s[4] = {0, 0, 0, 0};
+  rp_status st = seed_state(engine, seed, stream, s);
+  if (st) return st;
+  memcpy(words, s, sizeof(s));
+  *nw = engine == RP_PHILOX4X32_10 ? 3 : 4;
+  return RP_OK;
+}
+
+rp_status rp_jump_state(rp_engine engine, uint64_t* words, uint64_t delta_hi, uint64_t delta_lo) {
+  if (!words) return fail(RP_ERR_NULL, "words is NULL");
+  if (engine < 1 || engine > 3) return fail(RP_ERR_ENGINE, "unknown engine id " + std::to_string((int)engine));
+  std::lock_guard<std::mutex> lk(g_mu);
+  u128 d = ((u128)delta_hi << 64) | delta_lo;
+  if (engine == RP_PHILOX4X32_10 && (d & 1)) return fail(RP_ERR_PARAM, "Philox state jumps must be even (two words per block)");
+  jump_state(engine, (u64*)words, d);
+  return RP_OK;
+}
+
+rp_status rp_ziggurat_tables(int which, uint64_t* k, double* w, double* f, double* R) {
+  if (!k || !w || !f || !R) return fail(RP_ERR_NULL, "NULL table pointer");
+  if (which != 0 && which != 1) return fail(RP_ERR_PARAM, "which must be 0 (normal) or 1 (exponential)");
+  const unsigned long long* K = which ? RP_ZIG_E_K : RP_ZIG_N_K;
+  const double* W = which ? RP_ZIG_E_W : RP_ZIG_N_W;
+  const double* F = which ? RP_ZIG_E_F : RP_ZIG_N_F;
+  for (int i = 0; i < 256; ++i) { k[i] = K[i]; w[i] = W[i]; f[i] = F[i]; }
+  *R = which ? RP_ZIG_E_R : RP_ZIG_N_R;
+  return RP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,74 @@
+// Internal interface between the host side (rp_host.cpp) and the kernels
+// (rp_kernels.cu) of librp.  Not part of the public ABI.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+
+namespace rp {
+
+enum Dist : int { D_U64 = 0, D_UNIFORM = 1, D_BOUNDED = 2, D_NORMAL = 3, D_EXP = 4, D_GAMMA = 5, D_BETA = 6 };
+
+// Device error bits (ctrl->err)
+enum : unsigned {
+  E_TIMEOUT = 1u,     // a bounded spin-wait gave up
+  E_LANDING = 2u,     // a segment walk jumped over the next sync point
+  E_OVERFLOW = 4u,    // a candidate needed words beyond the tile halo
+  E_NOSYNC = 8u,      // no tile-start sync point within the search window
+};
+
+// Per-launch control block in device memory (scratch).
+struct Ctrl {
+  unsigned long long done_tile;   // index of the tile that produced output n-1 (init: ~0)
+  unsigned long long total;       // outputs produced when the launch ran out of tiles
+  unsigned long long next_pos;    // absolute stream position after the last output
+  unsigned long long last_tile;   // last tile whose exit position was recorded
+  unsigned int err;               // E_* bits
+  unsigned int pad;
+  unsigned long long err_info;
+};
+
+// Engine description for one launch.  All word offsets are relative to the
+// launch's first word (the caller's *pos).
+struct EngineArgs {
+  int engine;                   // 1 xoshiro, 2 pcg, 3 philox
+  unsigned long long s[4];      // xoshiro: state at the first word; pcg: state hi, lo, inc hi, lo;
+                                // philox: counter lo, hi (seeded), key
+  unsigned long long word0;     // philox: index of the first word relative to the seeded counter
+  // xoshiro: nibble tables (64 chunks x 16 entries x 32 B) of T^(2^j), j = 0..63, and of T^stride
+  const void* gf2_pow;
+  const void* gf2_stride;
+  // pcg: affine powers (A_j, G_j) for 2^j steps, j = 0..63, as {A hi, A lo, G hi, G lo}
+  const unsigned long long* pcg_pow;
+  unsigned long long pcg_stride[4];   // (A, G) for the stride
+  unsigned long long stride;          // words between a thread's chunks in consecutive tiles
+};
+
+struct SampArgs {
+  unsigned long long m;       // bounded: modulus (0 = full range)
+  unsigned long long thresh;  // bounded: 2^64 mod m
+  double alpha_d, alpha_c;    // gamma: Marsaglia-Tsang d and c for shape alpha (or alpha+1)
+  double alpha;               // gamma: shape
+  double b_d, b_c, b_alpha;   // beta: second gamma
+};
+
+struct FillArgs {
+  EngineArgs eng;
+  SampArgs sp;
+  int dist;
+  unsigned long long n;          // outputs wanted in this launch
+  unsigned long long n_tiles;    // tiles available in this launch
+  void* out;
+  unsigned long long* tile_status;  // n_tiles words (zeroed)
+  Ctrl* ctrl;
+};
+
+// Kernel launcher (rp_kernels.cu).  Returns a cudaError_t value.
+int launch_fill(const FillArgs& a, int grid, void* stream);
+// Tile geometry and resources of a (engine, dist) kernel.
+struct TileGeom { int nt, c, tile_words, smem_bytes; };
+TileGeom tile_geom(int engine, int dist);
+int occupancy_blocks(int engine, int dist);   // resident CTAs per SM
+// One-time upload of ziggurat tables into device constant/global memory.
+int upload_tables();
+
+}  // namespace rp

@@ -1,0 +1,86 @@
+"""C-ABI checks that need no GPU: the library loads, exports every symbol
+that include/rp.h declares, and its host-side logic (seeding, jumps, tables,
+argument validation) agrees with the oracle.  No compute call reaches CUDA."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def rp():
+    import paper_2605_05099_gb300 as rp
+    rp.lib()
+    return rp
+
+
+def _declared_symbols():
+    hdr = open(os.path.join(ROOT, "include", "rp.h")).read()
+    return sorted(set(re.findall(r"\b(rp_[a-z0-9_]+)\s*\(", hdr)))
+
+
+def test_exports_every_declared_symbol(rp):
+    syms = _declared_symbols()
+    assert len(syms) >= 12
+    L = rp.lib()
+    for s in syms:
+        assert hasattr(L, s), s
+
+
+@pytest.mark.parametrize("engine", ["xoshiro256pp", "pcg64dxsm", "philox4x32_10"])
+def test_seed_state_matches_oracle(rp, orc, engine):
+    rng = np.random.default_rng(5)
+    for seed in [0, 1, 7, 99, 2024, 12345, 2 ** 40 + 3, 2 ** 64 - 1] + [int(x) for x in rng.integers(0, 2 ** 62, 20)]:
+        for stream in [None, 0, 1, 2 ** 33]:
+            g = orc.gen(engine, seed, stream)
+            w = rp.rp_seed_state(engine, seed, rp.NO_STREAM if stream is None else stream)
+            assert w == orc.state_words(g)[: len(w)], (engine, seed, stream)
+
+
+def test_jump_state_matches_oracle(rp, orc):
+    rng = np.random.default_rng(6)
+    s0 = rp.rp_seed_state("xoshiro256pp", 99)
+    for n in [1, 2, 1000, 2 ** 64 - 1, 2 ** 128 - 5] + [int(x) for x in rng.integers(0, 2 ** 62, 5)]:
+        assert rp.rp_jump_state("xoshiro256pp", s0, n) == orc.xoshiro_jump(s0, n, "matrix" if n < 2 ** 70 else "poly")
+    p0 = rp.rp_seed_state("pcg64dxsm", 5)
+    for n in [1, 3, 2 ** 64 + 17, int(rng.integers(0, 2 ** 62))]:
+        assert rp.rp_jump_state("pcg64dxsm", p0, n) == orc.pcg_advance(p0, n)
+    ph = rp.rp_seed_state("philox4x32_10", 3)
+    j = rp.rp_jump_state("philox4x32_10", ph, 2 ** 65 + 10)
+    c0, c1 = ph[0] | ph[1] << 64, j[0] | j[1] << 64
+    assert c1 - c0 == 2 ** 64 + 5 and j[2] == ph[2]
+
+
+def test_ziggurat_tables_match_oracle(rp, orc):
+    for which in (0, 1):
+        k, w, f, R = rp.rp_ziggurat_tables(which)
+        ok, ow, of, oR = orc.zig_table(which)
+        assert [int(x) for x in ok] == k
+        assert list(ow) == w and list(of) == f and oR == R
+
+
+def test_argument_errors(rp):
+    L = rp.lib()
+    pos = ctypes.c_uint64(0)
+    dummy = ctypes.c_void_p(0x1000)
+    # null pos, null out with n > 0, bad engine, misaligned out, bad params
+    assert L.rp_fill_u64(1, 1, rp.NO_STREAM, None, 10, dummy, None) == -1
+    assert L.rp_fill_u64(1, 1, rp.NO_STREAM, ctypes.byref(pos), 10, None, None) == -1
+    assert L.rp_fill_normal(9, 1, rp.NO_STREAM, ctypes.byref(pos), 10, dummy, None) == -3
+    assert "engine" in rp.rp_last_error()
+    assert L.rp_fill_exp(1, 1, rp.NO_STREAM, ctypes.byref(pos), 10, ctypes.c_void_p(0x1004), None) == -2
+    assert L.rp_fill_gamma(1, 1, rp.NO_STREAM, ctypes.byref(pos), 10, 0.0, dummy, None) == -2
+    assert L.rp_fill_gamma(1, 1, rp.NO_STREAM, ctypes.byref(pos), 10, float("nan"), dummy, None) == -2
+    assert L.rp_fill_beta(1, 1, rp.NO_STREAM, ctypes.byref(pos), 10, 1.0, -2.0, dummy, None) == -2
+    assert L.rp_seed_state(1, 1, 0, None, None) == -1
+    assert L.rp_jump_state(3, (ctypes.c_uint64 * 4)(), 0, 3) == -2  # odd Philox state jump
+    # n = 0 is a no-op that leaves pos alone (no device work)
+    pos = ctypes.c_uint64(77)
+    for fn in (L.rp_fill_u64, L.rp_fill_uniform, L.rp_fill_normal, L.rp_fill_exp):
+        assert fn(1, 1, rp.NO_STREAM, ctypes.byref(pos), 0, None, None) == 0
+    assert pos.value == 77
+    assert rp.rp_version().startswith("rp ")

@@ -1,0 +1,122 @@
+"""GPU parity: every fill through the C ABI against the oracle, element by
+element, bit-exact (words, uniforms, integers and ziggurat values; accept
+decisions are exact), plus the consumed-word count.  Sizes span several
+tiles (8192 words each) with ragged tails; edge cases cover n = 1, odd and
+large start positions, continuation across calls and the bounded moduli of
+the single-stream workload."""
+import numpy as np
+import pytest
+import torch
+
+from gpu_util import first_mismatch, gpu_fill, oracle_fill, same_bits
+
+pytestmark = pytest.mark.gpu
+
+ENGINES = ["xoshiro256pp", "pcg64dxsm", "philox4x32_10"]
+DISTS = [("u64", ()), ("uniform", ()), ("normal", ()), ("exp", ()), ("bounded", (6,)),
+         ("bounded", (1_000_000_007,)), ("bounded", (2 ** 63 + 1,))]
+SIZES = [1, 2, 63, 8191, 8192, 8193, 3 * 8192 + 17, 100_003]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+@pytest.mark.parametrize("engine", ENGINES)
+@pytest.mark.parametrize("dist,params", DISTS, ids=lambda x: str(x))
+def test_parity_sizes(engine, dist, params):
+    for n in SIZES:
+        g, gpos = gpu_fill(dist, engine, 2024, None, 0, n, params)
+        o, opos = oracle_fill(dist, engine, 2024, None, 0, n, params)
+        assert same_bits(g, o), (engine, dist, params, n, first_mismatch(g, o))
+        assert gpos == opos, (engine, dist, n, gpos, opos)
+
+
+@pytest.mark.parametrize("engine", ENGINES)
+@pytest.mark.parametrize("dist,params", [("normal", ()), ("exp", ()), ("uniform", ()), ("bounded", (2 ** 63 + 1,))],
+                         ids=lambda x: str(x))
+def test_parity_positions_and_streams(engine, dist, params):
+    for pos, stream in [(1, None), (3, 5), (8191, None), (2 ** 40 + 3, 1), (2 ** 62 + 1, None)]:
+        n = 20_000
+        g, gpos = gpu_fill(dist, engine, 7, stream, pos, n, params)
+        o, opos = oracle_fill(dist, engine, 7, stream, pos, n, params)
+        assert same_bits(g, o), (engine, dist, pos, stream, first_mismatch(g, o))
+        assert gpos == opos
+
+
+@pytest.mark.parametrize("engine", ENGINES)
+def test_continuation_two_fills_equal_one(engine):
+    """A fill consumes exactly the words its variates used (stream
+    continuation): normal(n1) then normal(n2) == normal(n1 + n2)."""
+    for dist in ("normal", "exp"):
+        a, p1 = gpu_fill(dist, engine, 11, None, 0, 12_345)
+        b, p2 = gpu_fill(dist, engine, 11, None, p1, 54_321)
+        c, p3 = gpu_fill(dist, engine, 11, None, 0, 12_345 + 54_321)
+        assert same_bits(np.concatenate([a, b]), c) and p2 == p3
+
+
+def test_config1_words_then_uniforms():
+    """xoshiro256++ seed 12345: 2^20 raw words, then 2^20 uniforms continuing
+    the stream (words 2^20 .. 2^21 - 1), bit-exact."""
+    n = 1 << 20
+    g1, p1 = gpu_fill("u64", "xoshiro256pp", 12345, None, 0, n)
+    g2, p2 = gpu_fill("uniform", "xoshiro256pp", 12345, None, p1, n)
+    o1, q1 = oracle_fill("u64", "xoshiro256pp", 12345, None, 0, n)
+    o2, q2 = oracle_fill("uniform", "xoshiro256pp", 12345, None, q1, n)
+    assert p1 == q1 == n and p2 == q2 == 2 * n
+    assert same_bits(g1, o1) and same_bits(g2, o2)
+
+
+@pytest.mark.parametrize("engine", ENGINES)
+def test_full_size_normal_exp(engine):
+    """Single-stream workload size (n = 2^28) for the ziggurat samplers on
+    xoshiro256++, and a 2^24 prefix-sized fill for the other engines:
+    whole-array bit compare and consumed words."""
+    n = (1 << 28) if engine == "xoshiro256pp" else (1 << 24)
+    for dist in ("normal", "exp"):
+        g, gpos = gpu_fill(dist, engine, 2024, None, 0, n)
+        o, opos = oracle_fill(dist, engine, 2024, None, 0, n)
+        assert gpos == opos
+        assert same_bits(g, o), first_mismatch(g, o)
+        del g, o
+
+
+def test_full_size_bounded_half_range():
+    n = 1 << 26
+    g, gpos = gpu_fill("bounded", "xoshiro256pp", 2024, None, 0, n, (2 ** 63 + 1,))
+    o, opos = oracle_fill("bounded", "xoshiro256pp", 2024, None, 0, n, (2 ** 63 + 1,))
+    assert gpos == opos and same_bits(g, o)
+
+
+def test_bounded_edge_moduli():
+    for m in (1, 2, 3, 2 ** 32 + 1, 2 ** 64 - 1, 0):
+        g, gpos = gpu_fill("bounded", "philox4x32_10", 5, None, 0, 30_000, (m,))
+        o, opos = oracle_fill("bounded", "philox4x32_10", 5, None, 0, 30_000, (m,))
+        assert same_bits(g, o) and gpos == opos, m
+
+
+def test_philox_bijection_matches_curand():
+    """Pin of the oracle's (and library's) Philox4x32-10 bijection against
+    cuRAND's device API, run as a black box: key = seed, counter =
+    (0, 0, subsequence) + i."""
+    import ctypes
+    import os
+    import subprocess
+    import oracle
+    here = os.path.join(os.path.dirname(os.path.abspath(__file__)), "gpu_helpers")
+    so = os.path.join(here, "libcurand_philox.so")
+    subprocess.check_call(["nvcc", "-gencode", "arch=compute_103a,code=sm_103a", "-O2", "-shared",
+                           "-Xcompiler", "-fPIC", "-o", so, os.path.join(here, "curand_philox.cu")])
+    L = ctypes.CDLL(so)
+    L.curand_philox_blocks.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int, ctypes.c_void_p]
+    for seed, subseq in [(0, 0), (2024, 0), (2 ** 64 - 1, 2 ** 64 - 1), (0x123456789abcdef, 77)]:
+        nb = 4096
+        buf = np.empty(4 * nb, np.uint32)
+        assert L.curand_philox_blocks(seed, subseq, nb, buf.ctypes.data) == 0
+        key = [seed & 0xFFFFFFFF, seed >> 32]
+        for i in range(0, nb, 97):
+            c = (subseq << 64) + i
+            ctr = [(c >> (32 * j)) & 0xFFFFFFFF for j in range(4)]
+            assert oracle.philox(ctr, key) == [int(x) for x in buf[4 * i: 4 * i + 4]], (seed, subseq, i)
