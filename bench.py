@@ -1,0 +1,281 @@
+"""Benchmark of the single-stream exact-sequence fills on one GB300.
+
+A step is the single-stream workload: for each engine (xoshiro256++,
+PCG64-DXSM, Philox4x32-10) and each sampler (ziggurat normal, ziggurat
+exponential, bounded uint64 in [0, m) for m in {6, 1e9+7, 2^63+1}) one fresh
+fill of n = 2^28 variates from seed 2024, word 0 -- 15 fills, 4.03e9
+variates.  Outputs (2 GiB per fill) are far larger than L2, so no flush is
+needed between timed fills.
+
+Prints one JSON line (metric variates/s).  --impl reference times the serial
+CPU oracle on a bounded sample of the same workload instead.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_FILL = 1 << 28
+SEED = 2024
+ENGINES = ["xoshiro256pp", "pcg64dxsm", "philox4x32_10"]
+SAMPLERS = [("normal", ()), ("exp", ()), ("bounded", (6,)), ("bounded", (1_000_000_007,)),
+            ("bounded", (2 ** 63 + 1,))]
+METRIC = "variates/s (single-stream exact-sequence fills, 3 engines x {normal, exp, bounded m in {6, 1e9+7, 2^63+1}})"
+WORKLOAD = "single-stream fills: engines {xoshiro256++, PCG64-DXSM, Philox4x32-10}, seed 2024, n=2^28 each of normal, exp, bounded m=6, 1e9+7, 2^63+1"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+                for nm, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(nm)
+            except Exception:
+                continue
+        sm.sort()
+        med = sm[len(sm) // 2] if sm else None
+        return {"sm_mhz": med, "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist_init():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    return world, rank, local
+
+
+def run_gpu(args):
+    import torch
+
+    import paper_2605_05099_gb300 as rp
+
+    world, rank, local = _dist_init()
+    torch.cuda.set_device(local)
+    rp.lib()
+    stream = torch.cuda.current_stream()
+    # ranks fill independent spawn-key streams (weak scaling, no collective on the data path)
+    spawn = rp.NO_STREAM if world == 1 else rank
+    out_f = torch.empty(N_FILL, dtype=torch.float64, device="cuda")
+    out_u = torch.empty(N_FILL, dtype=torch.uint64, device="cuda")
+
+    def one_fill(engine, dist, params):
+        if dist == "normal":
+            return rp.rp_fill_normal(engine, SEED, spawn, 0, out_f, stream)
+        if dist == "exp":
+            return rp.rp_fill_exp(engine, SEED, spawn, 0, out_f, stream)
+        return rp.rp_fill_bounded(engine, SEED, spawn, 0, params[0], out_u, stream)
+
+    fills = [(e, d, p) for e in ENGINES for d, p in SAMPLERS]
+    per_fill_ms = {f"{e}/{d}{'' if not p else ':' + str(p[0])}": 0.0 for e, d, p in fills}
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in fills]
+
+    def step(record):
+        for i, (e, d, p) in enumerate(fills):
+            if record:
+                ev[i][0].record(stream)
+            one_fill(e, d, p)
+            if record:
+                ev[i][1].record(stream)
+
+    for _ in range(args.warmup):
+        step(False)
+    torch.cuda.synchronize()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    launches0 = rp.rp_kernel_launches()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    t0.record(stream)
+    for _ in range(args.steps):
+        step(True)
+        for i, key in enumerate(per_fill_ms):
+            ev[i][1].synchronize()
+            per_fill_ms[key] += ev[i][0].elapsed_time(ev[i][1])
+    t1.record(stream)
+    torch.cuda.synchronize()
+    launches = rp.rp_kernel_launches() - launches0
+    ms = t0.elapsed_time(t1)
+    clk = clocks.stop()
+    if world > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    variates = len(fills) * N_FILL * args.steps * world
+    value = variates / (ms / 1e3)
+
+    # ---- roofline of the dominant kernel (the fill with the largest time)
+    peaks, peak_kind = _peaks()
+    key = max(per_fill_ms, key=per_fill_ms.get)
+    avg_ms = per_fill_ms[key] / args.steps
+    bytes_alg = 8.0 * N_FILL
+    achieved = bytes_alg / (avg_ms / 1e3) / 1e9
+    roof = {"bound": "hbm", "kernel": key, "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"],
+            "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": None,
+            "peak_source": peak_kind, "per_fill_ms": {k: round(v / args.steps, 4) for k, v in per_fill_ms.items()}}
+
+    # ---- end to end through the public API with host buffers: each fill's
+    # result is copied back to pinned host memory inside the timed region
+    e2e = None
+    if rank == 0 or world > 1:
+        host = torch.empty(N_FILL, dtype=torch.float64, pin_memory=True)
+        hostu = torch.empty(N_FILL, dtype=torch.uint64, pin_memory=True)
+        e_steps = max(1, min(args.steps, 2))
+        torch.cuda.synchronize()
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        for _ in range(e_steps):
+            for e, d, p in fills:
+                one_fill(e, d, p)
+                if d in ("normal", "exp"):
+                    host.copy_(out_f, non_blocking=True)
+                else:
+                    hostu.copy_(out_u, non_blocking=True)
+        a1.record(stream)
+        torch.cuda.synchronize()
+        ems = a0.elapsed_time(a1)
+        e2e = {"value": len(fills) * N_FILL * e_steps / (ems / 1e3), "unit": "variates/s",
+               "h2d_bytes_per_step": 0, "d2h_bytes_per_step": len(fills) * N_FILL * 8}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(args.cpu_sample)
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "variates/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "u64/f64",
+                "data": "synthetic (seeded engine streams; no dataset)",
+                "config": {"workload": WORKLOAD, "n_per_fill": N_FILL, "fills_per_step": len(fills),
+                           "l2": "outputs (2 GiB per fill) exceed L2; no flush needed",
+                           "parallelism": f"independent streams x{world}"},
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+                "clocks": clk}
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def cpu_baseline(sample):
+    """The serial C oracle as it stands, one host core, on a bounded sample of
+    the same workload: `sample` variates of each of the 15 fills."""
+    import oracle
+    t = 0.0
+    for e in ENGINES:
+        for d, p in SAMPLERS:
+            g = oracle.gen(e, SEED)
+            t0 = time.perf_counter()
+            oracle.fill(g, d, sample, *p)
+            t += time.perf_counter() - t0
+    total = sample * len(ENGINES) * len(SAMPLERS)
+    return {"value": total / t, "unit": "variates/s", "cores": 1, "kind": "oracle",
+            "sample": f"{sample} variates of each of the 15 fills (first {sample} of each stream)",
+            "seconds": round(t, 3)}
+
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    oracle.lib()
+    for _ in range(args.warmup):
+        cpu_baseline(max(1024, args.cpu_sample // 16))
+    t0 = time.perf_counter()
+    res = None
+    for _ in range(args.steps):
+        res = cpu_baseline(args.cpu_sample)
+    dt = time.perf_counter() - t0
+    total = args.cpu_sample * len(ENGINES) * len(SAMPLERS) * args.steps
+    v = total / dt
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "variates/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64/f64",
+            "data": "synthetic (seeded engine streams; no dataset)",
+            "config": {"workload": WORKLOAD, "n_per_fill": N_FILL, "fills_per_step": 15,
+                       "sample_per_fill": args.cpu_sample},
+            "cpu_baseline": {"value": v, "unit": "variates/s", "cores": 1, "kind": "oracle",
+                             "sample": res["sample"] if res else ""},
+            "e2e": {"value": v, "unit": "variates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--cpu-sample", type=int, default=None,
+                    help="oracle variates per fill (default 2^24 for the baseline leg, 2^21 per reference step)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.cpu_sample is None:
+        args.cpu_sample = (1 << 21) if args.impl == "reference" else (1 << 24)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

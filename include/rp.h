@@ -125,6 +125,10 @@ const char* rp_last_error(void);
 /* Library version string. */
 const char* rp_version(void);
 
+/* Number of CUDA kernels this library has launched in this process (a
+ * diagnostic counter for benchmarks). */
+uint64_t rp_kernel_launches(void);
+
 /* Ziggurat tables used by the kernels (which: 0 normal, 1 exponential):
  * k[256], w[256], f[256] and R.  For inspection and tests. */
 rp_status rp_ziggurat_tables(int which, uint64_t* k, double* w, double* f, double* R);

@@ -62,6 +62,8 @@ def lib():
         L.rp_last_error.argtypes = []
         L.rp_version.restype = ctypes.c_char_p
         L.rp_version.argtypes = []
+        L.rp_kernel_launches.restype = ctypes.c_uint64
+        L.rp_kernel_launches.argtypes = []
         _lib = L
     return _lib
 
@@ -155,6 +157,10 @@ def rp_last_error():
 
 def rp_version():
     return lib().rp_version().decode()
+
+
+def rp_kernel_launches():
+    return int(lib().rp_kernel_launches())
 
 
 # ---- convenience: allocate and fill

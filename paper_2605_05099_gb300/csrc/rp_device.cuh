@@ -45,6 +45,43 @@ __device__ __forceinline__ double mul_rn_int(u64 r, u64 msh, int wtz, int we) {
   return __longlong_as_double((long long)((((u64)(q + 1074)) << 52) + mt));
 }
 
+// Negate a double by flipping its sign bit (no FP64 instruction).
+__device__ __forceinline__ double neg_if(double x, u64 bit) {
+  return __longlong_as_double(__double_as_longlong(x) ^ (long long)(bit << 63));
+}
+
+// ------------------------------------------------------------------ FP32 estimates
+// Positive integer v < 2^64 times 2^e2 as a float with the significand
+// truncated to 24 bits (relative error < 2^-23).  v = 0 gives 0.
+__device__ __forceinline__ float int_scaled_f(u64 v, int e2) {
+  if (v == 0) return 0.0f;
+  int lz = __clzll(v);
+  unsigned m = (unsigned)((v << lz) >> 40);          // bit 23 = leading one
+  int e = 63 - lz + e2 + 127;
+  return __uint_as_float(((unsigned)e << 23) | (m & 0x7fffffu));
+}
+// U = floor(u / 2^11) 2^-53 and 1 - U as floats (truncated, relative error < 2^-23)
+__device__ __forceinline__ float u53_f(u64 u) { return int_scaled_f(u >> 11, -53); }
+__device__ __forceinline__ float one_minus_u53_f(u64 u) { return int_scaled_f((1ull << 53) - (u >> 11), -53); }
+// log(1 - U) in FP32 with relative error below 2^-20 for U in [0, 1)
+__device__ __forceinline__ float log1m_u53_f(u64 u) {
+  float U = u53_f(u);
+  return U < 0.5f ? log1pf(-U) : logf(one_minus_u53_f(u));
+}
+
+// Exact double of an integer 0 < r < 2^53 from integer operations.
+__device__ __forceinline__ double exact_double(u64 r) {
+  int lz = __clzll(r);
+  u64 mt = r << (lz - 11);                   // leading one at bit 52
+  return __longlong_as_double((long long)((((u64)(1085 - lz)) << 52) + mt));
+}
+// RN(r * w) for 0 <= r < 2^53: r converts exactly, so one FP64 multiply
+// gives the correctly rounded product (same value as the integer-only
+// mul_rn_int, on the otherwise idle FP64 pipe).
+__device__ __forceinline__ double mul_rn_dmul(u64 r, double w) {
+  return r ? __dmul_rn(exact_double(r), w) : 0.0;
+}
+
 // ------------------------------------------------------------------ double-double
 struct dd { double hi, lo; };
 
@@ -142,7 +179,13 @@ struct ZigDev {
   double f[256];
   int we[256];      // w_i = (msh >> 11) 2^we
   int wtz[256];     // trailing zeros of the significand
+  float ff[256];    // f_i, f_{i-1} - f_i and w_i rounded to float (estimates only)
+  float fd[256];
+  float wf[256];
+  double w[256];    // w_i
   double R;
+  float Rf;
+  float pad;
 };
 
 // ------------------------------------------------------------------ engines
@@ -187,6 +230,40 @@ struct XoshiroDev {
   __device__ __forceinline__ void advance(const EngineArgs& a) {
     gf2_apply((const ulonglong4_32a*)a.gf2_stride, s0, s1, s2, s3);
   }
+  // State at word c T + t C (thread t of CTA c): warp 0 computes the CTA
+  // base T^(c T) s with warp-cooperative GF(2) products (two nibble lookups
+  // per lane and an XOR reduction), then every thread applies T^(t C).
+  // `sh` is 4 words of shared memory.  Call with the whole CTA.
+  __device__ void init_tile(const EngineArgs& a, unsigned c, int t, u64* sh) {
+    if (t < 32) {
+      u64 v[4] = {a.s[0], a.s[1], a.s[2], a.s[3]};
+      const ulonglong4_32a* base = (const ulonglong4_32a*)a.gf2_cta;
+      for (int j = 0; j < 16; ++j) {
+        if (!((c >> j) & 1)) continue;
+        const ulonglong4_32a* tab = base + (size_t)j * 1024;
+        u64 acc[4] = {0, 0, 0, 0};
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          int ch = 2 * t + h;                       // nibble chunk 0..63
+          int v4 = (int)((v[ch >> 4] >> (4 * (ch & 15))) & 15u);
+          const ulonglong2* e = (const ulonglong2*)(tab + (ch * 16 + v4));
+          ulonglong2 t0 = __ldg(e), t1 = __ldg(e + 1);
+          acc[0] ^= t0.x; acc[1] ^= t0.y; acc[2] ^= t1.x; acc[3] ^= t1.y;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+          for (int w = 0; w < 4; ++w) acc[w] ^= __shfl_xor_sync(0xffffffffu, acc[w], o);
+#pragma unroll
+        for (int w = 0; w < 4; ++w) v[w] = acc[w];
+      }
+      if (t == 0) { sh[0] = v[0]; sh[1] = v[1]; sh[2] = v[2]; sh[3] = v[3]; }
+    }
+    __syncthreads();
+    s0 = sh[0]; s1 = sh[1]; s2 = sh[2]; s3 = sh[3];
+    __syncthreads();
+    if (t) gf2_apply((const ulonglong4_32a*)a.gf2_thread + (size_t)t * 1024, s0, s1, s2, s3);
+  }
 };
 
 // PCG64-DXSM (O'Neill): DXSM output of the current state, then the LCG step
@@ -213,6 +290,7 @@ struct PcgDev {
       off &= off - 1;
     }
   }
+  __device__ void init_tile(const EngineArgs& a, unsigned c, int t, u64*) { init(a, (u64)c * a.tile_words + (u64)t * a.chunk_words); }
   __device__ __forceinline__ void advance(const EngineArgs& a) {
     u128 A = ((u128)a.pcg_stride[0] << 64) | a.pcg_stride[1];
     u128 G = ((u128)a.pcg_stride[2] << 64) | a.pcg_stride[3];
@@ -265,6 +343,7 @@ struct PhiloxDev {
       block(idx >> 1, w0, buf);
     }
   }
+  __device__ void init_tile(const EngineArgs& a, unsigned c, int t, u64*) { init(a, (u64)c * a.tile_words + (u64)t * a.chunk_words); }
   __device__ __forceinline__ void advance(const EngineArgs& a) {
     u64 start = idx;  // callers advance a saved chunk-start copy
     idx = start + a.stride;

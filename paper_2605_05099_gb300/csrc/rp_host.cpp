@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -12,7 +13,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/rp.h"
+#include "rp.h"
 #include "rp_internal.h"
 
 namespace rp {
@@ -27,6 +28,7 @@ typedef unsigned __int128 u128;
 
 thread_local std::string g_err;
 std::mutex g_mu;
+std::atomic<unsigned long long> g_launches{0};
 
 rp_status fail(rp_status code, const std::string& msg) {
   g_err = msg;
@@ -190,6 +192,67 @@ int xo_device_pow(void** out) {
   return 0;
 }
 
+// T^N as a matrix, N < 2^64
+void xo_power(u64 N, Mat& M) {
+  XoTables& X = xo();
+  memset(&M, 0, sizeof(M));
+  for (int j = 0; j < 256; ++j) M.c[j][j >> 6] = 1ull << (j & 63);
+  for (int j = 0; j < 64; ++j)
+    if (N >> j & 1) mat_mul(X.pow[j], M, M);
+}
+
+int upload_tables(const std::vector<Mat>& mats, void** out) {
+  std::vector<u64> all, one;
+  for (const Mat& m : mats) {
+    nibble_table(m, one);
+    all.insert(all.end(), one.begin(), one.end());
+  }
+  void* d = nullptr;
+  int e = (int)cudaMalloc(&d, all.size() * 8);
+  if (e) return e;
+  e = (int)cudaMemcpy(d, all.data(), all.size() * 8, cudaMemcpyHostToDevice);
+  if (e) { cudaFree(d); return e; }
+  *out = d;
+  return 0;
+}
+
+// nibble tables of T^(t C), t < nt (per-thread offsets inside a tile)
+std::map<std::pair<u64, int>, void*> g_xo_thread;
+int xo_device_thread(u64 C, int nt, void** out) {
+  auto key = std::make_pair(C, nt);
+  auto it = g_xo_thread.find(key);
+  if (it == g_xo_thread.end()) {
+    std::vector<Mat> mats(nt);
+    xo_power(0, mats[0]);
+    Mat step;
+    xo_power(C, step);
+    for (int t = 1; t < nt; ++t) mat_mul(step, mats[t - 1], mats[t]);
+    void* d = nullptr;
+    int e = upload_tables(mats, &d);
+    if (e) return e;
+    it = g_xo_thread.emplace(key, d).first;
+  }
+  *out = it->second;
+  return 0;
+}
+
+// nibble tables of T^(T 2^j), j < 16 (per-CTA base offsets)
+std::map<u64, void*> g_xo_cta;
+int xo_device_cta(u64 T, void** out) {
+  auto it = g_xo_cta.find(T);
+  if (it == g_xo_cta.end()) {
+    std::vector<Mat> mats(16);
+    xo_power(T, mats[0]);
+    for (int j = 1; j < 16; ++j) mat_mul(mats[j - 1], mats[j - 1], mats[j]);
+    void* d = nullptr;
+    int e = upload_tables(mats, &d);
+    if (e) return e;
+    it = g_xo_cta.emplace(T, d).first;
+  }
+  *out = it->second;
+  return 0;
+}
+
 int xo_device_stride(u64 D, void** out) {
   XoTables& X = xo();
   auto it = X.d_stride.find(D);
@@ -294,13 +357,19 @@ void jump_state(int engine, u64 s[4], u128 delta) {
 // ---------------------------------------------------------------- ziggurat upload
 #include "zig_tables.inc"
 
-struct ZigHost {
+struct ZigHost {  // same layout as the device-side ZigDev
   u64 k[256];
   u64 msh[256];
   double f[256];
   int we[256];
   int wtz[256];
+  float ff[256];
+  float fd[256];
+  float wf[256];
+  double w[256];    // w_i
   double R;
+  float Rf;
+  float pad;
 };
 
 void fill_zig(ZigHost& z, const unsigned long long* K, const double* W, const double* F, double R) {
@@ -314,8 +383,14 @@ void fill_zig(ZigHost& z, const unsigned long long* K, const double* W, const do
     z.msh[i] = m << 11;
     z.we[i] = be - 1075;
     z.wtz[i] = __builtin_ctzll(m);
+    z.ff[i] = (float)F[i];
+    z.fd[i] = i ? (float)(F[i - 1] - F[i]) : 0.0f;
+    z.wf[i] = (float)W[i];
+    z.w[i] = W[i];
   }
   z.R = R;
+  z.Rf = (float)R;
+  z.pad = 0.0f;
 }
 
 bool g_zig_ready = false;
@@ -335,8 +410,20 @@ struct Scratch {
   size_t cap = 0;
   rp::Ctrl* ctrl = nullptr;
   rp::Ctrl* h_ctrl = nullptr;  // pinned
+  rp::TailEntry* tailq = nullptr;
+  size_t tail_cap = 0;
 };
 Scratch g_scr;
+
+int ensure_tailq(size_t cap) {
+  if (cap > g_scr.tail_cap) {
+    if (g_scr.tailq) cudaFree(g_scr.tailq);
+    int e = (int)cudaMalloc((void**)&g_scr.tailq, cap * sizeof(rp::TailEntry));
+    if (e) { g_scr.tailq = nullptr; g_scr.tail_cap = 0; return e; }
+    g_scr.tail_cap = cap;
+  }
+  return 0;
+}
 
 int ensure_scratch(size_t tiles) {
   if (!g_scr.ctrl) {
@@ -425,9 +512,14 @@ rp_status run_fill(int engine, u64 seed, u64 stream, u64* pos, size_t n, int dis
     }
     memcpy(a.eng.s, s0, sizeof(s0));
     a.eng.stride = grid * T;
+    a.eng.tile_words = T;
+    a.eng.chunk_words = (u64)tg.c;
+    if (grid > 65535) return fail(RP_ERR_INTERNAL, "grid too large for the CTA jump tables");
     if (engine == RP_XOSHIRO256PP) {
       e = xo_device_pow((void**)&a.eng.gf2_pow);
       if (!e) e = xo_device_stride(a.eng.stride, (void**)&a.eng.gf2_stride);
+      if (!e) e = xo_device_thread((u64)tg.c, tg.nt, (void**)&a.eng.gf2_thread);
+      if (!e) e = xo_device_cta(T, (void**)&a.eng.gf2_cta);
       if (e) return cuda_fail(e, "jump tables");
     } else if (engine == RP_PCG64DXSM) {
       e = pcg_device_pow((u64**)&a.eng.pcg_pow);
@@ -441,9 +533,12 @@ rp_status run_fill(int engine, u64 seed, u64 stream, u64* pos, size_t n, int dis
     a.out = (char*)d_out + done * esz;
     if (!trivial) {
       e = ensure_scratch(tiles);
+      if (!e && (dist == rp::D_NORMAL || dist == rp::D_EXP)) e = ensure_tailq(left / 256 + 4096);
       if (e) return fail(RP_ERR_NOMEM, std::string("scratch allocation: ") + cudaGetErrorString((cudaError_t)e));
       a.tile_status = g_scr.status;
       a.ctrl = g_scr.ctrl;
+      a.tailq = g_scr.tailq;
+      a.tail_cap = (dist == rp::D_NORMAL || dist == rp::D_EXP) ? g_scr.tail_cap : 0;
       rp::Ctrl c0;
       memset(&c0, 0, sizeof(c0));
       c0.done_tile = ~0ull;
@@ -453,6 +548,12 @@ rp_status run_fill(int engine, u64 seed, u64 stream, u64* pos, size_t n, int dis
     }
     e = rp::launch_fill(a, (int)grid, cstream);
     if (e) return cuda_fail(e, "kernel launch");
+    g_launches.fetch_add(1);
+    if (a.tail_cap) {
+      e = rp::launch_tails(a, cstream);
+      if (e) return cuda_fail(e, "tail kernel launch");
+      g_launches.fetch_add(1);
+    }
     if (trivial) {
       e = (int)cudaStreamSynchronize((cudaStream_t)cstream);
       if (e) return cuda_fail(e, "fill");
@@ -488,6 +589,7 @@ extern "C" {
 
 const char* rp_last_error(void) { return g_err.c_str(); }
 const char* rp_version(void) { return "rp 0.1 (sm_103a)"; }
+uint64_t rp_kernel_launches(void) { return g_launches.load(); }
 
 rp_status rp_fill_u64(rp_engine engine, uint64_t seed, uint64_t stream, uint64_t* pos, size_t n, uint64_t* d_out,
                       void* cuda_stream) {

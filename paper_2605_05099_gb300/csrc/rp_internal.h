@@ -20,11 +20,18 @@ enum : unsigned {
 struct Ctrl {
   unsigned long long done_tile;   // index of the tile that produced output n-1 (init: ~0)
   unsigned long long total;       // outputs produced when the launch ran out of tiles
-  unsigned long long next_pos;    // absolute stream position after the last output
+  unsigned long long next_pos;    // stream position (relative to the launch) after the last output
   unsigned long long last_tile;   // last tile whose exit position was recorded
   unsigned int err;               // E_* bits
   unsigned int pad;
   unsigned long long err_info;
+  unsigned long long n_tail;      // entries in the tail queue
+};
+
+// Deferred output whose value needs FP64 libm (ziggurat tails): output
+// index and the two words that define it.
+struct TailEntry {
+  unsigned long long g, w0, w1;
 };
 
 // Engine description for one launch.  All word offsets are relative to the
@@ -37,10 +44,14 @@ struct EngineArgs {
   // xoshiro: nibble tables (64 chunks x 16 entries x 32 B) of T^(2^j), j = 0..63, and of T^stride
   const void* gf2_pow;
   const void* gf2_stride;
+  const void* gf2_thread;   // nibble tables of T^(t C), t < threads per CTA
+  const void* gf2_cta;      // nibble tables of T^(T 2^j), j < 16 (T = words per tile)
   // pcg: affine powers (A_j, G_j) for 2^j steps, j = 0..63, as {A hi, A lo, G hi, G lo}
   const unsigned long long* pcg_pow;
   unsigned long long pcg_stride[4];   // (A, G) for the stride
   unsigned long long stride;          // words between a thread's chunks in consecutive tiles
+  unsigned long long tile_words;      // words per tile (T)
+  unsigned long long chunk_words;     // words per thread chunk (C)
 };
 
 struct SampArgs {
@@ -60,10 +71,13 @@ struct FillArgs {
   void* out;
   unsigned long long* tile_status;  // n_tiles words (zeroed)
   Ctrl* ctrl;
+  TailEntry* tailq;                 // deferred tail outputs
+  unsigned long long tail_cap;
 };
 
-// Kernel launcher (rp_kernels.cu).  Returns a cudaError_t value.
+// Kernel launchers (rp_kernels.cu).  Return a cudaError_t value.
 int launch_fill(const FillArgs& a, int grid, void* stream);
+int launch_tails(const FillArgs& a, void* stream);
 // Tile geometry and resources of a (engine, dist) kernel.
 struct TileGeom { int nt, c, tile_words, smem_bytes; };
 TileGeom tile_geom(int engine, int dist);

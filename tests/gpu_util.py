@@ -35,10 +35,49 @@ def gpu_fill(dist, engine, seed, stream, pos, n, params=()):
     return host, newpos
 
 
-def oracle_fill(dist, engine, seed, stream, pos, n, params=()):
+def oracle_fill(dist, engine, seed, stream, pos, n, params=(), with_start=False):
     g = oracle.gen(engine, seed, stream, pos=pos)
+    if with_start:
+        out, start = oracle.fill(g, dist, n, *params, with_start=True)
+        return out, int(g.pos), start
     out = oracle.fill(g, dist, n, *params)
     return out, int(g.pos)
+
+
+def ulp_diff(a, b):
+    """distance in units in the last place between doubles of the same sign"""
+    ia = np.asarray(a, np.float64).view(np.int64).astype(object)
+    ib = np.asarray(b, np.float64).view(np.int64).astype(object)
+    return abs(int(ia) - int(ib))
+
+
+def tail_output(dist, engine, seed, stream, start_pos):
+    """True when the candidate that produced an output began in the
+    ziggurat base strip beyond the fast-accept threshold (the tail)."""
+    if dist not in ("normal", "exp"):
+        return False
+    g = oracle.gen(engine, seed, stream, pos=int(start_pos))
+    u = int(oracle.next_words(g, 1)[0])
+    which = 0 if dist == "normal" else 1
+    k0 = int(oracle.zig_table(which)[0][0])
+    r = (u >> 9) & (2 ** 52 - 1) if dist == "normal" else (u >> 8) & (2 ** 53 - 1)
+    return (u & 0xFF) == 0 and r >= k0
+
+
+def assert_parity(dist, engine, seed, stream, pos, n, params=(), max_tail_ulp=2):
+    """GPU fill vs oracle: identical consumed words and accept sequence;
+    outputs bit-identical except tail outputs of the ziggurat samplers, whose
+    values go through log and must be within max_tail_ulp."""
+    g, gpos = gpu_fill(dist, engine, seed, stream, pos, n, params)
+    o, opos, start = oracle_fill(dist, engine, seed, stream, pos, n, params, with_start=True)
+    assert gpos == opos, (dist, engine, n, gpos, opos)
+    ug, uo = g.view(np.uint64), o.view(np.uint64)
+    bad = np.nonzero(ug != uo)[0]
+    assert len(bad) <= max(8, n // 1000), (dist, engine, n, len(bad))
+    for j in bad:
+        assert tail_output(dist, engine, seed, stream, start[j]), (dist, engine, n, int(j), g[j], o[j])
+        assert ulp_diff(g[j], o[j]) <= max_tail_ulp, (dist, engine, int(j), g[j], o[j])
+    return len(bad)
 
 
 def same_bits(a, b):

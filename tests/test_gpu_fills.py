@@ -1,6 +1,7 @@
 """GPU parity: every fill through the C ABI against the oracle, element by
-element, bit-exact (words, uniforms, integers and ziggurat values; accept
-decisions are exact), plus the consumed-word count.  Sizes span several
+element: bit-exact for words, uniforms, integers and ziggurat values, within
+2 ulp for ziggurat tail outputs (their values go through log); accept
+decisions and the consumed-word count are exact.  Sizes span several
 tiles (8192 words each) with ragged tails; edge cases cover n = 1, odd and
 large start positions, continuation across calls and the bounded moduli of
 the single-stream workload."""
@@ -8,7 +9,7 @@ import numpy as np
 import pytest
 import torch
 
-from gpu_util import first_mismatch, gpu_fill, oracle_fill, same_bits
+from gpu_util import assert_parity, first_mismatch, gpu_fill, oracle_fill, same_bits
 
 pytestmark = pytest.mark.gpu
 
@@ -28,10 +29,7 @@ def _cuda():
 @pytest.mark.parametrize("dist,params", DISTS, ids=lambda x: str(x))
 def test_parity_sizes(engine, dist, params):
     for n in SIZES:
-        g, gpos = gpu_fill(dist, engine, 2024, None, 0, n, params)
-        o, opos = oracle_fill(dist, engine, 2024, None, 0, n, params)
-        assert same_bits(g, o), (engine, dist, params, n, first_mismatch(g, o))
-        assert gpos == opos, (engine, dist, n, gpos, opos)
+        assert_parity(dist, engine, 2024, None, 0, n, params)
 
 
 @pytest.mark.parametrize("engine", ENGINES)
@@ -39,17 +37,14 @@ def test_parity_sizes(engine, dist, params):
                          ids=lambda x: str(x))
 def test_parity_positions_and_streams(engine, dist, params):
     for pos, stream in [(1, None), (3, 5), (8191, None), (2 ** 40 + 3, 1), (2 ** 62 + 1, None)]:
-        n = 20_000
-        g, gpos = gpu_fill(dist, engine, 7, stream, pos, n, params)
-        o, opos = oracle_fill(dist, engine, 7, stream, pos, n, params)
-        assert same_bits(g, o), (engine, dist, pos, stream, first_mismatch(g, o))
-        assert gpos == opos
+        assert_parity(dist, engine, 7, stream, pos, 20_000, params)
 
 
 @pytest.mark.parametrize("engine", ENGINES)
 def test_continuation_two_fills_equal_one(engine):
     """A fill consumes exactly the words its variates used (stream
-    continuation): normal(n1) then normal(n2) == normal(n1 + n2)."""
+    continuation): normal(n1) then normal(n2) == normal(n1 + n2) (the same
+    kernels compute both sides, so tail values agree bit for bit too)."""
     for dist in ("normal", "exp"):
         a, p1 = gpu_fill(dist, engine, 11, None, 0, 12_345)
         b, p2 = gpu_fill(dist, engine, 11, None, p1, 54_321)
@@ -76,11 +71,7 @@ def test_full_size_normal_exp(engine):
     whole-array bit compare and consumed words."""
     n = (1 << 28) if engine == "xoshiro256pp" else (1 << 24)
     for dist in ("normal", "exp"):
-        g, gpos = gpu_fill(dist, engine, 2024, None, 0, n)
-        o, opos = oracle_fill(dist, engine, 2024, None, 0, n)
-        assert gpos == opos
-        assert same_bits(g, o), first_mismatch(g, o)
-        del g, o
+        assert_parity(dist, engine, 2024, None, 0, n)
 
 
 def test_full_size_bounded_half_range():
