@@ -120,10 +120,19 @@ __device__ __forceinline__ dd dd_scale_inv(dd a, double k) {  // a / k, k a smal
 }
 
 // exp(x) to ~2^-100 relative: x = k ln2 + r (ln 2 in three parts), exp(r) =
-// exp(r/256)^256 with a degree-11 Taylor polynomial, then 2^k.
-__device__ dd dd_exp_dev(double x) {
+// exp(r/256)^256 with the degree-11 Taylor polynomial evaluated by Horner in
+// double-double with the coefficients 1/j! stored as double-double (no
+// divisions), then 2^k.
+__device__ __noinline__ static dd dd_exp_dev(double x) {
   const double L1 = 0x1.62e42fefa39efp-1, L2 = 0x1.abc9e3b39803fp-56, L3 = 0x1.7b57a079a1934p-111;
   const double INV_LN2 = 0x1.71547652b82fep+0;
+  // 1/j!, j = 2..11, as (hi, lo)
+  const double CH[10] = {0x1.0000000000000p-1, 0x1.5555555555555p-3, 0x1.5555555555555p-5, 0x1.1111111111111p-7,
+                         0x1.6c16c16c16c17p-10, 0x1.a01a01a01a01ap-13, 0x1.a01a01a01a01ap-16, 0x1.71de3a556c734p-19,
+                         0x1.27e4fb7789f5cp-22, 0x1.ae64567f544e4p-26};
+  const double CL[10] = {0.0, 0x1.5555555555555p-57, 0x1.5555555555555p-59, 0x1.1111111111111p-63,
+                         -0x1.f49f49f49f49fp-65, 0x1.a01a01a01a01ap-73, 0x1.a01a01a01a01ap-76, -0x1.c154f8ddc6c00p-73,
+                         0x1.cbbc05b4fa99ap-76, -0x1.c062e06d1f209p-80};
   double k = rint(__dmul_rn(x, INV_LN2));
   dd a = dd_prod(k, L1);
   dd r = dd_addx({x, 0.0}, {-a.hi, -a.lo});
@@ -132,15 +141,17 @@ __device__ dd dd_exp_dev(double x) {
   r = dd_addx(r, {-__dmul_rn(k, L3), 0.0});
   r.hi = ldexp(r.hi, -8);
   r.lo = ldexp(r.lo, -8);
-  dd p = {1.0, 0.0};
-  for (int j = 11; j >= 1; --j) p = dd_addx({1.0, 0.0}, dd_scale_inv(dd_mulx(r, p), (double)j));
+  dd p = {CH[9], CL[9]};
+  for (int j = 8; j >= 0; --j) p = dd_addx(dd_mulx(p, r), {CH[j], CL[j]});
+  p = dd_addx(dd_mulx(p, r), {1.0, 0.0});  // 1 + r (1 + r/2 + ...)
+  p = dd_addx(dd_mulx(p, r), {1.0, 0.0});
   for (int j = 0; j < 8; ++j) p = dd_mulx(p, p);
   int ki = (int)k;
   return {ldexp(p.hi, ki), ldexp(p.lo, ki)};
 }
 
 // log(y), y > 0, by one Newton step on exp from the libm value.
-__device__ dd dd_log_dev(double y) {
+__device__ __noinline__ static dd dd_log_dev(double y) {
   double y0 = log(y);
   dd e = dd_exp_dev(-y0);
   dd z = dd_addx(dd_mulx(e, {y, 0.0}), {-1.0, 0.0});

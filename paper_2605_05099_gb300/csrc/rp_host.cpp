@@ -455,12 +455,33 @@ int sm_count() {
 
 std::map<std::pair<int, int>, int> g_occ;
 
+// Marsaglia-Tsang constants (Sec. 3.1, gamma): d = s - 1/3, c = 1/sqrt(9 d),
+// s = alpha (alpha >= 1) or alpha + 1 with the boost U^(1/alpha).
+rp::MTParams mt_params(double alpha) {
+  rp::MTParams p{};
+  double s = alpha >= 1.0 ? alpha : alpha + 1.0;
+  volatile double third = 1.0 / 3.0;
+  p.d = s - third;
+  volatile double nine_d = 9.0 * p.d;
+  volatile double sq = std::sqrt(nine_d);
+  p.c = 1.0 / sq;
+  p.alpha = alpha;
+  p.df = (float)p.d;
+  p.cf = (float)p.c;
+  p.boost = alpha < 1.0 ? 1 : 0;
+  return p;
+}
+
+double gamma_wpv(const rp::MTParams& p) { return p.boost ? 3.2 : 2.15; }
+
 // expected words per variate (upper estimate used to size one launch)
 double words_per_variate(int dist, const rp::SampArgs& sp) {
   switch (dist) {
     case rp::D_BOUNDED: return sp.m ? 1.0 / (1.0 - (double)sp.thresh * 0x1.0p-64) : 1.0;
     case rp::D_NORMAL: return 1.0235;
     case rp::D_EXP: return 1.036;
+    case rp::D_GAMMA: return gamma_wpv(sp.ga);
+    case rp::D_BETA: return gamma_wpv(sp.ga) + gamma_wpv(sp.gb);
     default: return 1.0;
   }
 }
@@ -533,12 +554,13 @@ rp_status run_fill(int engine, u64 seed, u64 stream, u64* pos, size_t n, int dis
     a.out = (char*)d_out + done * esz;
     if (!trivial) {
       e = ensure_scratch(tiles);
-      if (!e && (dist == rp::D_NORMAL || dist == rp::D_EXP)) e = ensure_tailq(left / 256 + 4096);
+      const bool queued = dist == rp::D_NORMAL || dist == rp::D_EXP || dist == rp::D_GAMMA || dist == rp::D_BETA;
+      if (!e && queued) e = ensure_tailq(left / 256 + 4096);
       if (e) return fail(RP_ERR_NOMEM, std::string("scratch allocation: ") + cudaGetErrorString((cudaError_t)e));
       a.tile_status = g_scr.status;
       a.ctrl = g_scr.ctrl;
       a.tailq = g_scr.tailq;
-      a.tail_cap = (dist == rp::D_NORMAL || dist == rp::D_EXP) ? g_scr.tail_cap : 0;
+      a.tail_cap = queued ? g_scr.tail_cap : 0;
       rp::Ctrl c0;
       memset(&c0, 0, sizeof(c0));
       c0.done_tile = ~0ull;
@@ -624,12 +646,48 @@ rp_status rp_fill_exp(rp_engine engine, uint64_t seed, uint64_t stream, uint64_t
   return run_fill(engine, seed, stream, (u64*)pos, n, rp::D_EXP, sp, d_out, cuda_stream);
 }
 
-rp_status rp_fill_gamma(rp_engine, uint64_t, uint64_t, uint64_t*, size_t, double, double*, void*) {
-  return fail(RP_ERR_PARAM, "gamma fill not built yet");
+rp_status rp_fill_gamma(rp_engine engine, uint64_t seed, uint64_t stream, uint64_t* pos, size_t n, double alpha,
+                        double* d_out, void* cuda_stream) {
+  if (!(alpha > 0.0) || !std::isfinite(alpha)) return fail(RP_ERR_PARAM, "gamma shape must be positive and finite");
+  rp::SampArgs sp{};
+  sp.ga = mt_params(alpha);
+  return run_fill(engine, seed, stream, (u64*)pos, n, rp::D_GAMMA, sp, d_out, cuda_stream);
 }
 
-rp_status rp_fill_beta(rp_engine, uint64_t, uint64_t, uint64_t*, size_t, double, double, double*, void*) {
-  return fail(RP_ERR_PARAM, "beta fill not built yet");
+rp_status rp_fill_beta(rp_engine engine, uint64_t seed, uint64_t stream, uint64_t* pos, size_t n, double a, double b,
+                       double* d_out, void* cuda_stream) {
+  if (!(a > 0.0) || !(b > 0.0) || !std::isfinite(a) || !std::isfinite(b))
+    return fail(RP_ERR_PARAM, "beta parameters must be positive and finite");
+  rp::SampArgs sp{};
+  sp.ga = mt_params(a);
+  sp.gb = mt_params(b);
+  if (a != b) return run_fill(engine, seed, stream, (u64*)pos, n, rp::D_BETA, sp, d_out, cuda_stream);
+  // Equal shapes: X and Y are consecutive Gamma(a) variates of the stream, so
+  // the fill is a gamma fill of 2n followed by the pairwise ratio.  Done in
+  // blocks to bound the scratch buffer.
+  if (!pos) return fail(RP_ERR_NULL, "pos is NULL");
+  if (n == 0) return RP_OK;
+  if (!d_out) return fail(RP_ERR_NULL, "output pointer is NULL");
+  const size_t blk = (size_t)1 << 24;
+  double* tmp = nullptr;
+  size_t cap = std::min(n, blk);
+  int e = (int)cudaMalloc((void**)&tmp, cap * 2 * sizeof(double));
+  if (e) return fail(RP_ERR_NOMEM, "beta scratch allocation failed");
+  u64 p = *pos;
+  rp_status st = RP_OK;
+  for (size_t done = 0; done < n && st == RP_OK; done += cap) {
+    size_t m = std::min(cap, n - done);
+    rp::SampArgs sg{};
+    sg.ga = sp.ga;
+    st = run_fill(engine, seed, stream, &p, 2 * m, rp::D_GAMMA, sg, tmp, cuda_stream);
+    if (st) break;
+    e = rp::launch_beta_pairs(tmp, d_out + done, m, cuda_stream);
+    if (!e) e = (int)cudaStreamSynchronize((cudaStream_t)cuda_stream);
+    if (e) st = cuda_fail(e, "beta pairs");
+  }
+  cudaFree(tmp);
+  if (st == RP_OK) *pos = p;
+  return st;
 }
 
 rp_status rp_seed_state(rp_engine engine, uint64_t seed, uint64_t stream, uint64_t* words, int* nw) {

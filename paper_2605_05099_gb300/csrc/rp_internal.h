@@ -32,6 +32,7 @@ struct Ctrl {
 // index and the two words that define it.
 struct TailEntry {
   unsigned long long g, w0, w1;
+  unsigned long long x[6];   // gamma/beta: the record words of the variate
 };
 
 // Engine description for one launch.  All word offsets are relative to the
@@ -54,12 +55,19 @@ struct EngineArgs {
   unsigned long long chunk_words;     // words per thread chunk (C)
 };
 
+// Marsaglia-Tsang constants of one gamma shape: d = s - 1/3, c = 1/sqrt(9 d)
+// for s = alpha (alpha >= 1) or s = alpha + 1 with the boost U^(1/alpha).
+struct MTParams {
+  double d, c, alpha;
+  float df, cf;
+  int boost;
+  int pad;
+};
+
 struct SampArgs {
   unsigned long long m;       // bounded: modulus (0 = full range)
   unsigned long long thresh;  // bounded: 2^64 mod m
-  double alpha_d, alpha_c;    // gamma: Marsaglia-Tsang d and c for shape alpha (or alpha+1)
-  double alpha;               // gamma: shape
-  double b_d, b_c, b_alpha;   // beta: second gamma
+  MTParams ga, gb;            // gamma: ga; beta: X ~ ga, Y ~ gb
 };
 
 struct FillArgs {
@@ -78,6 +86,7 @@ struct FillArgs {
 // Kernel launchers (rp_kernels.cu).  Return a cudaError_t value.
 int launch_fill(const FillArgs& a, int grid, void* stream);
 int launch_tails(const FillArgs& a, void* stream);
+int launch_beta_pairs(const double* g, double* out, unsigned long long m, void* stream);
 // Tile geometry and resources of a (engine, dist) kernel.
 struct TileGeom { int nt, c, tile_words, smem_bytes; };
 TileGeom tile_geom(int engine, int dist);
