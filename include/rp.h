@@ -107,6 +107,22 @@ rp_status rp_fill_beta(rp_engine engine, uint64_t seed, uint64_t stream, uint64_
                        size_t n, double a, double b, double* d_out, void* cuda_stream);
 
 /* ---------------------------------------------------------------------
+ * Pathwise (reparameterisation) gradients.  For z = F^{-1}(u; theta) at
+ * fixed u, dz/dtheta = -(dF/dtheta)(z) / f(z): the implicit derivative of the
+ * CDF.  Not in the paper (its samplers have no gradients); FP64 throughout.
+ *   d_z       device array of n variates (as drawn by rp_fill_gamma/beta)
+ *   d_g       device array of n upstream gradients dL/dz, or NULL
+ *   d_dz*     device arrays receiving the per-sample dz/dtheta, or NULL
+ *   h_grad*   host scalars receiving sum_i g_i dz_i/dtheta (needed when d_g
+ *             is given; deterministic fixed-order reduction)
+ * The call returns after the kernels have finished.  alpha, a, b > 0.
+ * ------------------------------------------------------------------- */
+rp_status rp_gamma_grad(const double* d_z, double alpha, const double* d_g, size_t n, double* d_dzda,
+                        double* h_grad_alpha, void* cuda_stream);
+rp_status rp_beta_grad(const double* d_z, double a, double b, const double* d_g, size_t n, double* d_dzda,
+                       double* d_dzdb, double* h_grad_a, double* h_grad_b, void* cuda_stream);
+
+/* ---------------------------------------------------------------------
  * Seeding and stream control (Sec. 2.3), host only.
  * ------------------------------------------------------------------- */
 /* Engine state words from (seed, spawn key): xoshiro s0..s3; PCG64 state

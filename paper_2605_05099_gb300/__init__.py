@@ -53,6 +53,8 @@ def lib():
             "rp_seed_state": [i32, u64, u64, pu64, ctypes.POINTER(i32)],
             "rp_jump_state": [i32, pu64, u64, u64],
             "rp_ziggurat_tables": [i32, pu64, ctypes.POINTER(dbl), ctypes.POINTER(dbl), ctypes.POINTER(dbl)],
+            "rp_gamma_grad": [vp, dbl, vp, sz, vp, ctypes.POINTER(dbl), vp],
+            "rp_beta_grad": [vp, dbl, dbl, vp, sz, vp, vp, ctypes.POINTER(dbl), ctypes.POINTER(dbl), vp],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -127,6 +129,79 @@ def rp_fill_gamma(engine, seed, stream, pos, alpha, out, cuda_stream=None):
 def rp_fill_beta(engine, seed, stream, pos, a, b, out, cuda_stream=None):
     return _fill(lib().rp_fill_beta, engine, seed, stream, pos, out, torch.float64, (float(a), float(b)),
                  cuda_stream)
+
+
+def _ptr_or_null(t, n):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous():
+        raise TypeError("expected a contiguous float64 CUDA tensor")
+    if t.numel() != n:
+        raise ValueError("size mismatch")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def rp_gamma_grad(z, alpha, g=None, dzda=None, cuda_stream=None):
+    """Pathwise gradient of Gamma(alpha) variates z: fills dzda (optional) with
+    dz/dalpha and returns sum(g * dz/dalpha) (None without g)."""
+    n = z.numel()
+    out = ctypes.c_double()
+    _check(lib().rp_gamma_grad(_ptr_or_null(z, n), float(alpha), _ptr_or_null(g, n), n, _ptr_or_null(dzda, n),
+                               ctypes.byref(out), _stream_handle(cuda_stream)))
+    return out.value if g is not None else None
+
+
+def rp_beta_grad(z, a, b, g=None, dzda=None, dzdb=None, cuda_stream=None):
+    """Pathwise gradient of Beta(a, b) variates z: dz/da, dz/db per sample
+    (optional) and the sums with g (None without g)."""
+    n = z.numel()
+    ga, gb = ctypes.c_double(), ctypes.c_double()
+    _check(lib().rp_beta_grad(_ptr_or_null(z, n), float(a), float(b), _ptr_or_null(g, n), n, _ptr_or_null(dzda, n),
+                              _ptr_or_null(dzdb, n), ctypes.byref(ga), ctypes.byref(gb), _stream_handle(cuda_stream)))
+    return (ga.value, gb.value) if g is not None else None
+
+
+class Gamma(torch.autograd.Function):
+    """z ~ Gamma(alpha, 1) (n draws from the given stream), differentiable in
+    alpha by the pathwise (implicit CDF) gradient computed in librp.
+    Gamma.apply(alpha, n, engine, seed, stream, pos) -> z; the new stream
+    position is left in Gamma.last_pos."""
+    last_pos = None
+
+    @staticmethod
+    def forward(ctx, alpha, n, engine, seed, stream, pos):
+        z = torch.empty(n, dtype=torch.float64, device="cuda")
+        Gamma.last_pos = rp_fill_gamma(engine, seed, stream, pos, float(alpha), z)
+        ctx.save_for_backward(z)
+        ctx.alpha = float(alpha)
+        return z
+
+    @staticmethod
+    def backward(ctx, grad_z):
+        (z,) = ctx.saved_tensors
+        ga = rp_gamma_grad(z, ctx.alpha, grad_z.to(torch.float64).contiguous())
+        return torch.tensor(ga, dtype=torch.float64), None, None, None, None, None
+
+
+class Beta(torch.autograd.Function):
+    """z ~ Beta(a, b), differentiable in a and b (pathwise gradient).
+    Beta.apply(a, b, n, engine, seed, stream, pos) -> z; new position in
+    Beta.last_pos."""
+    last_pos = None
+
+    @staticmethod
+    def forward(ctx, a, b, n, engine, seed, stream, pos):
+        z = torch.empty(n, dtype=torch.float64, device="cuda")
+        Beta.last_pos = rp_fill_beta(engine, seed, stream, pos, float(a), float(b), z)
+        ctx.save_for_backward(z)
+        ctx.ab = (float(a), float(b))
+        return z
+
+    @staticmethod
+    def backward(ctx, grad_z):
+        (z,) = ctx.saved_tensors
+        ga, gb = rp_beta_grad(z, ctx.ab[0], ctx.ab[1], grad_z.to(torch.float64).contiguous())
+        return torch.tensor(ga, dtype=torch.float64), torch.tensor(gb, dtype=torch.float64), None, None, None, None, None
 
 
 def rp_seed_state(engine, seed, stream=NO_STREAM):

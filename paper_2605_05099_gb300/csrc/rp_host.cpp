@@ -690,6 +690,68 @@ rp_status rp_fill_beta(rp_engine engine, uint64_t seed, uint64_t stream, uint64_
   return st;
 }
 
+namespace {
+double* g_grad_part = nullptr;   // device: block partials (2 per block) + 2 results
+double* g_grad_h = nullptr;      // pinned host copy of the 2 results
+
+int ensure_grad_scratch() {
+  if (!g_grad_part) {
+    int e = (int)cudaMalloc((void**)&g_grad_part, sizeof(double) * (2 * (size_t)rp::grad_blocks() + 2));
+    if (e) { g_grad_part = nullptr; return e; }
+    e = (int)cudaMallocHost((void**)&g_grad_h, 2 * sizeof(double));
+    if (e) return e;
+  }
+  return 0;
+}
+}  // namespace
+
+rp_status rp_gamma_grad(const double* d_z, double alpha, const double* d_g, size_t n, double* d_dzda,
+                        double* h_grad_alpha, void* cuda_stream) {
+  if (!(alpha > 0.0) || !std::isfinite(alpha)) return fail(RP_ERR_PARAM, "gamma shape must be positive and finite");
+  if (n == 0) { if (h_grad_alpha) *h_grad_alpha = 0.0; return RP_OK; }
+  if (!d_z) return fail(RP_ERR_NULL, "z is NULL");
+  if (d_g && !h_grad_alpha) return fail(RP_ERR_NULL, "h_grad_alpha is NULL while upstream gradients are given");
+  if (!d_g && !d_dzda) return fail(RP_ERR_NULL, "nothing to compute: both d_g and d_dzda are NULL");
+  std::lock_guard<std::mutex> lk(g_mu);
+  int e = ensure_grad_scratch();
+  if (e) return fail(RP_ERR_NOMEM, "gradient scratch allocation failed");
+  double* out = g_grad_part + 2 * (size_t)rp::grad_blocks();
+  e = rp::launch_gamma_grad(d_z, d_g, n, alpha, d_dzda, g_grad_part, out, cuda_stream);
+  if (e) return cuda_fail(e, "gamma gradient launch");
+  g_launches.fetch_add(2);
+  e = (int)cudaMemcpyAsync(g_grad_h, out, sizeof(double), cudaMemcpyDeviceToHost, (cudaStream_t)cuda_stream);
+  if (!e) e = (int)cudaStreamSynchronize((cudaStream_t)cuda_stream);
+  if (e) return cuda_fail(e, "gamma gradient");
+  if (d_g) *h_grad_alpha = g_grad_h[0];
+  return RP_OK;
+}
+
+rp_status rp_beta_grad(const double* d_z, double a, double b, const double* d_g, size_t n, double* d_dzda,
+                       double* d_dzdb, double* h_grad_a, double* h_grad_b, void* cuda_stream) {
+  if (!(a > 0.0) || !(b > 0.0) || !std::isfinite(a) || !std::isfinite(b))
+    return fail(RP_ERR_PARAM, "beta parameters must be positive and finite");
+  if (n == 0) {
+    if (h_grad_a) *h_grad_a = 0.0;
+    if (h_grad_b) *h_grad_b = 0.0;
+    return RP_OK;
+  }
+  if (!d_z) return fail(RP_ERR_NULL, "z is NULL");
+  if (d_g && (!h_grad_a || !h_grad_b)) return fail(RP_ERR_NULL, "h_grad_a/h_grad_b is NULL while upstream gradients are given");
+  if (!d_g && !d_dzda && !d_dzdb) return fail(RP_ERR_NULL, "nothing to compute");
+  std::lock_guard<std::mutex> lk(g_mu);
+  int e = ensure_grad_scratch();
+  if (e) return fail(RP_ERR_NOMEM, "gradient scratch allocation failed");
+  double* out = g_grad_part + 2 * (size_t)rp::grad_blocks();
+  e = rp::launch_beta_grad(d_z, d_g, n, a, b, d_dzda, d_dzdb, g_grad_part, out, cuda_stream);
+  if (e) return cuda_fail(e, "beta gradient launch");
+  g_launches.fetch_add(2);
+  e = (int)cudaMemcpyAsync(g_grad_h, out, 2 * sizeof(double), cudaMemcpyDeviceToHost, (cudaStream_t)cuda_stream);
+  if (!e) e = (int)cudaStreamSynchronize((cudaStream_t)cuda_stream);
+  if (e) return cuda_fail(e, "beta gradient");
+  if (d_g) { *h_grad_a = g_grad_h[0]; *h_grad_b = g_grad_h[1]; }
+  return RP_OK;
+}
+
 rp_status rp_seed_state(rp_engine engine, uint64_t seed, uint64_t stream, uint64_t* words, int* nw) {
   if (!words || !nw) return fail(RP_ERR_NULL, "words/nw is NULL");
   u64 s[4] = {0, 0, 0, 0};

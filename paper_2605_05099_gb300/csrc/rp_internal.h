@@ -87,6 +87,12 @@ struct FillArgs {
 int launch_fill(const FillArgs& a, int grid, void* stream);
 int launch_tails(const FillArgs& a, void* stream);
 int launch_beta_pairs(const double* g, double* out, unsigned long long m, void* stream);
+// gradients (rp_grad.cu)
+int grad_blocks();
+int launch_gamma_grad(const double* z, const double* g, size_t n, double alpha, double* dz, double* part, double* out,
+                      void* stream);
+int launch_beta_grad(const double* z, const double* g, size_t n, double a, double b, double* dza, double* dzb,
+                     double* part, double* out, void* stream);
 // Tile geometry and resources of a (engine, dist) kernel.
 struct TileGeom { int nt, c, tile_words, smem_bytes; };
 TileGeom tile_geom(int engine, int dist);
