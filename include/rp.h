@@ -107,6 +107,35 @@ rp_status rp_fill_beta(rp_engine engine, uint64_t seed, uint64_t stream, uint64_
                        size_t n, double a, double b, double* d_out, void* cuda_stream);
 
 /* ---------------------------------------------------------------------
+ * Normal fill on fixed scratch (Philox4x32-10 only).  Randompack has no
+ * counterpart: this entry point exists for callers that must not allocate
+ * device memory -- code running inside a device allocator's own callbacks
+ * (an out-of-memory or pool-trim hook, where allocating would re-enter the
+ * allocator), processes whose device memory is all reserved by a caching
+ * pool (a fresh cudaMalloc would fail although the pool has room), and
+ * loops that cannot take the device-wide synchronisation of cudaFree.
+ *
+ * Same arguments, stream semantics and output as rp_fill_normal with
+ * engine = RP_PHILOX4X32_10, bit for bit.  Its look-back status words,
+ * control block and tail queue live in one file-scope device array of the
+ * library (about 1.5 MB per device, in place from the moment the library's
+ * device code is loaded), so no allocation routine is called.
+ *   n        0 .. RP_STATIC_MAX_N; larger n is refused with RP_ERR_PARAM
+ *            before any device work (split the call, or use
+ *            rp_fill_normal).
+ * The first call on each device does a one-time setup with that device
+ * current: it looks up the array's address (cudaGetSymbolAddress) and
+ * uploads the ziggurat tables; make that first call before any stream
+ * capture begins.  Every call on a device uses the same array, so two calls
+ * with work in flight at once would race on it; the library's internal
+ * lock, held until the call has synchronised its stream, keeps calls from
+ * several host threads apart.
+ * ------------------------------------------------------------------- */
+#define RP_STATIC_MAX_N ((size_t)1 << 22)
+rp_status rp_fill_normal_philox_static(uint64_t seed, uint64_t stream, uint64_t* pos, size_t n,
+                                       double* d_out, void* cuda_stream);
+
+/* ---------------------------------------------------------------------
  * Pathwise (reparameterisation) gradients.  For z = F^{-1}(u; theta) at
  * fixed u, dz/dtheta = -(dF/dtheta)(z) / f(z): the implicit derivative of the
  * CDF.  Not in the paper (its samplers have no gradients); FP64 throughout.

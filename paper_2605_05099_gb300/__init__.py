@@ -47,6 +47,7 @@ def lib():
             "rp_fill_uniform": [i32, u64, u64, pu64, sz, vp, vp],
             "rp_fill_bounded": [i32, u64, u64, pu64, sz, u64, vp, vp],
             "rp_fill_normal": [i32, u64, u64, pu64, sz, vp, vp],
+            "rp_fill_normal_philox_static": [u64, u64, pu64, sz, vp, vp],
             "rp_fill_exp": [i32, u64, u64, pu64, sz, vp, vp],
             "rp_fill_gamma": [i32, u64, u64, pu64, sz, dbl, vp, vp],
             "rp_fill_beta": [i32, u64, u64, pu64, sz, dbl, dbl, vp, vp],
@@ -116,6 +117,18 @@ def rp_fill_bounded(engine, seed, stream, pos, m, out, cuda_stream=None):
 
 def rp_fill_normal(engine, seed, stream, pos, out, cuda_stream=None):
     return _fill(lib().rp_fill_normal, engine, seed, stream, pos, out, torch.float64, cuda_stream=cuda_stream)
+
+
+STATIC_MAX_N = 1 << 22
+
+
+def rp_fill_normal_philox_static(seed, stream, pos, out, cuda_stream=None):
+    """Philox normal fill on the library's fixed device scratch (no
+    allocation; n <= STATIC_MAX_N).  Same values as rp_fill_normal."""
+    p, n = _out(out, torch.float64)
+    cpos = ctypes.c_uint64(pos)
+    _check(lib().rp_fill_normal_philox_static(seed, stream, ctypes.byref(cpos), n, p, _stream_handle(cuda_stream)))
+    return cpos.value
 
 
 def rp_fill_exp(engine, seed, stream, pos, out, cuda_stream=None):

@@ -784,3 +784,137 @@ rp_status rp_ziggurat_tables(int which, uint64_t* k, double* w, double* f, doubl
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------- normal fill on fixed scratch
+// rp_fill_normal_philox_static: the Philox normal fill of rp_fill_normal run
+// on the fixed device block of rp_static_scratch.cu instead of scratch from
+// cudaMalloc.  Philox is counter-based, so the launch needs no jump tables
+// either; nothing on this path calls an allocation routine.
+namespace {
+static_assert(rp::kStaticMaxN == RP_STATIC_MAX_N, "public and internal scratch limits differ");
+
+constexpr int kStaticMaxDevices = 64;
+struct StaticDev {
+  bool ready;
+  unsigned long long* base;   // the scratch block on this device
+  u64 grid_cap;               // SMs x resident CTAs of the fill kernel
+};
+StaticDev g_static[kStaticMaxDevices];
+
+// One-time setup for the current device `dev`: the scratch address, the
+// ziggurat tables in every kernel module, the launch limits.
+rp_status static_setup(int dev, StaticDev& D) {
+  void* p = nullptr;
+  int e = rp::static_scratch_address(&p);
+  if (e) return cuda_fail(e, "scratch symbol address");
+  if (!p || ((uintptr_t)p & 255)) return fail(RP_ERR_INTERNAL, "scratch symbol is not 256-byte aligned");
+  ZigHost z[2];
+  fill_zig(z[0], RP_ZIG_N_K, RP_ZIG_N_W, RP_ZIG_N_F, RP_ZIG_N_R);
+  fill_zig(z[1], RP_ZIG_E_K, RP_ZIG_E_W, RP_ZIG_E_F, RP_ZIG_E_R);
+  e = rp::upload_zig(z);
+  if (e) return cuda_fail(e, "ziggurat table upload");
+  int sms = 0;
+  e = (int)cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e) return cuda_fail(e, "device attribute");
+  int occ = rp::occupancy_blocks(RP_PHILOX4X32_10, rp::D_NORMAL);
+  D.base = (unsigned long long*)p;
+  D.grid_cap = (u64)(sms > 0 ? sms : 1) * (u64)(occ > 0 ? occ : 1);
+  D.ready = true;
+  return RP_OK;
+}
+}  // namespace
+
+extern "C" rp_status rp_fill_normal_philox_static(uint64_t seed, uint64_t stream, uint64_t* pos, size_t n,
+                                                  double* d_out, void* cuda_stream) {
+  if (!pos) return fail(RP_ERR_NULL, "pos is NULL");
+  if (n > RP_STATIC_MAX_N)
+    return fail(RP_ERR_PARAM, "n = " + std::to_string(n) + " exceeds RP_STATIC_MAX_N = 4194304 (2^22), " +
+                                  "the capacity of the fixed scratch; use rp_fill_normal or split the call");
+  if (n == 0) return RP_OK;
+  if (!d_out) return fail(RP_ERR_NULL, "output pointer is NULL");
+  if ((uintptr_t)d_out & 7) return fail(RP_ERR_PARAM, "output pointer must be 8-byte aligned");
+  // The lock is held until the stream has been synchronised, so calls from
+  // several host threads never have work on the shared block at once.
+  std::lock_guard<std::mutex> lk(g_mu);
+  int dev = 0;
+  int e = (int)cudaGetDevice(&dev);
+  if (e) return cuda_fail(e, "current device");
+  if (dev < 0 || dev >= kStaticMaxDevices) return fail(RP_ERR_PARAM, "device ordinal out of range");
+  StaticDev& D = g_static[dev];
+  if (!D.ready) {
+    rp_status st = static_setup(dev, D);
+    if (st) return st;
+  }
+  u64 s[4] = {0, 0, 0, 0};
+  rp_status st = seed_state(RP_PHILOX4X32_10, seed, stream, s);
+  if (st) return st;
+
+  rp::Ctrl* ctrl = (rp::Ctrl*)D.base;
+  unsigned long long* status = D.base + rp::kStaticCtrlWords;
+  rp::TailEntry* tailq = (rp::TailEntry*)(D.base + rp::kStaticCtrlWords + rp::kStaticTiles);
+  cudaStream_t cs = (cudaStream_t)cuda_stream;
+
+  rp::FillArgs a;
+  memset(&a, 0, sizeof(a));
+  a.eng.engine = RP_PHILOX4X32_10;
+  a.dist = rp::D_NORMAL;
+  rp::TileGeom tg = rp::tile_geom(RP_PHILOX4X32_10, rp::D_NORMAL);
+  const u64 T = (u64)tg.tile_words;
+  memcpy(a.eng.s, s, sizeof(s));
+  a.eng.tile_words = T;
+  a.eng.chunk_words = (u64)tg.c;
+  a.tile_status = status;
+  a.ctrl = ctrl;
+  a.tailq = tailq;
+  a.tail_cap = rp::kStaticTailCap;
+
+  u64 cur = *pos;
+  size_t done = 0;
+  for (int launch = 0; done < n; ++launch) {
+    if (launch > 64) return fail(RP_ERR_INTERNAL, "too many continuation launches");
+    const size_t left = n - done;
+    const double wpv = 1.0235;
+    const double need = (double)left * wpv + 8.0 * std::sqrt((double)left * wpv) + 64.0;
+    const u64 tiles = (u64)(need / (double)T) + 2;
+    if (tiles > rp::kStaticTiles) return fail(RP_ERR_INTERNAL, "tile count exceeds the fixed scratch");
+    const u64 grid = std::min<u64>(tiles, D.grid_cap);
+    a.eng.word0 = cur;
+    a.eng.stride = grid * T;
+    a.n = left;
+    a.n_tiles = tiles;
+    a.out = d_out + done;
+    // What must start at zero: the status words of this launch's tiles and
+    // the control block (its tail count included), except done_tile, which
+    // starts at all ones.  Tail entries are written before they are read.
+    e = (int)cudaMemsetAsync(status, 0, tiles * 8, cs);
+    if (!e) e = (int)cudaMemsetAsync(ctrl, 0, sizeof(rp::Ctrl), cs);
+    if (!e) e = (int)cudaMemsetAsync(&ctrl->done_tile, 0xff, sizeof(ctrl->done_tile), cs);
+    if (e) return cuda_fail(e, "scratch reset");
+    e = rp::launch_fill(a, (int)grid, cuda_stream);
+    if (e) return cuda_fail(e, "kernel launch");
+    g_launches.fetch_add(1);
+    e = rp::launch_tails(a, cuda_stream);
+    if (e) return cuda_fail(e, "tail kernel launch");
+    g_launches.fetch_add(1);
+    rp::Ctrl c;
+    e = (int)cudaMemcpyAsync(&c, ctrl, sizeof(c), cudaMemcpyDeviceToHost, cs);
+    if (!e) e = (int)cudaStreamSynchronize(cs);
+    if (e) return cuda_fail(e, "fill");
+    if (c.err) {
+      char buf[160];
+      snprintf(buf, sizeof buf, "device check failed (bits 0x%x, tile %llu)", c.err, (unsigned long long)c.err_info);
+      return fail(c.err & rp::E_TIMEOUT ? RP_ERR_TIMEOUT : RP_ERR_INTERNAL, buf);
+    }
+    if (c.n_tail > rp::kStaticTailCap) return fail(RP_ERR_INTERNAL, "tail queue of the fixed scratch overflowed");
+    if (c.done_tile != ~0ull) {
+      cur += c.next_pos;
+      done = n;
+    } else {
+      if (c.total == 0 && c.next_pos == 0) return fail(RP_ERR_INTERNAL, "launch produced no output");
+      done += c.total;
+      cur += c.next_pos;
+    }
+  }
+  *pos = cur;
+  return RP_OK;
+}

@@ -93,6 +93,19 @@ int launch_gamma_grad(const double* z, const double* g, size_t n, double alpha, 
                       void* stream);
 int launch_beta_grad(const double* z, const double* g, size_t n, double a, double b, double* dza, double* dzb,
                      double* part, double* out, void* stream);
+// Fixed scratch of the normal fill that allocates nothing
+// (rp_static_scratch.cu).  Sized for at most kStaticMaxN outputs per call:
+// a Philox normal fill of n outputs needs at most
+// (1.0235 n + 8 sqrt(1.0235 n) + 64) / 32768 + 2 tiles (133 at the maximum)
+// and n / 256 + 4096 tail entries, the bounds the allocating path uses.
+constexpr unsigned long long kStaticMaxN = 1ull << 22;
+constexpr unsigned long long kStaticTiles = 256;
+constexpr unsigned long long kStaticTailCap = kStaticMaxN / 256 + 4096;
+constexpr size_t kStaticCtrlWords = 32;
+constexpr size_t kStaticWords = kStaticCtrlWords + kStaticTiles + kStaticTailCap * (sizeof(TailEntry) / 8);
+static_assert(sizeof(Ctrl) <= kStaticCtrlWords * 8, "control block does not fit its slot");
+static_assert(sizeof(TailEntry) % 8 == 0, "tail entries must be whole words");
+int static_scratch_address(void** p);
 // Tile geometry and resources of a (engine, dist) kernel.
 struct TileGeom { int nt, c, tile_words, smem_bytes; };
 TileGeom tile_geom(int engine, int dist);
