@@ -52,7 +52,7 @@ class ClockSampler:
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -61,7 +61,17 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.rows.append([x.strip() for x in line.split(",")])
+            self.rows.append((time.time(), [x.strip() for x in line.split(",")]))
+
+    def wait_first(self, timeout=3.0):
+        """Block until nvidia-smi has produced its first sample."""
+        t0 = time.time()
+        while self.proc is not None and not self.rows and time.time() - t0 < timeout:
+            time.sleep(0.02)
+
+    def mark(self, t_begin, t_end):
+        """Host time window of the timed region (samples outside it are dropped)."""
+        self.window = (t_begin, t_end)
 
     def stop(self):
         if self.proc is None:
@@ -74,7 +84,11 @@ class ClockSampler:
         self.t.join(timeout=2)
         sm, mx, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for r in self.rows:
+        win = getattr(self, "window", None)
+        rows = [r for t, r in self.rows if win is None or win[0] <= t <= win[1] + 0.25]
+        if not rows:
+            rows = [r for _, r in self.rows]
+        for r in rows:
             try:
                 sm.append(float(r[1]))
                 mx = float(r[2])
@@ -86,6 +100,10 @@ class ClockSampler:
         sm.sort()
         med = sm[len(sm) // 2] if sm else None
         return {"sm_mhz": med, "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _key(engine, dist, params):
+    return f"{engine}/{dist}{'' if not params else ':' + str(params[0])}"
 
 
 def _dist_init():
@@ -120,7 +138,12 @@ def run_gpu(args):
         return rp.rp_fill_bounded(engine, SEED, spawn, 0, params[0], out_u, stream)
 
     fills = [(e, d, p) for e in ENGINES for d, p in SAMPLERS]
-    per_fill_ms = {f"{e}/{d}{'' if not p else ':' + str(p[0])}": 0.0 for e, d, p in fills}
+    if args.only:
+        fills = [f for f in fills if _key(*f) == args.only]
+        if not fills:
+            raise SystemExit(f"--only {args.only}: no such fill; keys are "
+                             + ", ".join(_key(e, d, p) for e in ENGINES for d, p in SAMPLERS))
+    per_fill_ms = {_key(e, d, p): 0.0 for e, d, p in fills}
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in fills]
 
     def step(record):
@@ -131,17 +154,19 @@ def run_gpu(args):
             if record:
                 ev[i][1].record(stream)
 
+    clocks = ClockSampler(local)
+    clocks.start()
+    clocks.wait_first()
     for _ in range(args.warmup):
         step(False)
     torch.cuda.synchronize()
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
-    clocks = ClockSampler(local)
-    clocks.start()
     launches0 = rp.rp_kernel_launches()
     t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
+    h_begin = time.time()
     t0.record(stream)
     for _ in range(args.steps):
         step(True)
@@ -150,6 +175,7 @@ def run_gpu(args):
             per_fill_ms[key] += ev[i][0].elapsed_time(ev[i][1])
     t1.record(stream)
     torch.cuda.synchronize()
+    clocks.mark(h_begin, time.time())
     launches = rp.rp_kernel_launches() - launches0
     ms = t0.elapsed_time(t1)
     clk = clocks.stop()
@@ -204,7 +230,9 @@ def run_gpu(args):
                 "data": "synthetic (seeded engine streams; no dataset)",
                 "config": {"workload": WORKLOAD, "n_per_fill": N_FILL, "fills_per_step": len(fills),
                            "l2": "outputs (2 GiB per fill) exceed L2; no flush needed",
-                           "parallelism": f"independent streams x{world}"},
+                           "parallelism": f"independent streams x{world}",
+                           **({"profiling_subset": args.only or f"n=2^{args.log2n}"}
+                              if (args.only or args.log2n != 28) else {})},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
                 "clocks": clk}
         print(json.dumps(line))
@@ -262,15 +290,20 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--cpu-sample", type=int, default=None,
                     help="oracle variates per fill (default 2^24 for the baseline leg, 2^21 per reference step)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--only", default=None,
+                    help="profiling: run only this fill (e.g. xoshiro256pp/normal); not a bench line")
+    ap.add_argument("--log2n", type=int, default=28, help="profiling: n = 2^log2n per fill (bench: 28)")
     args = ap.parse_args()
+    global N_FILL
+    N_FILL = 1 << args.log2n
     if args.cpu_sample is None:
-        args.cpu_sample = (1 << 21) if args.impl == "reference" else (1 << 24)
+        args.cpu_sample = (1 << 21) if args.impl == "reference" else (1 << 26)
     if args.impl == "reference":
         run_reference(args)
     else:

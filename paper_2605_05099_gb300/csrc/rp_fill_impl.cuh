@@ -10,23 +10,26 @@
 // known, so every thread streams its chunk out through a per-warp staging
 // buffer that turns the chunk-contiguous runs into coalesced 128-byte lines.
 //
-// Rejection samplers: each thread runs the serial sampler as a state machine
-// fed one word at a time.  The parallel parse (chains of candidates across
-// chunk seams) uses sync points:
+// Rejection samplers: each thread walks the serial sampler's chain of
+// candidates over its chunk.  The parallel parse (chains across chunk seams)
+// uses sync points for samplers whose candidate length follows from its
+// first word (ziggurat normal/exponential, bounded; rp_lean.cuh):
 //   * len(q) is the number of words a candidate starting at word q would
 //     consume (evaluated speculatively for any q);
 //   * the sync point of a chunk is the first s in [G, G+S) (relative to the
 //     chunk) such that every candidate starting in [0, s) ends by s.  The
 //     true chain, which enters the chunk from the previous one, then passes
 //     through s unless a candidate longer than G straddles the seam;
-//   * thread t runs the sampler from its sync point to the next chunk's sync
-//     point, which it evaluates itself from the same words with the same
-//     rule, and checks that the chain lands on it (E_LANDING otherwise).
-// Pass 1 counts the outputs of each segment; a block scan and a decoupled
-// look-back over tile counts give every thread its first output index; pass
-// 2 regenerates the chunk and writes the values through the staging buffer.
-// Outputs whose value needs FP64 libm (ziggurat tails, ~3e-4 of outputs) are
-// queued and evaluated by full warps in a second kernel.
+//   * thread t walks from its sync point to the next chunk's sync point,
+//     which it evaluates itself from the same words with the same rule, and
+//     checks that the chain lands on it (E_LANDING otherwise).
+// Gamma and beta attempts have no such points; their seams are merge points
+// (k_merge below).  Pass 1 counts the outputs of each segment; a block scan
+// and a decoupled look-back over tile counts give every thread its first
+// output index; pass 2 regenerates the chunk and writes the values through
+// the staging buffer.  Outputs whose value needs FP64 libm (ziggurat tails,
+// ~3e-4 of outputs) are queued and evaluated by full warps in a second
+// kernel.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -43,8 +46,6 @@ namespace {
 
 constexpr u64 M52 = (1ull << 52) - 1;
 constexpr u64 M53 = (1ull << 53) - 1;
-constexpr int kG = 8;                                 // sync window
-constexpr int kS = 24;                                // sync search length
 constexpr unsigned long long kSpinMax = 1ull << 25;   // bounded waits (x ~100 ns)
 constexpr int kStage = 16;                            // outputs staged per lane
 constexpr int kRow = kStage + 1;                      // padded row stride (no bank conflicts)
@@ -107,30 +108,7 @@ __device__ __forceinline__ bool tail_pair_accept(u64 w1, u64 w2, const ZigDev& z
 #include "rp_gamma.cuh"
 
 // ------------------------------------------------------------------ samplers
-// Each sampler is a state machine fed one word at a time, run twice over a
-// segment.  Pass 1 (feed1) counts outputs and records the accept decisions
-// in chain order: wedge tests are queued per lane and evaluated after the
-// chunk (all lanes together, instead of one divergent lane at a time), tail
-// pair tests are evaluated on the spot (they decide the candidate length).
-// Pass 2 (feed2) replays the recorded decisions; feed2 returns OUT_VAL with
-// the word whose value is the output, or OUT_TAIL with the two words of a
-// tail output (FP64 libm, evaluated later by full warps).
-enum { OUT_NONE = 0, OUT_VAL = 1, OUT_TAIL = 2 };
-constexpr int kPend = 16;    // wedge tests queued per lane and chunk
-
-struct Rec {
-  u64 wbits, tbits;          // wedge / tail-pair decisions in chain order
-  int nw, nt, np;            // decisions recorded, pending wedge tests
-  int replay;                // 0: pass 2 must re-evaluate decisions
-  u64 pu0[kPend], pu1[kPend];
-  __device__ __forceinline__ void reset() { wbits = tbits = 0; nw = nt = np = 0; replay = 1; }
-  __device__ __forceinline__ void push_tail(bool b) {
-    if (nt < 64) tbits |= (u64)b << nt;
-    else replay = 0;
-    ++nt;
-  }
-};
-
+// One word per variate: raw words and 53-bit uniforms.
 struct SampU64 {
   static constexpr bool kOnePerWord = true;
   typedef u64 out_t;
@@ -142,197 +120,19 @@ struct SampUniform {
   __device__ static __forceinline__ double value1(u64 u, const SampArgs&) { return u53_bits(u); }
 };
 
-// Lemire (Sec. 3.2): one word per attempt; accept when low64(u m) >= 2^64 mod m.
-struct SampBounded {
-  static constexpr bool kOnePerWord = false;
-  static constexpr bool kLen1 = true;
-  typedef u64 out_t;
-  struct M {
-    __device__ __forceinline__ void reset() {}
-    __device__ __forceinline__ bool idle() const { return true; }
-    __device__ __forceinline__ int feed1(u64 u, const ZigDev&, const SampArgs& a, Rec&) {
-      return u * a.m >= a.thresh;
-    }
-    __device__ __forceinline__ int feed2(u64 u, const ZigDev&, const SampArgs& a, Rec&, u64* ew, u64*, u64*) {
-      *ew = u;
-      return u * a.m >= a.thresh ? OUT_VAL : OUT_NONE;
-    }
-  };
-  __device__ static __forceinline__ int settle(Rec&, const ZigDev&) { return 0; }
-  __device__ static __forceinline__ u64 value(u64 u, const ZigDev&, const SampArgs& a) { return __umul64hi(u, a.m); }
-  template <class E>
-  __device__ static __forceinline__ int len(u64, const E&, const ZigDev&) { return 1; }
-  __device__ static double tail_value(u64, u64, const ZigDev&) { return 0.0; }
-};
-
-// Normal ziggurat (Sec. 3.1): bits 0-7 strip i, bit 8 sign, bits 9-60 r.
+// Values of ziggurat tail outputs (FP64 libm log, within 2 ulp of the
+// correctly rounded value), evaluated by k_tails from the queued words.
 struct SampNormal {
-  static constexpr bool kOnePerWord = false;
-  static constexpr bool kLen1 = false;
   typedef double out_t;
-  struct M {
-    int st;  // 0 idle, 1 wedge waiting for U, 2 tail waiting for U1, 3 tail waiting for U2
-    u64 u0, w1;
-    __device__ __forceinline__ void reset() { st = 0; }
-    __device__ __forceinline__ bool idle() const { return st == 0; }
-    __device__ __forceinline__ int feed1(u64 u, const ZigDev& z, const SampArgs&, Rec& rc) {
-      if (st == 0) {
-        int i = (int)(u & 0xff);
-        if (((u >> 9) & M52) < z.k[i]) return 1;
-        u0 = u;
-        st = i ? 1 : 2;
-        return 0;
-      }
-      if (st == 1) {
-        st = 0;
-        if (rc.np < kPend) {
-          rc.pu0[rc.np] = u0;
-          rc.pu1[rc.np] = u;
-          ++rc.np;
-          return 0;
-        }
-        rc.replay = 0;  // too many to queue: decide here, pass 2 re-decides
-        return wedge_accept<true>((u0 >> 9) & M52, (int)(u0 & 0xff), u, z);
-      }
-      if (st == 2) { w1 = u; st = 3; return 0; }
-      bool ok = tail_pair_accept(w1, u, z);
-      rc.push_tail(ok);
-      st = ok ? 0 : 2;
-      return ok;
-    }
-    __device__ __forceinline__ int feed2(u64 u, const ZigDev& z, const SampArgs&, Rec& rc, u64* ew, u64* t0,
-                                         u64* t1) {
-      if (st == 0) {
-        int i = (int)(u & 0xff);
-        if (((u >> 9) & M52) < z.k[i]) { *ew = u; return OUT_VAL; }
-        u0 = u;
-        st = i ? 1 : 2;
-        return OUT_NONE;
-      }
-      if (st == 1) {
-        st = 0;
-        bool ok = rc.replay ? ((rc.wbits >> rc.nw) & 1) : wedge_accept<true>((u0 >> 9) & M52, (int)(u0 & 0xff), u, z);
-        ++rc.nw;
-        if (!ok) return OUT_NONE;
-        *ew = u0;
-        return OUT_VAL;
-      }
-      if (st == 2) { w1 = u; st = 3; return OUT_NONE; }
-      bool ok = rc.replay ? ((rc.tbits >> rc.nt) & 1) : tail_pair_accept(w1, u, z);
-      ++rc.nt;
-      if (!ok) { st = 2; return OUT_NONE; }
-      st = 0;
-      *t0 = u0;
-      *t1 = w1;
-      return OUT_TAIL;
-    }
-  };
-  // pass-1 wedge tests queued in the chunk, all lanes together
-  __device__ static int settle(Rec& rc, const ZigDev& z) {
-    int c = 0;
-    for (int j = 0; j < rc.np; ++j) {
-      bool ok = wedge_accept<true>((rc.pu0[j] >> 9) & M52, (int)(rc.pu0[j] & 0xff), rc.pu1[j], z);
-      rc.wbits |= (u64)ok << j;
-      c += ok;
-    }
-    rc.nw = 0;
-    rc.nt = 0;
-    return c;
-  }
-  __device__ static __forceinline__ double value(u64 u, const ZigDev& z, const SampArgs&) {
-    int i = (int)(u & 0xff);
-    return neg_if(mul_rn_dmul((u >> 9) & M52, z.w[i]), (u >> 8) & 1);
-  }
-  // speculative candidate length at a word; `g` is the engine positioned
-  // right after it (copied, never advanced)
-  template <class E>
-  __device__ static __forceinline__ int len(u64 u, const E& g, const ZigDev& z) {
-    int i = (int)(u & 0xff);
-    if (((u >> 9) & M52) < z.k[i]) return 1;
-    if (i != 0) return 2;
-    E h = g;
-    for (int k = 1; k <= kTailPairsMax; ++k) {
-      u64 a = h.next(), b = h.next();
-      if (tail_pair_accept(a, b, z)) return 1 + 2 * k;
-    }
-    return 1 << 20;  // longer than any window: no sync point here
-  }
-  // +-(R + a), a = -log(1-U1)/R of the accepted pair; libm log (within 2 ulp
-  // of the correctly rounded value)
+  // +-(R + a), a = -log(1-U1)/R of the accepted pair; sign from the candidate word
   __device__ static double tail_value(u64 u0, u64 w1, const ZigDev& z) {
     double a = __ddiv_rn(-log(__dsub_rn(1.0, u53_bits(w1))), z.R);
     return neg_if(__dadd_rn(z.R, a), (u0 >> 8) & 1);
   }
 };
-
-// Exponential ziggurat (Sec. 3.1): bits 0-7 strip i, bits 8-60 r; tail R - log(1-U).
 struct SampExp {
-  static constexpr bool kOnePerWord = false;
-  static constexpr bool kLen1 = false;
   typedef double out_t;
-  struct M {
-    int st;  // 0 idle, 1 wedge waiting for U, 2 tail waiting for U
-    u64 u0;
-    __device__ __forceinline__ void reset() { st = 0; }
-    __device__ __forceinline__ bool idle() const { return st == 0; }
-    __device__ __forceinline__ int feed1(u64 u, const ZigDev& z, const SampArgs&, Rec& rc) {
-      if (st == 0) {
-        int i = (int)(u & 0xff);
-        if (((u >> 8) & M53) < z.k[i]) return 1;
-        u0 = u;
-        st = i ? 1 : 2;
-        return 0;
-      }
-      int s = st;
-      st = 0;
-      if (s == 2) return 1;  // the tail always accepts
-      if (rc.np < kPend) {
-        rc.pu0[rc.np] = u0;
-        rc.pu1[rc.np] = u;
-        ++rc.np;
-        return 0;
-      }
-      rc.replay = 0;
-      return wedge_accept<false>((u0 >> 8) & M53, (int)(u0 & 0xff), u, z);
-    }
-    __device__ __forceinline__ int feed2(u64 u, const ZigDev& z, const SampArgs&, Rec& rc, u64* ew, u64* t0,
-                                         u64* t1) {
-      if (st == 0) {
-        int i = (int)(u & 0xff);
-        if (((u >> 8) & M53) < z.k[i]) { *ew = u; return OUT_VAL; }
-        u0 = u;
-        st = i ? 1 : 2;
-        return OUT_NONE;
-      }
-      int s = st;
-      st = 0;
-      if (s == 2) { *t0 = u0; *t1 = u; return OUT_TAIL; }
-      bool ok = rc.replay ? ((rc.wbits >> rc.nw) & 1) : wedge_accept<false>((u0 >> 8) & M53, (int)(u0 & 0xff), u, z);
-      ++rc.nw;
-      if (!ok) return OUT_NONE;
-      *ew = u0;
-      return OUT_VAL;
-    }
-  };
-  __device__ static int settle(Rec& rc, const ZigDev& z) {
-    int c = 0;
-    for (int j = 0; j < rc.np; ++j) {
-      bool ok = wedge_accept<false>((rc.pu0[j] >> 8) & M53, (int)(rc.pu0[j] & 0xff), rc.pu1[j], z);
-      rc.wbits |= (u64)ok << j;
-      c += ok;
-    }
-    rc.nw = 0;
-    rc.nt = 0;
-    return c;
-  }
-  __device__ static __forceinline__ double value(u64 u, const ZigDev& z, const SampArgs&) {
-    return mul_rn_dmul((u >> 8) & M53, z.w[u & 0xff]);
-  }
-  template <class E>
-  __device__ static __forceinline__ int len(u64 u, const E&, const ZigDev& z) {
-    int i = (int)(u & 0xff);
-    return ((u >> 8) & M53) < z.k[i] ? 1 : 2;
-  }
+  // R - log(1 - U)
   __device__ static double tail_value(u64, u64 w1, const ZigDev& z) {
     return __dsub_rn(z.R, log(__dsub_rn(1.0, u53_bits(w1))));
   }
@@ -427,6 +227,8 @@ __device__ __forceinline__ void flush_rows(OT* __restrict__ out, const OT* row_b
   }
 }
 
+#include "rp_lean.cuh"
+
 // ------------------------------------------------------------------ kernels
 template <int NT, int C, class E, class S>
 __global__ void __launch_bounds__(NT) k_onepw(FillArgs a) {
@@ -449,131 +251,6 @@ __global__ void __launch_bounds__(NT) k_onepw(FillArgs a) {
       flush_rows<OT>(out, stage[wid], base + j0, kStage, a.n);
       __syncwarp();
     }
-    e.advance(a.eng);
-  }
-}
-
-template <int NT, int C, class E, class S>
-__global__ void __launch_bounds__(NT) k_reject(FillArgs a) {
-  typedef typename S::out_t OT;
-  constexpr int T = NT * C;
-  __shared__ __align__(16) OT stage[NT / 32][32 * kRow];
-  __shared__ int wsum[32];
-  __shared__ int misc[8];
-  __shared__ ZigDev zs;
-  const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
-  if (!S::kLen1) {
-    const int which = (a.dist == D_EXP) ? 1 : 0;
-    const u64* src = (const u64*)&g_zig[which];
-    u64* dst = (u64*)&zs;
-    for (int i = t; i < (int)(sizeof(ZigDev) / 8); i += NT) dst[i] = src[i];
-    __syncthreads();
-  }
-  const ZigDev& z = zs;
-  OT* out = (OT*)a.out;
-  __shared__ u64 sh4[4];
-  E e;
-  e.init_tile(a.eng, blockIdx.x, t, sh4);
-
-  for (u64 k = blockIdx.x; k < a.n_tiles; k += gridDim.x) {
-    if (ld_volatile(&a.ctrl->done_tile) < k) break;
-    // ---------------- pass 1: sync point, segment walk, count
-    E g = e;
-    int sig = 0, cnt = 0, endp = C;
-    bool ok = true;
-    if (!S::kLen1 && !(k == 0 && t == 0)) {
-      // first s in [G, G+S) with every candidate starting in [0, s) ending by s
-      int reach = 0;
-      sig = -1;
-      for (int q = 0; q < kG + kS; ++q) {
-        if (q >= kG && reach <= q) { sig = q; break; }
-        u64 u = g.next();
-        reach = max(reach, q + S::len(u, g, z));
-      }
-      if (sig < 0) { set_err(a.ctrl, E_NOSYNC, k); ok = false; }
-    }
-    typename S::M m;
-    m.reset();
-    Rec rc;
-    rc.reset();
-    if (ok) {
-      for (int p = sig; p < C; ++p) cnt += m.feed1(g.next(), z, a.sp, rc);
-      if (!S::kLen1) {
-        // the next chunk's sync point, by the same rule, while the chain runs on
-        int reach = C;
-        endp = -1;
-        for (int q = C; q < C + kG + kS; ++q) {
-          if (q - C >= kG && reach <= q) {
-            endp = q;
-            break;
-          }
-          u64 u = g.next();
-          reach = max(reach, q + S::len(u, g, z));
-          cnt += m.feed1(u, z, a.sp, rc);
-        }
-        if (endp < 0) { set_err(a.ctrl, E_NOSYNC, k); ok = false; }
-        else if (!m.idle()) { set_err(a.ctrl, E_LANDING, k); ok = false; }
-      }
-      cnt += S::settle(rc, z);
-    }
-    // ---------------- offsets
-    int off = block_exclusive_scan<NT>(cnt, wsum, &misc[1]);
-    if (t < 32) {
-      unsigned long long ex = lookback_warp(a.tile_status, k, (unsigned long long)misc[1], a.ctrl);
-      if (t == 0) {
-        misc[2] = (int)(ex & 0x7fffffff);
-        misc[3] = (int)(ex >> 31);
-        misc[4] = (ex == ~0ull);
-      }
-    }
-    __syncthreads();
-    if (misc[4]) break;
-    const u64 base = (u64)(unsigned)misc[2] | ((u64)(unsigned)misc[3] << 31);
-    const u64 chunk0 = k * (u64)T + (u64)t * C;   // stream position of the chunk
-    if (t == NT - 1 && k + 1 == a.n_tiles && base + (u64)misc[1] < a.n) {
-      // ran out of tiles: report where the chain continues
-      a.ctrl->total = base + (u64)misc[1];
-      a.ctrl->next_pos = chunk0 + (u64)endp;
-      a.ctrl->last_tile = k;
-    }
-    // ---------------- pass 2: regenerate, evaluate, stage, write
-    if (base < a.n) {
-      g = e;
-      for (int q = 0; q < sig; ++q) (void)g.next();
-      m.reset();
-      const u64 my0 = base + (u64)off;   // first output index of this thread
-      int emitted = 0;
-      int p = sig;
-      bool active = ok && cnt > 0;
-      while (__any_sync(0xffffffffu, active)) {
-        int ns = 0;
-        while (active && ns < kStage) {
-          u64 t0 = 0, t1 = 0, ew = 0;
-          int r = m.feed2(g.next(), z, a.sp, rc, &ew, &t0, &t1);
-          ++p;
-          if (r == OUT_NONE) continue;
-          const u64 gi = my0 + emitted + ns;
-          OT v = S::value(ew, z, a.sp);
-          if (r == OUT_TAIL && gi < a.n) {
-            unsigned long long qi = atomicAdd(&a.ctrl->n_tail, 1ull);
-            if (qi < a.tail_cap) a.tailq[qi] = TailEntry{gi, t0, t1};
-            else v = (OT)S::tail_value(t0, t1, z);
-          }
-          stage[wid][lane * kRow + ns] = v;
-          ++ns;
-          if (gi == a.n - 1) {
-            a.ctrl->next_pos = chunk0 + (u64)p;
-            atomicMin(&a.ctrl->done_tile, k);
-          }
-          if (emitted + ns == cnt) active = false;
-        }
-        __syncwarp();
-        flush_rows<OT>(out, stage[wid], my0 + emitted, ns, a.n);
-        __syncwarp();
-        emitted += ns;
-      }
-    }
-    __syncthreads();
     e.advance(a.eng);
   }
 }
@@ -789,19 +466,21 @@ int launch_merge(const FillArgs& a, int grid, cudaStream_t s, int* occ) {
 
 template <class E, class S>
 int launch_es(const FillArgs& a, int grid, cudaStream_t s, int* occ) {
-  if constexpr (S::kOnePerWord) {
-    if (occ) {
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k_onepw<NT_, C_, E, S>, NT_, 0);
-      return 0;
-    }
-    k_onepw<NT_, C_, E, S><<<grid, NT_, 0, s>>>(a);
-  } else {
-    if (occ) {
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k_reject<NT_, C_, E, S>, NT_, 0);
-      return 0;
-    }
-    k_reject<NT_, C_, E, S><<<grid, NT_, 0, s>>>(a);
+  if (occ) {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k_onepw<NT_, C_, E, S>, NT_, 0);
+    return 0;
   }
+  k_onepw<NT_, C_, E, S><<<grid, NT_, 0, s>>>(a);
+  return (int)cudaGetLastError();
+}
+
+template <class E, class S>
+int launch_lean(const FillArgs& a, int grid, cudaStream_t s, int* occ) {
+  if (occ) {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k_lean<NT_, C_, E, S>, NT_, 0);
+    return 0;
+  }
+  k_lean<NT_, C_, E, S><<<grid, NT_, 0, s>>>(a);
   return (int)cudaGetLastError();
 }
 
@@ -810,9 +489,9 @@ int dispatch_dist(const FillArgs& a, int grid, cudaStream_t s, int* occ) {
   switch (a.dist) {
     case D_U64: return launch_es<E, SampU64>(a, grid, s, occ);
     case D_UNIFORM: return launch_es<E, SampUniform>(a, grid, s, occ);
-    case D_BOUNDED: return launch_es<E, SampBounded>(a, grid, s, occ);
-    case D_NORMAL: return launch_es<E, SampNormal>(a, grid, s, occ);
-    case D_EXP: return launch_es<E, SampExp>(a, grid, s, occ);
+    case D_BOUNDED: return launch_lean<E, LeanBounded>(a, grid, s, occ);
+    case D_NORMAL: return launch_lean<E, LeanNormal>(a, grid, s, occ);
+    case D_EXP: return launch_lean<E, LeanExp>(a, grid, s, occ);
     case D_GAMMA: return launch_merge<E, SampGamma>(a, grid, s, occ);
     case D_BETA: return launch_merge<E, SampBeta>(a, grid, s, occ);
     default: return (int)cudaErrorInvalidValue;

@@ -1,0 +1,411 @@
+// Bitmap two-pass fill for samplers whose candidate length is fixed by the
+// candidate's first word: the normal ziggurat (1 word fast, 2 words wedge,
+// 1 + 2k words tail), the exponential ziggurat (1 or 2 words) and Lemire's
+// bounded integers (1 word).
+//
+// Tiles, chunks, sync points and the look-back are those of the file header.
+// What differs is how the two passes share work:
+//   pass 1 walks the chain and records, per thread, a bitmap of the chunk
+//          positions whose candidate produced an output (wedge tests are
+//          queued in shared memory and decided after the walk, all lanes
+//          together; tail outputs go to a per-tile list);
+//   pass 2 regenerates the words and turns every marked word into its value,
+//          with no parsing at all, writing through the per-warp staging rows.
+// The common step (a fast-accept candidate) is one 32-bit compare of the
+// word's top significand bits against k_i >> 20 (normal) or >> 21
+// (exponential); equal top bits fall back to the full 52/53-bit compare.
+//
+// Fragment of rp_fill_impl.cuh, included inside its namespace after the
+// samplers, scans and staging helpers.
+
+// Out-of-line copies of the rare tests, so that the unrolled walk stays small.
+__device__ __noinline__ bool tail_pair_nl(u64 w1, u64 w2, const ZigDev& z) { return tail_pair_accept(w1, w2, z); }
+template <bool kNormal>
+__device__ __noinline__ bool wedge_nl(u64 r, int i, u64 u2, const ZigDev& z) { return wedge_accept<kNormal>(r, i, u2, z); }
+
+struct LeanTab {
+  unsigned khi[256];   // top 32 bits of the 52/53-bit fast-accept bound k_i
+  double w[256];       // w_i
+};
+
+// RN(r w) for 0 <= r < 2^53 with one fused multiply-add: D = 2^52 + (r mod
+// 2^52) is exact, and D w - 2^52 w = (r mod 2^52) w exactly, so
+// fma(D, w, -2^52 w) rounds the exact product once; for r >= 2^52, D = r and
+// the addend is zero.  Same value as the definition's single rounding.
+// -2^52 w is formed on the bits of w (positive, normal, far from overflow):
+// exponent + 52 and the sign bit, one integer add on the high word.
+__device__ __forceinline__ double mul_rn_fma(u64 r, double w) {
+  const double D = __longlong_as_double((long long)(0x4330000000000000ull | (r & M52)));
+  const double c = __longlong_as_double(__double_as_longlong(w) + (long long)0x8340000000000000ull);
+  return __fma_rn(D, w, (r >> 52) ? 0.0 : c);
+}
+
+// Normal ziggurat (Sec. 3.1): bits 0-7 strip, bit 8 sign, bits 9-60 r.
+struct LeanNormal {
+  static constexpr bool kSync = true;
+  static constexpr int kWhich = 0;
+  static constexpr int kKShift = 20;
+  static constexpr int kG = 8, kS = 24;    // tails may overhang a seam by several words
+  static constexpr bool kTailPairs = true;
+  typedef double out_t;
+  __device__ static __forceinline__ bool fast_exact(u64 u, const ZigDev& z) { return ((u >> 9) & M52) < z.k[u & 0xff]; }
+  __device__ static __forceinline__ bool fast(u64 u, const LeanTab& tb, const ZigDev& z) {
+    const unsigned rh = (unsigned)(u >> 29), kh = tb.khi[u & 0xff];
+    if (rh != kh) return rh < kh;
+    return fast_exact(u, z);
+  }
+  __device__ static __forceinline__ double value(u64 u, const LeanTab& tb, const SampArgs&) {
+    const double x = mul_rn_fma((u >> 9) & M52, tb.w[u & 0xff]);
+    return __longlong_as_double(__double_as_longlong(x) ^ (long long)((u >> 8 & 1) << 63));
+  }
+  __device__ static __forceinline__ bool wedge(u64 u0, u64 u1, const ZigDev& z) {
+    return wedge_nl<true>((u0 >> 9) & M52, (int)(u0 & 0xff), u1, z);
+  }
+  template <class E>
+  __device__ static __forceinline__ int len(u64 u, const E& g, const LeanTab& tb, const ZigDev& z) {
+    if (fast(u, tb, z)) return 1;
+    if ((u & 0xff) != 0) return 2;
+    E h = g;
+    for (int k = 1; k <= kTailPairsMax; ++k) {
+      u64 a = h.next(), b = h.next();
+      if (tail_pair_nl(a, b, z)) return 1 + 2 * k;
+    }
+    return 1 << 20;
+  }
+};
+
+// Exponential ziggurat (Sec. 3.1): bits 0-7 strip, bits 8-60 r; the tail
+// takes one more word and always accepts, so every candidate is 1 or 2 words
+// and a sync window of 2 suffices.
+struct LeanExp {
+  static constexpr bool kSync = true;
+  static constexpr int kWhich = 1;
+  static constexpr int kKShift = 21;
+  static constexpr int kG = 2, kS = 24;
+  static constexpr bool kTailPairs = false;
+  typedef double out_t;
+  __device__ static __forceinline__ bool fast_exact(u64 u, const ZigDev& z) { return ((u >> 8) & M53) < z.k[u & 0xff]; }
+  __device__ static __forceinline__ bool fast(u64 u, const LeanTab& tb, const ZigDev& z) {
+    const unsigned rh = (unsigned)(u >> 29), kh = tb.khi[u & 0xff];
+    if (rh != kh) return rh < kh;
+    return fast_exact(u, z);
+  }
+  __device__ static __forceinline__ double value(u64 u, const LeanTab& tb, const SampArgs&) {
+    return mul_rn_fma((u >> 8) & M53, tb.w[u & 0xff]);
+  }
+  __device__ static __forceinline__ bool wedge(u64 u0, u64 u1, const ZigDev& z) {
+    return wedge_nl<false>((u0 >> 8) & M53, (int)(u0 & 0xff), u1, z);
+  }
+  template <class E>
+  __device__ static __forceinline__ int len(u64 u, const E&, const LeanTab& tb, const ZigDev& z) {
+    return fast(u, tb, z) ? 1 : 2;
+  }
+};
+
+// Lemire (Sec. 3.2): one word per attempt, no seams to synchronise.
+struct LeanBounded {
+  static constexpr bool kSync = false;
+  static constexpr int kWhich = 0;
+  static constexpr int kKShift = 20;
+  static constexpr int kG = 0, kS = 0;
+  static constexpr bool kTailPairs = false;
+  typedef u64 out_t;
+  __device__ static __forceinline__ bool fast_exact(u64, const ZigDev&) { return true; }
+  __device__ static __forceinline__ u64 value(u64 u, const LeanTab&, const SampArgs& a) {
+    return __umul64hi(u, a.m);
+  }
+  template <class E>
+  __device__ static __forceinline__ int len(u64, const E&, const LeanTab&, const ZigDev&) { return 1; }
+};
+
+constexpr int kLPend = 8;        // queued wedge tests per lane and chunk
+constexpr int kTileTails = 64;   // tail records per tile (mean ~9 for the normal)
+
+// Chain state of pass 1 for one thread.
+struct LeanChain {
+  int st;        // 0 expect a candidate, 1 wedge U word, 2/3 normal tail pair words, 4 exponential tail word
+  int pp;        // position of the pending candidate's first word
+  int np;        // queued wedge tests
+  u64 pu0, pw1;  // pending candidate's first word; first word of the current tail pair
+};
+
+// The uncommon steps of the pass-1 walk: a candidate that is not a fast
+// accept (or whose top bits tie with the bound), and every word inside a
+// multi-word candidate.  Output positions are marked in the bitmap (`mw` is
+// mask word b, still in a register; earlier words are in shared memory).
+template <int NT, class S>
+__device__ __forceinline__ void lean_rare(u64 u, int p, int b, unsigned& mw, LeanChain& c, const ZigDev& z,
+                                          unsigned (*msk)[NT], u64* queue, u64 (*tails)[3], int* ntails,
+                                          Ctrl* ctrl, u64 k) {
+  const int t = threadIdx.x;
+  auto mark = [&](int q) {
+    if ((q >> 5) == b) mw |= 1u << (q & 31);
+    else msk[q >> 5][t] |= 1u << (q & 31);
+  };
+  auto tail_rec = [&](u64 w1) {
+    int slot = atomicAdd(ntails, 1);
+    if (slot < kTileTails) {
+      tails[slot][0] = c.pu0;
+      tails[slot][1] = w1;
+      tails[slot][2] = ((u64)t << 32) | (unsigned)c.pp;
+    } else {
+      set_err(ctrl, E_OVERFLOW, k);
+    }
+  };
+  if (c.st == 0) {
+    if (S::fast_exact(u, z)) { mark(p); return; }   // top bits tied with the bound
+    c.pu0 = u;
+    c.pp = p;
+    c.st = (u & 0xff) ? 1 : (S::kTailPairs ? 2 : 4);
+  } else if (c.st == 1) {
+    c.st = 0;
+    const u64 u1 = (u & ~0x7ffull) | (u64)c.pp;   // U uses bits 11-63: the position rides in the low bits
+    if (c.np < kLPend) {
+      queue[(c.np * NT + t) * 2] = c.pu0;
+      queue[(c.np * NT + t) * 2 + 1] = u1;
+      ++c.np;
+    } else if (S::wedge(c.pu0, u1, z)) {
+      mark(c.pp);
+    }
+  } else if (c.st == 4) {
+    c.st = 0;
+    mark(c.pp);
+    tail_rec(u);
+  } else if (c.st == 2) {
+    c.pw1 = u;
+    c.st = 3;
+  } else if (tail_pair_nl(c.pw1, u, z)) {
+    c.st = 0;
+    mark(c.pp);
+    tail_rec(c.pw1);
+  } else {
+    c.st = 2;
+  }
+}
+
+// One word of the walk: the common case (a fast accept) sets one bit.
+template <int NT, class S>
+__device__ __forceinline__ void lean_step(u64 u, int p, int b, unsigned& mw, LeanChain& c, const LeanTab& tb,
+                                          const ZigDev& z, unsigned (*msk)[NT], u64* queue, u64 (*tails)[3],
+                                          int* ntails, Ctrl* ctrl, u64 k) {
+  const unsigned rh = (unsigned)(u >> 29), kh = tb.khi[u & 0xff];
+  if (c.st == 0 && rh < kh) mw |= 1u << (p & 31);
+  else lean_rare<NT, S>(u, p, b, mw, c, z, msk, queue, tails, ntails, ctrl, k);
+}
+
+// Staged rows -> output: row r of the warp holds lane r's `cnt` (<= 16)
+// consecutive outputs starting at tile-relative output `off`; each store
+// instruction writes two rows, 16 lanes each.  `lim` = outputs left in the
+// fill from the tile's first output.
+template <class OT>
+__device__ __forceinline__ void flush_rows16(OT* __restrict__ outb, const OT* rows, int off, int cnt, int lim) {
+  const int lane = threadIdx.x & 31;
+  const int half = lane >> 4, col = lane & 15;
+#pragma unroll 4
+  for (int r = 0; r < 32; r += 2) {
+    const int rr = r + half;
+    const int o = __shfl_sync(0xffffffffu, off, rr);
+    const int c = min(__shfl_sync(0xffffffffu, cnt, rr), lim - o);
+    if (col < c) outb[o + col] = rows[rr * kRow + col];
+  }
+}
+
+template <int NT, int C, class E, class S>
+__global__ void __launch_bounds__(NT, 8) k_lean(FillArgs a) {
+  static_assert(C % 32 == 0, "chunks are whole mask words");
+  typedef typename S::out_t OT;
+  static_assert(sizeof(OT) == 8, "staging holds 8-byte outputs");
+  constexpr int T = NT * C;
+  constexpr int kMW = C / 32 + 1;   // mask words: the chunk and the overhang into the next one
+  constexpr int kStageW = (NT / 32) * 32 * kRow;
+  constexpr int kQueueW = NT * kLPend * 2;
+  constexpr int kBufW = kStageW > kQueueW ? kStageW : kQueueW;
+  __shared__ __align__(16) u64 sbuf[kBufW];   // pass 1: wedge queue; pass 2: staging rows
+  __shared__ unsigned msk[kMW][NT];
+  __shared__ LeanTab tb;
+  __shared__ u64 tails[kTileTails][3];
+  __shared__ int ntails[2];   // by tile parity: reset one tile after use, behind a barrier
+  __shared__ int wsum[32];
+  __shared__ int misc[8];
+  __shared__ u64 sh4[4];
+  const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+  const ZigDev& z = g_zig[S::kWhich];
+  for (int i = t; i < 256; i += NT) {
+    tb.khi[i] = (unsigned)(z.k[i] >> S::kKShift);
+    tb.w[i] = z.w[i];
+  }
+  if (t == 0) { ntails[0] = 0; ntails[1] = 0; }
+  __syncthreads();
+  OT* out = (OT*)a.out;
+  OT* stage = (OT*)sbuf + wid * 32 * kRow;
+  E e;
+  e.init_tile(a.eng, blockIdx.x, t, sh4);
+
+  int par = 0;
+  for (u64 k = blockIdx.x; k < a.n_tiles; k += gridDim.x, par ^= 1) {
+    if (ld_volatile(&a.ctrl->done_tile) < k) break;
+    int* nts = &ntails[par];
+    // ---------------- pass 1: sync point, chain walk with output bitmap
+    int s = 0, endp = C;
+    bool ok = true;
+    if (S::kSync && !(k == 0 && t == 0)) {
+      E h = e;
+      int reach = 0;
+      s = -1;
+      for (int q = 0; q < S::kG + S::kS; ++q) {
+        if (q >= S::kG && reach <= q) { s = q; break; }
+        u64 u = h.next();
+        reach = max(reach, q + S::len(u, h, tb, z));
+      }
+      if (s < 0) { set_err(a.ctrl, E_NOSYNC, k); ok = false; s = 0; }
+    }
+    LeanChain c;
+    c.st = 0; c.pp = 0; c.np = 0; c.pu0 = 0; c.pw1 = 0;
+    E g = e;
+    if constexpr (!S::kSync) {
+      for (int b = 0; b < C / 32; ++b) {
+        unsigned mw = 0;
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const u64 u = g.next();
+          mw |= (unsigned)(u * a.sp.m >= a.sp.thresh) << j;
+        }
+        msk[b][t] = mw;
+      }
+      msk[kMW - 1][t] = 0;
+    } else {
+      {  // first mask word: positions before the sync point belong to the previous chain
+        unsigned mw = 0;
+#pragma unroll 4
+        for (int j = 0; j < 32; ++j) {
+          const u64 u = g.next();
+          if (j >= s) lean_step<NT, S>(u, j, 0, mw, c, tb, z, msk, sbuf, tails, nts, a.ctrl, k);
+        }
+        msk[0][t] = mw;
+      }
+      for (int b = 1; b < C / 32; ++b) {
+        unsigned mw = 0;
+#pragma unroll 4
+        for (int j = 0; j < 32; ++j)
+          lean_step<NT, S>(g.next(), b * 32 + j, b, mw, c, tb, z, msk, sbuf, tails, nts, a.ctrl, k);
+        msk[b][t] = mw;
+      }
+      // the next chunk's sync point by the same rule, while the chain runs on
+      {
+        unsigned mw = 0;
+        int reach = C;
+        endp = -1;
+        for (int q = C; q < C + S::kG + S::kS; ++q) {
+          if (q - C >= S::kG && reach <= q) { endp = q; break; }
+          u64 u = g.next();
+          reach = max(reach, q + S::len(u, g, tb, z));
+          lean_step<NT, S>(u, q, C / 32, mw, c, tb, z, msk, sbuf, tails, nts, a.ctrl, k);
+        }
+        msk[kMW - 1][t] = mw;
+        if (endp < 0) { set_err(a.ctrl, E_NOSYNC, k); ok = false; endp = C; }
+        else if (c.st != 0) { set_err(a.ctrl, E_LANDING, k); ok = false; }
+      }
+      // queued wedge tests, all lanes together
+      for (int j = 0; j < c.np; ++j) {
+        const u64 u0 = sbuf[(j * NT + t) * 2], u1 = sbuf[(j * NT + t) * 2 + 1];
+        if (S::wedge(u0, u1, z)) {
+          const int q = (int)(u1 & 0x7ff);
+          msk[q >> 5][t] |= 1u << (q & 31);
+        }
+      }
+    }
+    int cnt = 0;
+#pragma unroll
+    for (int w = 0; w < kMW; ++w) cnt += __popc(msk[w][t]);
+    if (!ok) cnt = 0;
+    // ---------------- offsets
+    const int off = block_exclusive_scan<NT>(cnt, wsum, &misc[1]);   // also orders the queue reads before staging
+    if (t < 32) {
+      unsigned long long ex = lookback_warp(a.tile_status, k, (unsigned long long)misc[1], a.ctrl);
+      if (t == 0) {
+        misc[2] = (int)(ex & 0x7fffffff);
+        misc[3] = (int)(ex >> 31);
+        misc[4] = (ex == ~0ull);
+      }
+    }
+    __syncthreads();
+    if (misc[4]) break;
+    const u64 base = (u64)(unsigned)misc[2] | ((u64)(unsigned)misc[3] << 31);
+    const u64 chunk0 = k * (u64)T + (u64)t * C;
+    const u64 my0 = base + (u64)off;
+    if (t == NT - 1 && k + 1 == a.n_tiles && base + (u64)misc[1] < a.n) {
+      // ran out of tiles: report where the chain continues
+      a.ctrl->total = base + (u64)misc[1];
+      a.ctrl->next_pos = chunk0 + (u64)endp;
+      a.ctrl->last_tile = k;
+    }
+    // tail outputs of this thread: output index from the bitmap rank
+    const int nt_tile = min(*nts, kTileTails);
+    for (int j = 0; j < nt_tile; ++j) {
+      const u64 tp = tails[j][2];
+      if ((int)(tp >> 32) != t) continue;
+      const int p = (int)(unsigned)tp;
+      int rank = 0;
+      for (int w = 0; w < (p >> 5); ++w) rank += __popc(msk[w][t]);
+      rank += __popc(msk[p >> 5][t] & ((1u << (p & 31)) - 1u));
+      const u64 gi = my0 + (u64)rank;
+      if (gi < a.n) {
+        unsigned long long qi = atomicAdd(&a.ctrl->n_tail, 1ull);
+        if (qi < a.tail_cap) a.tailq[qi] = TailEntry{gi, tails[j][0], tails[j][1]};
+        else set_err(a.ctrl, E_OVERFLOW, k);
+      }
+    }
+    // the thread holding output n-1 records where the stream continues
+    if (ok && cnt > 0 && my0 <= a.n - 1 && a.n - 1 < my0 + (u64)cnt) {
+      int want = (int)(a.n - 1 - my0), p = 0;
+      for (int w = 0; w < kMW; ++w) {
+        const unsigned m = msk[w][t];
+        const int pc = __popc(m);
+        if (want < pc) {
+          unsigned mm = m;
+          for (int r = 0; r < want; ++r) mm &= mm - 1u;
+          p = w * 32 + __ffs(mm) - 1;
+          break;
+        }
+        want -= pc;
+      }
+      E h = e;
+      for (int q = 0; q < p; ++q) (void)h.next();
+      const u64 u = h.next();
+      a.ctrl->next_pos = chunk0 + (u64)(p + S::len(u, h, tb, z));
+      atomicMin(&a.ctrl->done_tile, k);
+    }
+    // ---------------- pass 2: regenerate, evaluate marked words, stage, write
+    if (base < a.n) {
+      E g2 = e;
+      const int nblk = ok ? (endp + 31) >> 5 : 0;
+      const int maxblk = __reduce_max_sync(0xffffffffu, nblk);
+      OT* outb = out + base;
+      const u64 room = a.n - base;
+      const int lim = room < (u64)0x7fffffff ? (int)room : 0x7fffffff;
+      int myoff = off;
+      OT* row = stage + lane * kRow;
+      for (int hb = 0; hb < 2 * maxblk; ++hb) {   // half blocks of 16 words
+        int ns = 0;
+        if ((hb >> 1) < nblk) {
+          const unsigned m = msk[hb >> 1][t] >> ((hb & 1) * 16);
+#pragma unroll 8
+          for (int j = 0; j < 16; ++j) {
+            const u64 u = g2.next();
+            if ((m >> j) & 1u) {
+              row[ns] = S::value(u, tb, a.sp);
+              ++ns;
+            }
+          }
+        }
+        __syncwarp();
+        flush_rows16<OT>(outb, stage, myoff, ns, lim);
+        __syncwarp();
+        myoff += ns;
+      }
+    }
+    __syncthreads();
+    if (t == 0) *nts = 0;   // next used two tiles on, after another barrier
+    e.advance(a.eng);
+  }
+}
