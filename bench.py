@@ -30,6 +30,17 @@ METRIC = "variates/s (single-stream exact-sequence fills, 3 engines x {normal, e
 WORKLOAD = "single-stream fills: engines {xoshiro256++, PCG64-DXSM, Philox4x32-10}, seed 2024, n=2^28 each of normal, exp, bounded m=6, 1e9+7, 2^63+1"
 
 
+# DRAM bytes (read + write) per launch of the fill kernel at n = 2^28, from
+# one ncu capture at n = 2^26 scaled by outputs (profiles/k_lean_*_n2e26.md).
+# Null for any kernel without a capture of its current version.
+TRAFFIC = {
+    "philox4x32_10/normal": 2129293312,
+    "philox4x32_10/bounded:9223372036854775809": 2277019648,
+    "xoshiro256pp/normal": 2197997568,
+    "xoshiro256pp/exp": 2141146112,
+}
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -194,7 +205,8 @@ def run_gpu(args):
     bytes_alg = 8.0 * N_FILL
     achieved = bytes_alg / (avg_ms / 1e3) / 1e9
     roof = {"bound": "hbm", "kernel": key, "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"],
-            "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": None,
+            "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4),
+            "traffic": TRAFFIC.get(key) if N_FILL == 1 << 28 else None,
             "peak_source": peak_kind, "per_fill_ms": {k: round(v / args.steps, 4) for k, v in per_fill_ms.items()}}
 
     # ---- end to end through the public API with host buffers: each fill's

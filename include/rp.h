@@ -160,8 +160,9 @@ rp_status rp_beta_grad(const double* d_z, double a, double b, const double* d_g,
 rp_status rp_seed_state(rp_engine engine, uint64_t seed, uint64_t stream, uint64_t* words, int* nw);
 
 /* Advance state words (layout as above) by delta = delta_hi 2^64 + delta_lo
- * words: GF(2) jump polynomial for xoshiro (Sec. 4.4), LCG skip-ahead for
- * PCG64 (Sec. 2.3), counter offset for Philox. */
+ * words: for xoshiro the product of the binary powers T^(2^j) of its GF(2)
+ * transition matrix (the same map as the jump polynomial of Sec. 4.4), LCG
+ * skip-ahead for PCG64 (Sec. 2.3), counter offset for Philox (delta even). */
 rp_status rp_jump_state(rp_engine engine, uint64_t* words, uint64_t delta_hi, uint64_t delta_lo);
 
 /* Message of the last failed call on this host thread ("" if none). */
