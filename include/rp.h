@@ -107,6 +107,75 @@ rp_status rp_fill_beta(rp_engine engine, uint64_t seed, uint64_t stream, uint64_
                        size_t n, double a, double b, double* d_out, void* cuda_stream);
 
 /* ---------------------------------------------------------------------
+ * Distributions by code, fills from explicit state, substreams and
+ * batched fills.
+ * ------------------------------------------------------------------- */
+typedef enum {
+  RP_DIST_U64 = 0,       /* raw words */
+  RP_DIST_UNIFORM = 1,   /* 53-bit U[0,1) */
+  RP_DIST_BOUNDED = 2,   /* [0, m), m = 0 full range */
+  RP_DIST_NORMAL = 3,
+  RP_DIST_EXP = 4,
+  RP_DIST_GAMMA = 5,     /* alpha = p0 */
+  RP_DIST_BETA = 6       /* a = p0, b = p1 */
+} rp_dist;
+
+/* Fill n variates of `dist` from a stream given by its state words (the
+ * engine before word 0, layout of rp_seed_state), starting at word *pos;
+ * *pos is set to the next unused word.  Same values as the seeded fills of
+ * the same stream.  d_out: device array of n 8-byte elements (uint64 for
+ * u64/bounded, double otherwise). */
+rp_status rp_fill_state(rp_engine engine, const uint64_t* words, uint64_t* pos, int dist, size_t n,
+                        double p0, double p1, uint64_t m, void* d_out, void* cuda_stream);
+
+/* State words of substream s of base_seed, the paper's recipe for parallel
+ * simulations (Sec. 2.3, "duplicate, then jump or set the stream"): the
+ * base state is seeded from base_seed with no spawn key; xoshiro256++ jumps
+ * it by s * 2^128 words, Philox4x32-10 sets its key to s, PCG64-DXSM sets
+ * its increment to 2 s + 1.  words must hold 4 entries; *nw receives the
+ * count used. */
+rp_status rp_substream_state(rp_engine engine, uint64_t base_seed, uint64_t s, uint64_t* words, int* nw);
+
+/* One request of a batch: n variates of `dist` from substream `stream`. */
+typedef struct {
+  uint64_t stream;   /* substream index s */
+  int32_t dist;      /* rp_dist */
+  int32_t reserved;  /* must be 0 */
+  uint64_t n;        /* variates (0: nothing) */
+  double p0, p1;     /* gamma: alpha = p0; beta: a = p0, b = p1 with a != b */
+  uint64_t m;        /* bounded: modulus (0: full range) */
+  void* d_out;       /* device array of n 8-byte elements, 8-byte aligned */
+  uint64_t pos;      /* first word of the substream to use */
+} rp_request;
+
+/* A batch plan: every request of a fixed set, served by one CUDA-graph
+ * launch of persistent kernels (one per kernel class: one-word, ziggurat and
+ * bounded, gamma and beta) that claim (request, tile) work items.  Not in
+ * the paper, whose parallel use is one generator object per simulation.
+ *   reqs      nreq requests (copied; output pointers must stay valid)
+ *   autotune  1: time the schedules (item order, class concurrency, words
+ *             per thread) on this request set and keep the fastest;
+ *             0: the default schedule
+ *   plan      receives the plan (owned by the caller; rp_batch_plan_destroy)
+ * Beta requests need a != b (equal shapes: rp_fill_beta or rp_fill_state).
+ * Tuning runs the batch several times; outputs are identical each time. */
+typedef struct rp_batch_plan rp_batch_plan;
+rp_status rp_batch_plan_create(const rp_request* reqs, size_t nreq, rp_engine engine, uint64_t base_seed,
+                               int autotune, rp_batch_plan** plan, void* cuda_stream);
+/* Runs the plan on cuda_stream and returns after it completed.  Every
+ * request is filled from its own start word; next_pos (nullable, nreq
+ * entries) receives each request's next unused word. */
+rp_status rp_batch_plan_run(rp_batch_plan* plan, uint64_t* next_pos, void* cuda_stream);
+/* Schedule chosen (bit 0 item order by size, bit 1 classes serialised,
+ * bit 2 128 words per thread), its tuned time in ms (0 if not tuned) and the
+ * number of work items. */
+rp_status rp_batch_plan_info(const rp_batch_plan* plan, int* schedule, double* tuned_ms, uint64_t* items);
+rp_status rp_batch_plan_destroy(rp_batch_plan* plan);
+/* One-shot: create (default schedule), run, write each request's next
+ * unused word back into reqs[i].pos, destroy. */
+rp_status rp_batch_run(rp_request* reqs, size_t nreq, rp_engine engine, uint64_t base_seed, void* cuda_stream);
+
+/* ---------------------------------------------------------------------
  * Normal fill on fixed scratch (Philox4x32-10 only).  Randompack has no
  * counterpart: this entry point exists for callers that must not allocate
  * device memory -- code running inside a device allocator's own callbacks

@@ -130,6 +130,12 @@ def substream(engine, base_seed, s):
     return g
 
 
+def jump(g, n):
+    """Advance a generator by n words (or_jump)."""
+    lib().or_jump(ctypes.byref(g), (n >> 64) & (2**64 - 1), n & (2**64 - 1))
+    return g
+
+
 def state_words(g):
     return [int(x) for x in g.s]
 

@@ -14,6 +14,7 @@ import os
 import torch
 
 XOSHIRO256PP, PCG64DXSM, PHILOX4X32_10 = 1, 2, 3
+DISTS = {"u64": 0, "uniform": 1, "bounded": 2, "normal": 3, "exp": 4, "gamma": 5, "beta": 6}
 ENGINES = {"xoshiro256pp": XOSHIRO256PP, "pcg64dxsm": PCG64DXSM, "philox4x32_10": PHILOX4X32_10}
 NO_STREAM = (1 << 64) - 1
 
@@ -22,6 +23,13 @@ LIB_PATH = os.path.join(_HERE, "librp.so")
 
 STATUS = {0: "RP_OK", -1: "RP_ERR_NULL", -2: "RP_ERR_PARAM", -3: "RP_ERR_ENGINE", -4: "RP_ERR_CUDA",
           -5: "RP_ERR_TIMEOUT", -6: "RP_ERR_NOMEM", -7: "RP_ERR_INTERNAL", -8: "RP_ERR_SEED"}
+
+
+class Request(ctypes.Structure):
+    """rp_request of include/rp.h: n variates of `dist` from substream `stream`."""
+    _fields_ = [("stream", ctypes.c_uint64), ("dist", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("n", ctypes.c_uint64), ("p0", ctypes.c_double), ("p1", ctypes.c_double),
+                ("m", ctypes.c_uint64), ("d_out", ctypes.c_void_p), ("pos", ctypes.c_uint64)]
 
 
 class RPError(RuntimeError):
@@ -55,6 +63,13 @@ def lib():
             "rp_jump_state": [i32, pu64, u64, u64],
             "rp_ziggurat_tables": [i32, pu64, ctypes.POINTER(dbl), ctypes.POINTER(dbl), ctypes.POINTER(dbl)],
             "rp_gamma_grad": [vp, dbl, vp, sz, vp, ctypes.POINTER(dbl), vp],
+            "rp_fill_state": [i32, pu64, pu64, i32, sz, dbl, dbl, u64, vp, vp],
+            "rp_substream_state": [i32, u64, u64, pu64, ctypes.POINTER(i32)],
+            "rp_batch_plan_create": [ctypes.POINTER(Request), sz, i32, u64, i32, ctypes.POINTER(vp), vp],
+            "rp_batch_plan_run": [vp, pu64, vp],
+            "rp_batch_plan_info": [vp, ctypes.POINTER(i32), ctypes.POINTER(dbl), pu64],
+            "rp_batch_plan_destroy": [vp],
+            "rp_batch_run": [ctypes.POINTER(Request), sz, i32, u64, vp],
             "rp_beta_grad": [vp, dbl, dbl, vp, sz, vp, vp, ctypes.POINTER(dbl), ctypes.POINTER(dbl), vp],
         }
         for name, args in sig.items():
@@ -215,6 +230,84 @@ class Beta(torch.autograd.Function):
         (z,) = ctx.saved_tensors
         ga, gb = rp_beta_grad(z, ctx.ab[0], ctx.ab[1], grad_z.to(torch.float64).contiguous())
         return torch.tensor(ga, dtype=torch.float64), torch.tensor(gb, dtype=torch.float64), None, None, None, None, None
+
+
+def _dist(d):
+    return DISTS[d] if isinstance(d, str) else int(d)
+
+
+def rp_fill_state(engine, words, pos, dist, out, p0=0.0, p1=0.0, m=0, cuda_stream=None):
+    """Fill `out` from a stream given by its state words (before word 0),
+    starting at word `pos`; returns the next unused word."""
+    w = (ctypes.c_uint64 * 4)(*[int(x) for x in list(words) + [0] * (4 - len(words))])
+    d = _dist(dist)
+    p, n = _out(out, torch.uint64 if d in (0, 2) else torch.float64)
+    cpos = ctypes.c_uint64(pos)
+    _check(lib().rp_fill_state(_engine(engine), w, ctypes.byref(cpos), d, n, float(p0), float(p1), int(m), p,
+                               _stream_handle(cuda_stream)))
+    return cpos.value
+
+
+def rp_substream_state(engine, base_seed, s):
+    """State words of substream s of base_seed (Sec. 2.3 recipe)."""
+    w = (ctypes.c_uint64 * 4)()
+    nw = ctypes.c_int()
+    _check(lib().rp_substream_state(_engine(engine), base_seed, s, w, ctypes.byref(nw)))
+    return [w[i] for i in range(nw.value)]
+
+
+def make_requests(specs):
+    """Request array from dicts with keys stream, dist, out (CUDA tensor) and
+    optional p0, p1, m, pos."""
+    arr = (Request * len(specs))()
+    for i, sp in enumerate(specs):
+        out = sp["out"]
+        if not isinstance(out, torch.Tensor) or not out.is_cuda or out.element_size() != 8 or not out.is_contiguous():
+            raise TypeError("request outputs must be contiguous 8-byte CUDA tensors")
+        arr[i] = Request(int(sp["stream"]), _dist(sp["dist"]), 0, out.numel(), float(sp.get("p0", 0.0)),
+                         float(sp.get("p1", 0.0)), int(sp.get("m", 0)), out.data_ptr() if out.numel() else None,
+                         int(sp.get("pos", 0)))
+    return arr
+
+
+class BatchPlan:
+    """A batch plan (rp_batch_plan_*): one CUDA-graph launch serves every
+    request; run() returns each request's next unused word."""
+
+    def __init__(self, reqs, engine, base_seed, autotune=False, cuda_stream=None):
+        self._reqs = reqs
+        self.n = len(reqs)
+        h = ctypes.c_void_p()
+        _check(lib().rp_batch_plan_create(reqs, self.n, _engine(engine), base_seed, int(bool(autotune)),
+                                          ctypes.byref(h), _stream_handle(cuda_stream)))
+        self._h = h
+
+    def run(self, cuda_stream=None):
+        np_ = (ctypes.c_uint64 * max(self.n, 1))()
+        _check(lib().rp_batch_plan_run(self._h, np_, _stream_handle(cuda_stream)))
+        return [np_[i] for i in range(self.n)]
+
+    def info(self):
+        sch, ms, it = ctypes.c_int(), ctypes.c_double(), ctypes.c_uint64()
+        _check(lib().rp_batch_plan_info(self._h, ctypes.byref(sch), ctypes.byref(ms), ctypes.byref(it)))
+        return {"schedule": sch.value, "tuned_ms": ms.value, "items": it.value}
+
+    def close(self):
+        if self._h:
+            lib().rp_batch_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def rp_batch_run(reqs, engine, base_seed, cuda_stream=None):
+    """One-shot batch: fills every request; returns the next unused words."""
+    _check(lib().rp_batch_run(reqs, len(reqs), _engine(engine), base_seed, _stream_handle(cuda_stream)))
+    return [reqs[i].pos for i in range(len(reqs))]
 
 
 def rp_seed_state(engine, seed, stream=NO_STREAM):

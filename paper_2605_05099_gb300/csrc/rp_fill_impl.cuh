@@ -227,30 +227,58 @@ __device__ __forceinline__ void flush_rows(OT* __restrict__ out, const OT* row_b
   }
 }
 
+// ------------------------------------------------------------------ batches
+static_assert(sizeof(FillArgs) % 8 == 0, "request arguments are copied as words");
+
+// Claims the CTA's next work item and copies its request's arguments into
+// shared memory.  Returns false once the list is exhausted.  All threads of
+// the CTA call it; it synchronises the CTA.
+__device__ __forceinline__ bool batch_claim(const BatchArgs& b, FillArgs& fa, BatchItem& bi,
+                                            unsigned long long* slot) {
+  if (threadIdx.x == 0) *slot = atomicAdd(b.next_item, 1ull);
+  __syncthreads();
+  const unsigned long long it = *slot;
+  if (it >= b.n_items) return false;
+  bi = b.items[it];
+  const u64* src = (const u64*)&b.reqs[bi.req];
+  u64* dst = (u64*)&fa;
+  for (int i = threadIdx.x; i < (int)(sizeof(FillArgs) / 8); i += blockDim.x) dst[i] = src[i];
+  __syncthreads();
+  return true;
+}
+
 #include "rp_lean.cuh"
 
 // ------------------------------------------------------------------ kernels
+// One tile of a one-word-per-variate fill: chunk words stream straight to
+// the output through the warp's staging rows.
 template <int NT, int C, class E, class S>
-__global__ void __launch_bounds__(NT) k_onepw(FillArgs a) {
-  // one word per variate: chunk words stream straight to the output
+__device__ __forceinline__ void onepw_tile(const FillArgs& a, u64 k, const E& e, typename S::out_t* stage_w) {
   typedef typename S::out_t OT;
   constexpr int T = NT * C;
+  const int t = threadIdx.x, lane = t & 31;
+  OT* out = (OT*)a.out;
+  E g = e;
+  const u64 base = k * (u64)T + (u64)t * C;
+  for (int j0 = 0; j0 < C; j0 += kStage) {
+#pragma unroll
+    for (int j = 0; j < kStage; ++j) stage_w[lane * kRow + j] = S::value1(g.next(), a.sp);
+    __syncwarp();
+    flush_rows<OT>(out, stage_w, base + j0, kStage, a.n);
+    __syncwarp();
+  }
+}
+
+template <int NT, int C, class E, class S>
+__global__ void __launch_bounds__(NT) k_onepw(FillArgs a) {
+  typedef typename S::out_t OT;
   __shared__ __align__(16) OT stage[NT / 32][32 * kRow];
   __shared__ u64 sh4[4];
-  const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
-  OT* out = (OT*)a.out;
+  const int t = threadIdx.x, wid = t >> 5;
   E e;
   e.init_tile(a.eng, blockIdx.x, t, sh4);
   for (u64 k = blockIdx.x; k < a.n_tiles; k += gridDim.x) {
-    E g = e;
-    u64 base = k * (u64)T + (u64)t * C;
-    for (int j0 = 0; j0 < C; j0 += kStage) {
-#pragma unroll
-      for (int j = 0; j < kStage; ++j) stage[wid][lane * kRow + j] = S::value1(g.next(), a.sp);
-      __syncwarp();
-      flush_rows<OT>(out, stage[wid], base + j0, kStage, a.n);
-      __syncwarp();
-    }
+    onepw_tile<NT, C, E, S>(a, k, e, stage[wid]);
     e.advance(a.eng);
   }
 }
@@ -301,131 +329,178 @@ __device__ int merge_search(E& g, int limit, const SampArgs& sp, const ZigDev& z
   return -1;
 }
 
+template <int NT>
+struct MergeSmem {
+  __align__(16) u64 stage[NT / 32][32 * (kRecS + 1) * kRecW];
+  int wsum[32];
+  int misc[8];
+  u64 sh4[4];
+};
+
+// One tile of a merge-seam fill (gamma, beta).  Returns false when the fill
+// needs no further tiles (or a device check failed): the caller stops.
 template <int NT, int C, class E, class S>
-__global__ void __launch_bounds__(NT) k_merge(FillArgs a) {
+__device__ bool merge_tile(const FillArgs& a, u64 k, const E& e, MergeSmem<NT>& sm) {
   constexpr int T = NT * C;
-  __shared__ __align__(16) u64 stage[NT / 32][32 * (kRecS + 1) * kRecW];
-  __shared__ int wsum[32];
-  __shared__ int misc[8];
-  __shared__ u64 sh4[4];
   const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
   const ZigDev& z = g_zig[0];   // read through L1 (keeps shared memory small)
   double* out = (double*)a.out;
-  E e;
-  e.init_tile(a.eng, blockIdx.x, t, sh4);
-
-  for (u64 k = blockIdx.x; k < a.n_tiles; k += gridDim.x) {
-    if (ld_volatile(&a.ctrl->done_tile) < k) break;
-    // ---------------- pass 1: merge point, walk, count, next merge point
-    E g = e;
-    int sig = 0, cnt = 0, endp = -1;
-    bool ok = true;
-    if (!(k == 0 && t == 0)) {
-      sig = merge_search<E, S>(g, C, a.sp, z, nullptr, nullptr);
-      if (sig < 0) ok = false;   // no merge point in this chunk: no segment
+  // one reader, so that every thread takes the same branch
+  if (t == 0) sm.misc[5] = ld_volatile(&a.ctrl->done_tile) < k;
+  __syncthreads();
+  if (sm.misc[5]) return false;
+  // ---------------- pass 1: merge point, walk, count, next merge point
+  E g = e;
+  int sig = 0, cnt = 0, endp = -1;
+  bool ok = true;
+  if (!(k == 0 && t == 0)) {
+    sig = merge_search<E, S>(g, C, a.sp, z, nullptr, nullptr);
+    if (sig < 0) ok = false;   // no merge point in this chunk: no segment
+  }
+  typename S::M m;
+  m.reset();
+  if (ok) {
+    for (int p = sig; p < C; ++p) cnt += m.feed(g.next(), a.sp, z);
+    int q = -1, u = 1;
+    for (; u <= kSkipMax; ++u) {
+      q = merge_search<E, S>(g, C, a.sp, z, &m, &cnt);
+      if (q != -1) break;       // else: the own chain has crossed that chunk; try the next
     }
-    typename S::M m;
+    if (q == -1) { set_err(a.ctrl, E_NOSYNC, k); ok = false; }
+    else if (q == -2) { set_err(a.ctrl, E_LANDING, k); ok = false; }
+    else endp = u * C + q;
+  }
+  // ---------------- offsets
+  int off = block_exclusive_scan<NT>(cnt, sm.wsum, &sm.misc[1]);
+  if (t < 32) {
+    unsigned long long ex = lookback_warp(a.tile_status, k, (unsigned long long)sm.misc[1], a.ctrl);
+    if (t == 0) {
+      sm.misc[2] = (int)(ex & 0x7fffffff);
+      sm.misc[3] = (int)(ex >> 31);
+      sm.misc[4] = (ex == ~0ull);
+    }
+  }
+  __syncthreads();
+  if (sm.misc[4]) return false;
+  const u64 base = (u64)(unsigned)sm.misc[2] | ((u64)(unsigned)sm.misc[3] << 31);
+  const u64 chunk0 = k * (u64)T + (u64)t * C;
+  if (k + 1 == a.n_tiles && base + (u64)sm.misc[1] < a.n) {
+    // ran out of tiles: the last segment of the tile ends where the chain continues
+    if (t == 0) sm.sh4[0] = 0;
+    __syncthreads();
+    if (ok) atomicMax((unsigned long long*)&sm.sh4[0], chunk0 + (u64)endp);
+    __syncthreads();
+    if (t == 0) {
+      a.ctrl->total = base + (u64)sm.misc[1];
+      a.ctrl->next_pos = sm.sh4[0];
+      a.ctrl->last_tile = k;
+    }
+  }
+  // ---------------- pass 2: regenerate, stage records, evaluate while writing
+  if (base < a.n) {
+    g = e;
+    for (int q = 0; q < sig; ++q) (void)g.next();
     m.reset();
-    if (ok) {
-      for (int p = sig; p < C; ++p) cnt += m.feed(g.next(), a.sp, z);
-      int q = -1, u = 1;
-      for (; u <= kSkipMax; ++u) {
-        q = merge_search<E, S>(g, C, a.sp, z, &m, &cnt);
-        if (q != -1) break;       // else: the own chain has crossed that chunk; try the next
-      }
-      if (q == -1) { set_err(a.ctrl, E_NOSYNC, k); ok = false; }
-      else if (q == -2) { set_err(a.ctrl, E_LANDING, k); ok = false; }
-      else endp = u * C + q;
-    }
-    // ---------------- offsets
-    int off = block_exclusive_scan<NT>(cnt, wsum, &misc[1]);
-    if (t < 32) {
-      unsigned long long ex = lookback_warp(a.tile_status, k, (unsigned long long)misc[1], a.ctrl);
-      if (t == 0) {
-        misc[2] = (int)(ex & 0x7fffffff);
-        misc[3] = (int)(ex >> 31);
-        misc[4] = (ex == ~0ull);
-      }
-    }
-    __syncthreads();
-    if (misc[4]) break;
-    const u64 base = (u64)(unsigned)misc[2] | ((u64)(unsigned)misc[3] << 31);
-    const u64 chunk0 = k * (u64)T + (u64)t * C;
-    if (k + 1 == a.n_tiles && base + (u64)misc[1] < a.n) {
-      // ran out of tiles: the last segment of the tile ends where the chain continues
-      if (t == 0) sh4[0] = 0;
-      __syncthreads();
-      if (ok) atomicMax((unsigned long long*)&sh4[0], chunk0 + (u64)endp);
-      __syncthreads();
-      if (t == 0) {
-        a.ctrl->total = base + (u64)misc[1];
-        a.ctrl->next_pos = sh4[0];
-        a.ctrl->last_tile = k;
-      }
-    }
-    // ---------------- pass 2: regenerate, stage records, evaluate while writing
-    if (base < a.n) {
-      g = e;
-      for (int q = 0; q < sig; ++q) (void)g.next();
-      m.reset();
-      const u64 my0 = base + (u64)off;
-      int emitted = 0;
-      int p = sig;
-      bool active = ok && cnt > 0;
-      u64* myrow = &stage[wid][lane * (kRecS + 1) * kRecW];
-      while (__any_sync(0xffffffffu, active)) {
-        int ns = 0;
-        while (active && ns < kRecS) {
-          u64 u = g.next();
-          ++p;
-          if (!m.feed(u, a.sp, z)) continue;
-          u64* r = myrow + ns * kRecW;
-          m.record(r);
-          const u64 gi = my0 + emitted + ns;
-          r[7] = 0;
-          if (S::needs_tail(r) && gi < a.n) {
-            unsigned long long qi = atomicAdd(&a.ctrl->n_tail, 1ull);
-            if (qi < a.tail_cap) {
-              TailEntry te;
-              te.g = gi; te.w0 = r[0]; te.w1 = 0;
-              for (int j = 0; j < 6; ++j) te.x[j] = r[1 + j];
-              a.tailq[qi] = te;
-              r[7] = 1;
-            }
-          }
-          ++ns;
-          if (gi == a.n - 1) {
-            a.ctrl->next_pos = chunk0 + (u64)p;
-            atomicMin(&a.ctrl->done_tile, k);
-          }
-          if (emitted + ns == cnt) active = false;
-        }
-        __syncwarp();
-        // evaluate and write: 32 lanes on 32 consecutive (row, slot) entries
-        const u64 dst = my0 + emitted;
-        for (int it = 0; it < kRecS; ++it) {
-          int ent = it * 32 + lane;
-          int rr = ent / kRecS, col = ent % kRecS;
-          u64 d = __shfl_sync(0xffffffffu, dst, rr);
-          int c = __shfl_sync(0xffffffffu, ns, rr);
-          if (col < c && d + col < a.n) {
-            const u64* r = &stage[wid][(rr * (kRecS + 1) + col) * kRecW];
-            if (!r[7]) out[d + col] = S::value(r, a.sp, z);
+    const u64 my0 = base + (u64)off;
+    int emitted = 0;
+    int p = sig;
+    bool active = ok && cnt > 0;
+    u64* myrow = &sm.stage[wid][lane * (kRecS + 1) * kRecW];
+    while (__any_sync(0xffffffffu, active)) {
+      int ns = 0;
+      while (active && ns < kRecS) {
+        u64 u = g.next();
+        ++p;
+        if (!m.feed(u, a.sp, z)) continue;
+        u64* r = myrow + ns * kRecW;
+        m.record(r);
+        const u64 gi = my0 + emitted + ns;
+        r[7] = 0;
+        if (S::needs_tail(r) && gi < a.n) {
+          unsigned long long qi = atomicAdd(a.tail_count, 1ull);
+          if (qi < a.tail_cap) {
+            TailEntry te;
+            te.g = a.tail_abs ? (u64)(out + gi) : gi;
+            te.w0 = r[0];
+            te.w1 = (u64)a.req;
+            for (int j = 0; j < 6; ++j) te.x[j] = r[1 + j];
+            a.tailq[qi] = te;
+            r[7] = 1;
           }
         }
-        __syncwarp();
-        emitted += ns;
+        ++ns;
+        if (gi == a.n - 1) {
+          a.ctrl->next_pos = chunk0 + (u64)p;
+          atomicMin(&a.ctrl->done_tile, k);
+        }
+        if (emitted + ns == cnt) active = false;
       }
+      __syncwarp();
+      // evaluate and write: 32 lanes on 32 consecutive (row, slot) entries
+      const u64 dst = my0 + emitted;
+      for (int it = 0; it < kRecS; ++it) {
+        int ent = it * 32 + lane;
+        int rr = ent / kRecS, col = ent % kRecS;
+        u64 d = __shfl_sync(0xffffffffu, dst, rr);
+        int c = __shfl_sync(0xffffffffu, ns, rr);
+        if (col < c && d + col < a.n) {
+          const u64* r = &sm.stage[wid][(rr * (kRecS + 1) + col) * kRecW];
+          if (!r[7]) out[d + col] = S::value(r, a.sp, z);
+        }
+      }
+      __syncwarp();
+      emitted += ns;
     }
-    __syncthreads();
+  }
+  __syncthreads();
+  return true;
+}
+
+template <int NT, int C, class E, class S>
+__global__ void __launch_bounds__(NT) k_merge(FillArgs a) {
+  __shared__ MergeSmem<NT> sm;
+  E e;
+  e.init_tile(a.eng, blockIdx.x, threadIdx.x, sm.sh4);
+  for (u64 k = blockIdx.x; k < a.n_tiles; k += gridDim.x) {
+    if (!merge_tile<NT, C, E, S>(a, k, e, sm)) break;
     e.advance(a.eng);
+  }
+}
+
+template <int NT, int C, class E>
+__global__ void __launch_bounds__(NT) k_onepw_batch(BatchArgs b) {
+  __shared__ __align__(16) u64 stage[NT / 32][32 * kRow];
+  __shared__ u64 sh4[4];
+  __shared__ FillArgs fa;
+  __shared__ unsigned long long slot;
+  const int wid = threadIdx.x >> 5;
+  BatchItem bi;
+  while (batch_claim(b, fa, bi, &slot)) {
+    E e;
+    e.init_tile(fa.eng, bi.tile, threadIdx.x, sh4);
+    if (fa.dist == D_U64) onepw_tile<NT, C, E, SampU64>(fa, bi.tile, e, stage[wid]);
+    else onepw_tile<NT, C, E, SampUniform>(fa, bi.tile, e, (double*)stage[wid]);
+  }
+}
+
+template <int NT, int C, class E>
+__global__ void __launch_bounds__(NT) k_merge_batch(BatchArgs b) {
+  __shared__ MergeSmem<NT> sm;
+  __shared__ FillArgs fa;
+  __shared__ unsigned long long slot;
+  BatchItem bi;
+  while (batch_claim(b, fa, bi, &slot)) {
+    E e;
+    e.init_tile(fa.eng, bi.tile, threadIdx.x, sm.sh4);
+    if (fa.dist == D_GAMMA) merge_tile<NT, C, E, SampGamma>(fa, bi.tile, e, sm);
+    else merge_tile<NT, C, E, SampBeta>(fa, bi.tile, e, sm);
   }
 }
 
 template <class S>
 __global__ void k_tails_rec(FillArgs a) {
   const ZigDev& z = g_zig[0];
-  unsigned long long n = ld_volatile(&a.ctrl->n_tail);
+  unsigned long long n = ld_volatile(a.tail_count);
   if (n > a.tail_cap) n = a.tail_cap;
   double* out = (double*)a.out;
   for (unsigned long long i = blockIdx.x * (u64)blockDim.x + threadIdx.x; i < n; i += (u64)gridDim.x * blockDim.x) {
@@ -438,7 +513,7 @@ __global__ void k_tails_rec(FillArgs a) {
 template <class S>
 __global__ void k_tails(FillArgs a) {
   const ZigDev& z = g_zig[a.dist == D_EXP ? 1 : 0];
-  unsigned long long n = ld_volatile(&a.ctrl->n_tail);
+  unsigned long long n = ld_volatile(a.tail_count);
   if (n > a.tail_cap) n = a.tail_cap;
   typedef typename S::out_t OT;
   OT* out = (OT*)a.out;
@@ -484,6 +559,28 @@ int launch_lean(const FillArgs& a, int grid, cudaStream_t s, int* occ) {
   return (int)cudaGetLastError();
 }
 
+// Batched classes: grid <= 0 reports the occupancy in *occ.
+template <class E, int CB>
+int launch_batch_c(int cls, const BatchArgs& b, int grid, cudaStream_t s, int* occ) {
+  if (cls == BC_ONEPW) {
+    if (grid <= 0) return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k_onepw_batch<NT_, CB, E>, NT_, 0);
+    k_onepw_batch<NT_, CB, E><<<grid, NT_, 0, s>>>(b);
+  } else if (cls == BC_LEAN) {
+    if (grid <= 0) return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k_lean_batch<NT_, CB, E>, NT_, 0);
+    k_lean_batch<NT_, CB, E><<<grid, NT_, 0, s>>>(b);
+  } else {
+    if (grid <= 0) return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k_merge_batch<NTM_, CM_, E>, NTM_, 0);
+    k_merge_batch<NTM_, CM_, E><<<grid, NTM_, 0, s>>>(b);
+  }
+  return (int)cudaGetLastError();
+}
+
+template <class E>
+int launch_batch_cls(int cls, int cvar, const BatchArgs& b, int grid, cudaStream_t s, int* occ) {
+  if (cvar == 1 && cls != BC_MERGE) return launch_batch_c<E, 128>(cls, b, grid, s, occ);
+  return launch_batch_c<E, C_>(cls, b, grid, s, occ);
+}
+
 template <class E>
 int dispatch_dist(const FillArgs& a, int grid, cudaStream_t s, int* occ) {
   switch (a.dist) {
@@ -506,6 +603,9 @@ int dispatch_dist(const FillArgs& a, int grid, cudaStream_t s, int* occ) {
   namespace rp {                                                                               \
   int dispatch_##NAME(const FillArgs& a, int grid, void* s, int* occ) {                        \
     return dispatch_dist<ENGINE>(a, grid, (cudaStream_t)s, occ);                               \
+  }                                                                                            \
+  int batch_##NAME(int cls, int cvar, const BatchArgs& b, int grid, void* s, int* occ) {      \
+    return launch_batch_cls<ENGINE>(cls, cvar, b, grid, (cudaStream_t)s, occ);                 \
   }                                                                                            \
   int upload_zig_##NAME(const void* host2) {                                                   \
     return (int)cudaMemcpyToSymbol(g_zig, host2, 2 * sizeof(ZigDev));                          \

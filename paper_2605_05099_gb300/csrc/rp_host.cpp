@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <atomic>
 #include <cmath>
 #include <cstdio>
@@ -486,17 +487,11 @@ double words_per_variate(int dist, const rp::SampArgs& sp) {
   }
 }
 
-rp_status run_fill(int engine, u64 seed, u64 stream, u64* pos, size_t n, int dist, const rp::SampArgs& sp,
-                   void* d_out, void* cstream) {
-  if (!pos) return fail(RP_ERR_NULL, "pos is NULL");
-  if (n == 0) return RP_OK;
-  if (!d_out) return fail(RP_ERR_NULL, "output pointer is NULL");
-  if ((uintptr_t)d_out & 7) return fail(RP_ERR_PARAM, "output pointer must be 8-byte aligned");
-  if (engine < 1 || engine > 3) return fail(RP_ERR_ENGINE, "unknown engine id " + std::to_string(engine));
-  std::lock_guard<std::mutex> lk(g_mu);
-  u64 s[4] = {0, 0, 0, 0};
-  rp_status st = seed_state(engine, seed, stream, s);
-  if (st) return st;
+// Fill from explicit state words (the engine at word 0 of the stream; *pos
+// words in).  Caller holds g_mu.
+rp_status run_fill_state_locked(int engine, const u64 s_in[4], u64* pos, size_t n, int dist, const rp::SampArgs& sp,
+                                void* d_out, void* cstream) {
+  u64 s[4] = {s_in[0], s_in[1], s_in[2], s_in[3]};
   int e = ensure_zig();
   if (e) return cuda_fail(e, "ziggurat table upload");
 
@@ -561,6 +556,7 @@ rp_status run_fill(int engine, u64 seed, u64 stream, u64* pos, size_t n, int dis
       a.ctrl = g_scr.ctrl;
       a.tailq = g_scr.tailq;
       a.tail_cap = queued ? g_scr.tail_cap : 0;
+      a.tail_count = &g_scr.ctrl->n_tail;
       rp::Ctrl c0;
       memset(&c0, 0, sizeof(c0));
       c0.done_tile = ~0ull;
@@ -603,6 +599,26 @@ rp_status run_fill(int engine, u64 seed, u64 stream, u64* pos, size_t n, int dis
   }
   *pos = cur;
   return RP_OK;
+}
+
+rp_status check_fill_args(int engine, u64* pos, size_t n, void* d_out) {
+  if (!pos) return fail(RP_ERR_NULL, "pos is NULL");
+  if (n == 0) return RP_OK;
+  if (!d_out) return fail(RP_ERR_NULL, "output pointer is NULL");
+  if ((uintptr_t)d_out & 7) return fail(RP_ERR_PARAM, "output pointer must be 8-byte aligned");
+  if (engine < 1 || engine > 3) return fail(RP_ERR_ENGINE, "unknown engine id " + std::to_string(engine));
+  return RP_OK;
+}
+
+rp_status run_fill(int engine, u64 seed, u64 stream, u64* pos, size_t n, int dist, const rp::SampArgs& sp,
+                   void* d_out, void* cstream) {
+  rp_status st = check_fill_args(engine, pos, n, d_out);
+  if (st || n == 0) return st;
+  std::lock_guard<std::mutex> lk(g_mu);
+  u64 s[4] = {0, 0, 0, 0};
+  st = seed_state(engine, seed, stream, s);
+  if (st) return st;
+  return run_fill_state_locked(engine, s, pos, n, dist, sp, d_out, cstream);
 }
 
 }  // namespace
@@ -867,6 +883,7 @@ extern "C" rp_status rp_fill_normal_philox_static(uint64_t seed, uint64_t stream
   a.ctrl = ctrl;
   a.tailq = tailq;
   a.tail_cap = rp::kStaticTailCap;
+  a.tail_count = &ctrl->n_tail;
 
   u64 cur = *pos;
   size_t done = 0;
@@ -917,4 +934,516 @@ extern "C" rp_status rp_fill_normal_philox_static(uint64_t seed, uint64_t stream
   }
   *pos = cur;
   return RP_OK;
+}
+
+// ---------------------------------------------------------------- fills from state, substreams
+namespace {
+
+// Sampler arguments of (dist, p0, p1, m) with the checks of the seeded fills;
+// *dist_out is the kernel distribution (bounded with m = 0 -> raw words).
+rp_status make_samp(int dist, double p0, double p1, u64 m, rp::SampArgs& sp, int* dist_out) {
+  memset(&sp, 0, sizeof(sp));
+  *dist_out = dist;
+  switch (dist) {
+    case RP_DIST_U64: case RP_DIST_UNIFORM: case RP_DIST_NORMAL: case RP_DIST_EXP: return RP_OK;
+    case RP_DIST_BOUNDED:
+      sp.m = m;
+      if (m == 0) { *dist_out = rp::D_U64; return RP_OK; }
+      sp.thresh = (0 - m) % m;
+      return RP_OK;
+    case RP_DIST_GAMMA:
+      if (!(p0 > 0.0) || !std::isfinite(p0)) return fail(RP_ERR_PARAM, "gamma shape must be positive and finite");
+      sp.ga = mt_params(p0);
+      return RP_OK;
+    case RP_DIST_BETA:
+      if (!(p0 > 0.0) || !(p1 > 0.0) || !std::isfinite(p0) || !std::isfinite(p1))
+        return fail(RP_ERR_PARAM, "beta parameters must be positive and finite");
+      sp.ga = mt_params(p0);
+      sp.gb = mt_params(p1);
+      return RP_OK;
+    default:
+      return fail(RP_ERR_PARAM, "unknown distribution code " + std::to_string(dist));
+  }
+}
+
+// Beta(a, a) from a state: consecutive Gamma(a) pairs (as rp_fill_beta).
+rp_status beta_equal_state_locked(int engine, const u64 s[4], u64* pos, size_t n, const rp::SampArgs& sp,
+                                  double* d_out, void* cstream) {
+  const size_t blk = (size_t)1 << 24;
+  double* tmp = nullptr;
+  size_t cap = std::min(n, blk);
+  int e = (int)cudaMalloc((void**)&tmp, cap * 2 * sizeof(double));
+  if (e) return fail(RP_ERR_NOMEM, "beta scratch allocation failed");
+  u64 p = *pos;
+  rp_status st = RP_OK;
+  for (size_t done = 0; done < n && st == RP_OK; done += cap) {
+    size_t m = std::min(cap, n - done);
+    rp::SampArgs sg{};
+    sg.ga = sp.ga;
+    st = run_fill_state_locked(engine, s, &p, 2 * m, rp::D_GAMMA, sg, tmp, cstream);
+    if (st) break;
+    e = rp::launch_beta_pairs(tmp, d_out + done, m, cstream);
+    if (!e) e = (int)cudaStreamSynchronize((cudaStream_t)cstream);
+    if (e) st = cuda_fail(e, "beta pairs");
+  }
+  cudaFree(tmp);
+  if (st == RP_OK) *pos = p;
+  return st;
+}
+
+rp_status substream_words(int engine, u64 base_seed, u64 sidx, u64 w[4]) {
+  rp_status st = seed_state(engine, base_seed, RP_NO_STREAM, w);
+  if (st) return st;
+  if (engine == RP_XOSHIRO256PP) {
+    const u64 limbs[3] = {0, 0, sidx};   // s * 2^128
+    xo_jump_limbs(w, limbs, 3);
+  } else if (engine == RP_PHILOX4X32_10) {
+    w[2] = sidx;
+  } else {
+    const u128 inc = ((u128)sidx << 1) | 1u;
+    w[2] = (u64)(inc >> 64);
+    w[3] = (u64)inc;
+  }
+  return RP_OK;
+}
+
+}  // namespace
+
+extern "C" rp_status rp_fill_state(rp_engine engine, const uint64_t* words, uint64_t* pos, int dist, size_t n,
+                                   double p0, double p1, uint64_t m, void* d_out, void* cuda_stream) {
+  if (!words) return fail(RP_ERR_NULL, "words is NULL");
+  rp_status st = check_fill_args(engine, (u64*)pos, n, d_out);
+  if (st || n == 0) return st;
+  rp::SampArgs sp;
+  int kd = 0;
+  st = make_samp(dist, p0, p1, m, sp, &kd);
+  if (st) return st;
+  u64 s[4] = {words[0], words[1], words[2], engine == RP_PHILOX4X32_10 ? 0 : words[3]};
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (dist == RP_DIST_BETA && p0 == p1)
+    return beta_equal_state_locked(engine, s, (u64*)pos, n, sp, (double*)d_out, cuda_stream);
+  return run_fill_state_locked(engine, s, (u64*)pos, n, kd, sp, d_out, cuda_stream);
+}
+
+extern "C" rp_status rp_substream_state(rp_engine engine, uint64_t base_seed, uint64_t s, uint64_t* words, int* nw) {
+  if (!words || !nw) return fail(RP_ERR_NULL, "words/nw is NULL");
+  if (engine < 1 || engine > 3) return fail(RP_ERR_ENGINE, "unknown engine id " + std::to_string((int)engine));
+  std::lock_guard<std::mutex> lk(g_mu);
+  u64 w[4] = {0, 0, 0, 0};
+  rp_status st = substream_words(engine, base_seed, s, w);
+  if (st) return st;
+  memcpy(words, w, sizeof(w));
+  *nw = engine == RP_PHILOX4X32_10 ? 3 : 4;
+  return RP_OK;
+}
+
+// ---------------------------------------------------------------- batch plans
+// A plan holds, for one request set: each request's substream state, the
+// per-request kernel arguments and (request, tile) work lists of the chosen
+// schedule, the scratch (tile status words, control blocks, tail queues,
+// claim counters) and the instantiated CUDA graph that runs everything.
+struct rp_batch_plan {
+  int engine = 0;
+  u64 base_seed = 0;
+  size_t nreq = 0;
+  std::vector<rp_request> req;
+  std::vector<std::array<u64, 4>> sub;   // substream state (before word 0)
+  std::vector<int> cls;                  // kernel class, -1: nothing to do
+  std::vector<int> kdist;                // kernel distribution
+  std::vector<rp::SampArgs> sp;
+  // scratch
+  unsigned long long* d_status = nullptr;
+  size_t status_cap = 0;
+  rp::Ctrl* d_ctrl = nullptr;
+  rp::Ctrl* h_ctrl = nullptr;            // pinned
+  unsigned long long* d_count = nullptr; // [0..2] claim counters, [3] ziggurat tails, [4] gamma/beta tails
+  rp::TailEntry* d_tailq[2] = {nullptr, nullptr};
+  u64 tail_cap[2] = {0, 0};
+  cudaStream_t cs[3] = {nullptr, nullptr, nullptr};
+  cudaEvent_t ev_fork = nullptr, ev_join[3] = {nullptr, nullptr, nullptr};
+  // chosen schedule
+  int schedule = 0;
+  double tuned_ms = 0.0;
+  rp::FillArgs* d_fa = nullptr;
+  rp::BatchItem* d_items = nullptr;
+  u64 n_items_total = 0;
+  std::vector<u64> tiles;                // per request, chosen schedule
+  cudaGraphExec_t exec = nullptr;
+};
+
+namespace {
+
+int batch_class(int kdist) {
+  if (kdist == rp::D_U64 || kdist == rp::D_UNIFORM) return rp::BC_ONEPW;
+  if (kdist == rp::D_GAMMA || kdist == rp::D_BETA) return rp::BC_MERGE;
+  return rp::BC_LEAN;
+}
+
+struct BatchBuild {
+  rp::FillArgs* d_fa = nullptr;
+  rp::BatchItem* d_items = nullptr;
+  u64 n_items[3] = {0, 0, 0}, item_off[3] = {0, 0, 0};
+  std::vector<u64> tiles;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  void release() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    if (d_fa) cudaFree(d_fa);
+    if (d_items) cudaFree(d_items);
+    exec = nullptr; graph = nullptr; d_fa = nullptr; d_items = nullptr;
+  }
+};
+
+// Builds the device work lists and the graph of one schedule.
+// schedule bit 0: items of larger requests first; bit 1: classes one after
+// another instead of concurrently; bit 2: 128 words per thread.
+rp_status batch_build(rp_batch_plan& P, int schedule, BatchBuild& B) {
+  const int cvar = (schedule >> 2) & 1;
+  const size_t R = P.nreq;
+  std::vector<rp::FillArgs> fa(R);
+  B.tiles.assign(R, 0);
+  u64 status_off = 0;
+  int e = 0;
+  void *gpow = nullptr, *gthr[3] = {nullptr, nullptr, nullptr}, *gcta[3] = {nullptr, nullptr, nullptr};
+  u64* ppow = nullptr;
+  if (P.engine == RP_XOSHIRO256PP) {
+    e = xo_device_pow(&gpow);
+    for (int c = 0; c < 3 && !e; ++c) {
+      rp::TileGeom tg = rp::batch_geom(c, cvar);
+      e = xo_device_thread((u64)tg.c, tg.nt, &gthr[c]);
+      if (!e) e = xo_device_cta((u64)tg.tile_words, &gcta[c]);
+    }
+  } else if (P.engine == RP_PCG64DXSM) {
+    e = pcg_device_pow(&ppow);
+  }
+  if (e) return cuda_fail(e, "jump tables");
+  for (size_t r = 0; r < R; ++r) {
+    const int c = P.cls[r];
+    if (c < 0) continue;
+    rp::FillArgs& a = fa[r];
+    memset(&a, 0, sizeof(a));
+    const rp::TileGeom tg = rp::batch_geom(c, cvar);
+    const u64 T = (u64)tg.tile_words, n = P.req[r].n;
+    u64 tiles;
+    if (c == rp::BC_ONEPW) {
+      tiles = (n + T - 1) / T;
+    } else {
+      const double wpv = words_per_variate(P.kdist[r], P.sp[r]);
+      const double need = (double)n * wpv + 8.0 * std::sqrt((double)n * (wpv > 1.0 ? wpv : 1.0)) + 64.0;
+      tiles = (u64)(need / (double)T) + 2;
+    }
+    if (tiles >= 65536) return fail(RP_ERR_PARAM, "request " + std::to_string(r) + " is too large for a batch");
+    B.tiles[r] = tiles;
+    a.eng.engine = P.engine;
+    u64 s0[4];
+    memcpy(s0, P.sub[r].data(), sizeof(s0));
+    if (P.engine == RP_PHILOX4X32_10) a.eng.word0 = P.req[r].pos;
+    else jump_state(P.engine, s0, (u128)P.req[r].pos);
+    memcpy(a.eng.s, s0, sizeof(s0));
+    a.eng.gf2_pow = gpow;
+    a.eng.gf2_thread = gthr[c];
+    a.eng.gf2_cta = gcta[c];
+    a.eng.pcg_pow = ppow;
+    a.eng.tile_words = T;
+    a.eng.chunk_words = (u64)tg.c;
+    a.sp = P.sp[r];
+    a.dist = P.kdist[r];
+    a.n = n;
+    a.n_tiles = tiles;
+    a.out = P.req[r].d_out;
+    a.tile_status = P.d_status + status_off;
+    a.ctrl = P.d_ctrl + r;
+    const int q = c == rp::BC_MERGE ? 1 : 0;
+    a.tailq = c == rp::BC_ONEPW ? nullptr : P.d_tailq[q];
+    a.tail_cap = c == rp::BC_ONEPW ? 0 : P.tail_cap[q];
+    a.tail_count = P.d_count + 3 + q;
+    a.tail_abs = 1;
+    a.req = (int)r;
+    status_off += tiles;
+  }
+  if (status_off > P.status_cap) return fail(RP_ERR_INTERNAL, "batch status words exceed the plan's scratch");
+  // work lists: per class, requests in the schedule's order, tiles ascending
+  std::vector<size_t> order(R);
+  for (size_t r = 0; r < R; ++r) order[r] = r;
+  if (schedule & 1)
+    std::stable_sort(order.begin(), order.end(), [&](size_t x, size_t y) { return P.req[x].n > P.req[y].n; });
+  std::vector<rp::BatchItem> items;
+  for (int c = 0; c < 3; ++c) {
+    B.item_off[c] = items.size();
+    for (size_t r : order)
+      if (P.cls[r] == c)
+        for (u64 k = 0; k < B.tiles[r]; ++k) items.push_back(rp::BatchItem{(unsigned)r, (unsigned)k});
+    B.n_items[c] = items.size() - B.item_off[c];
+  }
+  e = (int)cudaMalloc((void**)&B.d_fa, std::max<size_t>(R, 1) * sizeof(rp::FillArgs));
+  if (!e) e = (int)cudaMalloc((void**)&B.d_items, std::max<size_t>(items.size(), 1) * sizeof(rp::BatchItem));
+  if (e) { B.release(); return fail(RP_ERR_NOMEM, "batch work-list allocation failed"); }
+  e = (int)cudaMemcpy(B.d_fa, fa.data(), R * sizeof(rp::FillArgs), cudaMemcpyHostToDevice);
+  if (!e && !items.empty())
+    e = (int)cudaMemcpy(B.d_items, items.data(), items.size() * sizeof(rp::BatchItem), cudaMemcpyHostToDevice);
+  if (e) { B.release(); return cuda_fail(e, "batch upload"); }
+  // class kernel arguments and grids
+  rp::BatchArgs ba[3];
+  int grid[3] = {0, 0, 0};
+  const int sms = sm_count();
+  for (int c = 0; c < 3; ++c) {
+    ba[c].reqs = B.d_fa;
+    ba[c].items = B.d_items + B.item_off[c];
+    ba[c].n_items = B.n_items[c];
+    ba[c].next_item = P.d_count + c;
+    const int q = c == rp::BC_MERGE ? 1 : 0;
+    ba[c].tailq = P.d_tailq[q];
+    ba[c].tail_count = P.d_count + 3 + q;
+    ba[c].tail_cap = P.tail_cap[q];
+    int occ = 0;
+    e = rp::launch_batch(P.engine, c, cvar, ba[c], 0, nullptr, &occ);
+    if (e) { B.release(); return cuda_fail(e, "batch occupancy"); }
+    const u64 g = (u64)sms * (u64)(occ > 0 ? occ : 1);
+    grid[c] = (int)std::min<u64>(g, std::max<u64>(B.n_items[c], 1));
+  }
+  // capture: reset scratch, run the classes (concurrently or in turn), tails
+  cudaStream_t ps = P.cs[0];
+  e = (int)cudaStreamBeginCapture(ps, cudaStreamCaptureModeThreadLocal);
+  if (e) { B.release(); return cuda_fail(e, "graph capture"); }
+  int ce = (int)cudaMemsetAsync(P.d_status, 0, std::max<u64>(status_off, 1) * 8, ps);
+  if (!ce) ce = (int)cudaMemsetAsync(P.d_ctrl, 0, R * sizeof(rp::Ctrl), ps);
+  if (!ce) ce = (int)cudaMemset2DAsync(P.d_ctrl, sizeof(rp::Ctrl), 0xff, sizeof(unsigned long long), R, ps);
+  if (!ce) ce = (int)cudaMemsetAsync(P.d_count, 0, 5 * sizeof(unsigned long long), ps);
+  const bool serial = (schedule >> 1) & 1;
+  if (!ce && !serial) ce = (int)cudaEventRecord(P.ev_fork, ps);
+  for (int c = 0; c < 3 && !ce; ++c) {
+    if (!B.n_items[c]) continue;
+    cudaStream_t s = serial ? ps : P.cs[c];
+    if (!serial && c != 0) ce = (int)cudaStreamWaitEvent(s, P.ev_fork, 0);
+    if (!ce) ce = rp::launch_batch(P.engine, c, cvar, ba[c], grid[c], s, nullptr);
+    if (!ce) ce = rp::launch_batch_tails(c, ba[c], s);
+    if (!ce && !serial && c != 0) {
+      ce = (int)cudaEventRecord(P.ev_join[c], s);
+      if (!ce) ce = (int)cudaStreamWaitEvent(ps, P.ev_join[c], 0);
+    }
+  }
+  e = (int)cudaStreamEndCapture(ps, &B.graph);
+  if (ce || e) { B.release(); return cuda_fail(ce ? ce : e, "graph capture"); }
+  e = (int)cudaGraphInstantiate(&B.exec, B.graph, 0);
+  if (e) { B.release(); return cuda_fail(e, "graph instantiate"); }
+  return RP_OK;
+}
+
+// Reads the control blocks after a run: device checks, and requests whose
+// tile estimate fell short are completed by a plain fill from where their
+// chain stopped.  next_pos (nullable) receives each request's next word.
+rp_status batch_finish(rp_batch_plan& P, const std::vector<u64>& tiles, u64* next_pos, void* cstream) {
+  for (size_t r = 0; r < P.nreq; ++r) {
+    const u64 pos0 = P.req[r].pos;
+    if (P.cls[r] < 0) { if (next_pos) next_pos[r] = pos0; continue; }
+    const rp::Ctrl& c = P.h_ctrl[r];
+    if (c.err) {
+      char buf[200];
+      snprintf(buf, sizeof buf, "batch request %zu: device check failed (bits 0x%x, tile %llu)", r, c.err,
+               (unsigned long long)c.err_info);
+      return fail(c.err & rp::E_TIMEOUT ? RP_ERR_TIMEOUT : RP_ERR_INTERNAL, buf);
+    }
+    const u64 n = P.req[r].n;
+    if (P.cls[r] == rp::BC_ONEPW) {
+      if (next_pos) next_pos[r] = pos0 + n;
+      continue;
+    }
+    if (c.done_tile != ~0ull) {
+      if (next_pos) next_pos[r] = pos0 + c.next_pos;
+      continue;
+    }
+    if (c.total >= n || (c.total == 0 && c.next_pos == 0))
+      return fail(RP_ERR_INTERNAL, "batch request " + std::to_string(r) + " produced no usable output");
+    (void)tiles;
+    u64 p = pos0 + c.next_pos;
+    u64 s[4];
+    memcpy(s, P.sub[r].data(), sizeof(s));
+    rp_status st = run_fill_state_locked(P.engine, s, &p, n - c.total, P.kdist[r], P.sp[r],
+                                         (char*)P.req[r].d_out + c.total * 8, cstream);
+    if (st) return st;
+    if (next_pos) next_pos[r] = p;
+  }
+  return RP_OK;
+}
+
+rp_status batch_launch(rp_batch_plan& P, cudaGraphExec_t exec, void* cstream) {
+  cudaStream_t s = (cudaStream_t)cstream;
+  int e = (int)cudaGraphLaunch(exec, s);
+  if (!e && P.nreq) e = (int)cudaMemcpyAsync(P.h_ctrl, P.d_ctrl, P.nreq * sizeof(rp::Ctrl), cudaMemcpyDeviceToHost, s);
+  if (!e) e = (int)cudaStreamSynchronize(s);
+  if (e) return cuda_fail(e, "batch run");
+  g_launches.fetch_add(1);
+  return RP_OK;
+}
+
+void plan_free(rp_batch_plan* P) {
+  if (!P) return;
+  if (P->exec) cudaGraphExecDestroy(P->exec);
+  if (P->d_fa) cudaFree(P->d_fa);
+  if (P->d_items) cudaFree(P->d_items);
+  if (P->d_status) cudaFree(P->d_status);
+  if (P->d_ctrl) cudaFree(P->d_ctrl);
+  if (P->h_ctrl) cudaFreeHost(P->h_ctrl);
+  if (P->d_count) cudaFree(P->d_count);
+  for (int q = 0; q < 2; ++q)
+    if (P->d_tailq[q]) cudaFree(P->d_tailq[q]);
+  for (int c = 0; c < 3; ++c) {
+    if (P->cs[c]) cudaStreamDestroy(P->cs[c]);
+    if (P->ev_join[c]) cudaEventDestroy(P->ev_join[c]);
+  }
+  if (P->ev_fork) cudaEventDestroy(P->ev_fork);
+  delete P;
+}
+
+}  // namespace
+
+extern "C" rp_status rp_batch_plan_create(const rp_request* reqs, size_t nreq, rp_engine engine, uint64_t base_seed,
+                                          int autotune, rp_batch_plan** plan, void* cuda_stream) {
+  if (!plan) return fail(RP_ERR_NULL, "plan is NULL");
+  *plan = nullptr;
+  if (nreq && !reqs) return fail(RP_ERR_NULL, "reqs is NULL");
+  if (engine < 1 || engine > 3) return fail(RP_ERR_ENGINE, "unknown engine id " + std::to_string((int)engine));
+  std::lock_guard<std::mutex> lk(g_mu);
+  int e = ensure_zig();
+  if (e) return cuda_fail(e, "ziggurat table upload");
+  rp_batch_plan* P = new rp_batch_plan();
+  P->engine = engine;
+  P->base_seed = base_seed;
+  P->nreq = nreq;
+  P->req.assign(reqs, reqs + nreq);
+  P->sub.resize(nreq);
+  P->cls.assign(nreq, -1);
+  P->kdist.assign(nreq, 0);
+  P->sp.resize(nreq);
+  u64 tail_need[2] = {4096, 4096}, max_tiles = 0;
+  for (size_t r = 0; r < nreq; ++r) {
+    const rp_request& q = P->req[r];
+    if (q.reserved != 0) { plan_free(P); return fail(RP_ERR_PARAM, "rp_request.reserved must be 0"); }
+    int kd = 0;
+    rp_status st = make_samp(q.dist, q.p0, q.p1, q.m, P->sp[r], &kd);
+    if (st) { plan_free(P); return st; }
+    if (q.dist == RP_DIST_BETA && q.p0 == q.p1) {
+      plan_free(P);
+      return fail(RP_ERR_PARAM, "batched beta requests need a != b (use rp_fill_state for equal shapes)");
+    }
+    std::array<u64, 4> w{};
+    st = substream_words(engine, base_seed, q.stream, w.data());
+    if (st) { plan_free(P); return st; }
+    P->sub[r] = w;
+    P->kdist[r] = kd;
+    if (q.n == 0) continue;
+    if (!q.d_out) { plan_free(P); return fail(RP_ERR_NULL, "request " + std::to_string(r) + " has no output"); }
+    if ((uintptr_t)q.d_out & 7) { plan_free(P); return fail(RP_ERR_PARAM, "request outputs must be 8-byte aligned"); }
+    const int c = batch_class(kd);
+    P->cls[r] = c;
+    if (c != rp::BC_ONEPW) tail_need[c == rp::BC_MERGE ? 1 : 0] += q.n / 1024 + 64;
+    // status words: bound over the schedules (the smallest tiles)
+    const rp::TileGeom tg = rp::batch_geom(c, 1);
+    const double wpv = c == rp::BC_ONEPW ? 1.0 : words_per_variate(kd, P->sp[r]);
+    max_tiles += (u64)(((double)q.n * wpv + 8.0 * std::sqrt((double)q.n * std::max(wpv, 1.0)) + 64.0) /
+                       (double)tg.tile_words) + 3;
+  }
+  P->status_cap = max_tiles + 1;
+  e = (int)cudaMalloc((void**)&P->d_status, P->status_cap * 8);
+  if (!e) e = (int)cudaMalloc((void**)&P->d_ctrl, std::max<size_t>(nreq, 1) * sizeof(rp::Ctrl));
+  if (!e) e = (int)cudaMallocHost((void**)&P->h_ctrl, std::max<size_t>(nreq, 1) * sizeof(rp::Ctrl));
+  if (!e) e = (int)cudaMalloc((void**)&P->d_count, 8 * sizeof(unsigned long long));
+  for (int q = 0; q < 2 && !e; ++q) {
+    P->tail_cap[q] = tail_need[q];
+    e = (int)cudaMalloc((void**)&P->d_tailq[q], tail_need[q] * sizeof(rp::TailEntry));
+  }
+  for (int c = 0; c < 3 && !e; ++c) {
+    e = (int)cudaStreamCreateWithFlags(&P->cs[c], cudaStreamNonBlocking);
+    if (!e) e = (int)cudaEventCreateWithFlags(&P->ev_join[c], cudaEventDisableTiming);
+  }
+  if (!e) e = (int)cudaEventCreateWithFlags(&P->ev_fork, cudaEventDisableTiming);
+  if (e) { plan_free(P); return fail(RP_ERR_NOMEM, std::string("batch scratch: ") + cudaGetErrorString((cudaError_t)e)); }
+  // schedules: the default one, or the fastest of all when tuning
+  const int n_sched = autotune ? 8 : 1;
+  BatchBuild best;
+  float best_ms = 0.0f;
+  int best_s = -1;
+  cudaEvent_t t0 = nullptr, t1 = nullptr;
+  if (autotune) {
+    cudaEventCreate(&t0);
+    cudaEventCreate(&t1);
+  }
+  for (int sched = 0; sched < n_sched; ++sched) {
+    BatchBuild B;
+    rp_status st = batch_build(*P, sched, B);
+    if (st) { best.release(); plan_free(P); return st; }
+    if (autotune) {
+      float ms = 0.0f;
+      st = batch_launch(*P, B.exec, cuda_stream);   // warm
+      if (!st) st = batch_finish(*P, B.tiles, nullptr, cuda_stream);
+      if (!st) {
+        cudaEventRecord(t0, (cudaStream_t)cuda_stream);
+        e = (int)cudaGraphLaunch(B.exec, (cudaStream_t)cuda_stream);
+        cudaEventRecord(t1, (cudaStream_t)cuda_stream);
+        if (!e) e = (int)cudaEventSynchronize(t1);
+        if (e) st = cuda_fail(e, "batch tuning");
+        else cudaEventElapsedTime(&ms, t0, t1);
+      }
+      if (st) { B.release(); best.release(); plan_free(P); return st; }
+      if (best_s < 0 || ms < best_ms) {
+        best.release();
+        best = B;
+        best_ms = ms;
+        best_s = sched;
+      } else {
+        B.release();
+      }
+    } else {
+      best = B;
+      best_s = sched;
+    }
+  }
+  if (t0) cudaEventDestroy(t0);
+  if (t1) cudaEventDestroy(t1);
+  if (best.graph) { cudaGraphDestroy(best.graph); best.graph = nullptr; }
+  P->schedule = best_s;
+  P->tuned_ms = autotune ? best_ms : 0.0;
+  P->d_fa = best.d_fa;
+  P->d_items = best.d_items;
+  P->exec = best.exec;
+  P->tiles = best.tiles;
+  P->n_items_total = best.n_items[0] + best.n_items[1] + best.n_items[2];
+  *plan = P;
+  return RP_OK;
+}
+
+extern "C" rp_status rp_batch_plan_run(rp_batch_plan* plan, uint64_t* next_pos, void* cuda_stream) {
+  if (!plan) return fail(RP_ERR_NULL, "plan is NULL");
+  std::lock_guard<std::mutex> lk(g_mu);
+  rp_status st = batch_launch(*plan, plan->exec, cuda_stream);
+  if (st) return st;
+  return batch_finish(*plan, plan->tiles, (u64*)next_pos, cuda_stream);
+}
+
+extern "C" rp_status rp_batch_plan_info(const rp_batch_plan* plan, int* schedule, double* tuned_ms, uint64_t* items) {
+  if (!plan) return fail(RP_ERR_NULL, "plan is NULL");
+  if (schedule) *schedule = plan->schedule;
+  if (tuned_ms) *tuned_ms = plan->tuned_ms;
+  if (items) *items = plan->n_items_total;
+  return RP_OK;
+}
+
+extern "C" rp_status rp_batch_plan_destroy(rp_batch_plan* plan) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  plan_free(plan);
+  return RP_OK;
+}
+
+extern "C" rp_status rp_batch_run(rp_request* reqs, size_t nreq, rp_engine engine, uint64_t base_seed,
+                                  void* cuda_stream) {
+  rp_batch_plan* P = nullptr;
+  rp_status st = rp_batch_plan_create(reqs, nreq, engine, base_seed, 0, &P, cuda_stream);
+  if (st) return st;
+  std::vector<uint64_t> np(nreq);
+  st = rp_batch_plan_run(P, np.data(), cuda_stream);
+  if (!st)
+    for (size_t r = 0; r < nreq; ++r) reqs[r].pos = np[r];
+  rp_batch_plan_destroy(P);
+  return st;
 }

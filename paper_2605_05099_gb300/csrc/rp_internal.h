@@ -81,9 +81,38 @@ struct FillArgs {
   Ctrl* ctrl;
   TailEntry* tailq;                 // deferred tail outputs
   unsigned long long tail_cap;
+  unsigned long long* tail_count;   // entries claimed in tailq (&ctrl->n_tail for one fill)
+  int tail_abs;                     // 1: TailEntry.g is the output's address (batches), 0: its index
+  int req;                          // request index within a batch
 };
 
+// Batched fills: one work item is one tile of one request.  Items of a
+// request are listed in tile order, so a tile's predecessors are always
+// claimed before it (the look-back cannot wait on an unclaimed tile).
+struct BatchItem {
+  unsigned req, tile;
+};
+struct BatchArgs {
+  const FillArgs* reqs;             // per-request arguments (device)
+  const BatchItem* items;           // work list (device)
+  unsigned long long n_items;
+  unsigned long long* next_item;    // claim counter (zeroed before the launch)
+  TailEntry* tailq;                 // tail queue shared by the class
+  unsigned long long* tail_count;
+  unsigned long long tail_cap;
+};
+
+// Kernel classes of a batch (one persistent kernel each).
+enum BatchClass : int { BC_ONEPW = 0, BC_LEAN = 1, BC_MERGE = 2 };
+
 // Kernel launchers (rp_kernels.cu).  Return a cudaError_t value.
+// Batched launches: grid <= 0 asks for the occupancy (resident CTAs per SM)
+// in *occ instead of launching.  cvar selects the words per thread of the
+// one-word and bitmap classes: 0 -> 256, 1 -> 128 (merge class: 2048).
+int launch_batch(int engine, int cls, int cvar, const BatchArgs& b, int grid, void* stream, int* occ);
+int launch_batch_tails(int cls, const BatchArgs& b, void* stream);
+struct TileGeom;
+TileGeom batch_geom(int cls, int cvar);
 int launch_fill(const FillArgs& a, int grid, void* stream);
 int launch_tails(const FillArgs& a, void* stream);
 int launch_beta_pairs(const double* g, double* out, unsigned long long m, void* stream);

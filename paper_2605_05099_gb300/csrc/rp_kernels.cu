@@ -7,6 +7,9 @@ int dispatch_xo(const FillArgs& a, int grid, void* s, int* occ);
 int dispatch_pcg(const FillArgs& a, int grid, void* s, int* occ);
 int dispatch_ph(const FillArgs& a, int grid, void* s, int* occ);
 int upload_zig_xo(const void* host2);
+int batch_xo(int cls, int cvar, const BatchArgs& b, int grid, void* s, int* occ);
+int batch_pcg(int cls, int cvar, const BatchArgs& b, int grid, void* s, int* occ);
+int batch_ph(int cls, int cvar, const BatchArgs& b, int grid, void* s, int* occ);
 int upload_zig_pcg(const void* host2);
 int upload_zig_ph(const void* host2);
 
@@ -22,6 +25,55 @@ int dispatch(const FillArgs& a, int grid, void* s, int* occ) {
 }  // namespace
 
 int launch_fill(const FillArgs& a, int grid, void* stream) { return dispatch(a, grid, stream, nullptr); }
+
+int launch_batch(int engine, int cls, int cvar, const BatchArgs& b, int grid, void* stream, int* occ) {
+  switch (engine) {
+    case 1: return batch_xo(cls, cvar, b, grid, stream, occ);
+    case 2: return batch_pcg(cls, cvar, b, grid, stream, occ);
+    case 3: return batch_ph(cls, cvar, b, grid, stream, occ);
+    default: return (int)cudaErrorInvalidValue;
+  }
+}
+
+// Tail values of a batch: TailEntry.g holds the output's address.  Ziggurat
+// entries carry their distribution in x[0]; gamma/beta records carry the
+// request index in w1 (for its shape parameters).
+__global__ void k_tails_lean_batch(BatchArgs b) {
+  unsigned long long n = ld_volatile(b.tail_count);
+  if (n > b.tail_cap) n = b.tail_cap;
+  for (unsigned long long i = blockIdx.x * (u64)blockDim.x + threadIdx.x; i < n; i += (u64)gridDim.x * blockDim.x) {
+    const TailEntry te = b.tailq[i];
+    const bool ex = te.x[0] == (u64)D_EXP;
+    const double v = ex ? SampExp::tail_value(te.w0, te.w1, g_zig[1]) : SampNormal::tail_value(te.w0, te.w1, g_zig[0]);
+    *(double*)te.g = v;
+  }
+}
+
+__global__ void k_tails_rec_batch(BatchArgs b) {
+  unsigned long long n = ld_volatile(b.tail_count);
+  if (n > b.tail_cap) n = b.tail_cap;
+  for (unsigned long long i = blockIdx.x * (u64)blockDim.x + threadIdx.x; i < n; i += (u64)gridDim.x * blockDim.x) {
+    const TailEntry te = b.tailq[i];
+    const FillArgs& a = b.reqs[te.w1];
+    const u64 r[8] = {te.w0, te.x[0], te.x[1], te.x[2], te.x[3], te.x[4], te.x[5], 0};
+    const double v = a.dist == D_BETA ? SampBeta::value(r, a.sp, g_zig[0]) : SampGamma::value(r, a.sp, g_zig[0]);
+    *(double*)te.g = v;
+  }
+}
+
+int launch_batch_tails(int cls, const BatchArgs& b, void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  if (cls == BC_LEAN) k_tails_lean_batch<<<304, 256, 0, s>>>(b);
+  else if (cls == BC_MERGE) k_tails_rec_batch<<<304, 256, 0, s>>>(b);
+  else return 0;
+  return (int)cudaGetLastError();
+}
+
+TileGeom batch_geom(int cls, int cvar) {
+  if (cls == BC_MERGE) return TileGeom{NTM_, CM_, NTM_ * CM_, 0};
+  const int c = cvar == 1 ? 128 : C_;
+  return TileGeom{NT_, c, NT_ * c, 0};
+}
 
 int launch_tails(const FillArgs& a, void* stream) {
   cudaStream_t s = (cudaStream_t)stream;

@@ -210,41 +210,50 @@ __device__ __forceinline__ void flush_rows16(OT* __restrict__ outb, const OT* ro
   }
 }
 
+template <int NT, int C>
+struct LeanSmem {
+  static constexpr int kMW = C / 32 + 1;   // mask words: the chunk and the overhang into the next one
+  static constexpr int kStageW = (NT / 32) * 32 * kRow;
+  static constexpr int kQueueW = NT * kLPend * 2;
+  static constexpr int kBufW = kStageW > kQueueW ? kStageW : kQueueW;
+  __align__(16) u64 sbuf[kBufW];   // pass 1: wedge queue; pass 2: staging rows
+  unsigned msk[kMW][NT];
+  u64 tails[kTileTails][3];
+  int ntails[2];   // by tile parity: reset one tile after use, behind a barrier
+  int wsum[32];
+  int misc[8];
+  u64 sh4[4];
+};
+
+template <class S>
+__device__ __forceinline__ void lean_load_tab(LeanTab& tb, int nt) {
+  const ZigDev& z = g_zig[S::kWhich];
+  for (int i = threadIdx.x; i < 256; i += nt) {
+    tb.khi[i] = (unsigned)(z.k[i] >> S::kKShift);
+    tb.w[i] = z.w[i];
+  }
+}
+
+// One tile of a bitmap two-pass fill.  `e` is the engine at the thread's
+// chunk start, `tb` the sampler's shared table, `par` the tile parity.
+// Returns false when the fill needs no further tiles (or a device check
+// failed): the caller stops.
 template <int NT, int C, class E, class S>
-__global__ void __launch_bounds__(NT, 8) k_lean(FillArgs a) {
+__device__ bool lean_tile(const FillArgs& a, u64 k, const E& e, LeanSmem<NT, C>& sm, const LeanTab& tb, int par) {
   static_assert(C % 32 == 0, "chunks are whole mask words");
   typedef typename S::out_t OT;
   static_assert(sizeof(OT) == 8, "staging holds 8-byte outputs");
   constexpr int T = NT * C;
-  constexpr int kMW = C / 32 + 1;   // mask words: the chunk and the overhang into the next one
-  constexpr int kStageW = (NT / 32) * 32 * kRow;
-  constexpr int kQueueW = NT * kLPend * 2;
-  constexpr int kBufW = kStageW > kQueueW ? kStageW : kQueueW;
-  __shared__ __align__(16) u64 sbuf[kBufW];   // pass 1: wedge queue; pass 2: staging rows
-  __shared__ unsigned msk[kMW][NT];
-  __shared__ LeanTab tb;
-  __shared__ u64 tails[kTileTails][3];
-  __shared__ int ntails[2];   // by tile parity: reset one tile after use, behind a barrier
-  __shared__ int wsum[32];
-  __shared__ int misc[8];
-  __shared__ u64 sh4[4];
+  constexpr int kMW = LeanSmem<NT, C>::kMW;
   const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
   const ZigDev& z = g_zig[S::kWhich];
-  for (int i = t; i < 256; i += NT) {
-    tb.khi[i] = (unsigned)(z.k[i] >> S::kKShift);
-    tb.w[i] = z.w[i];
-  }
-  if (t == 0) { ntails[0] = 0; ntails[1] = 0; }
-  __syncthreads();
   OT* out = (OT*)a.out;
-  OT* stage = (OT*)sbuf + wid * 32 * kRow;
-  E e;
-  e.init_tile(a.eng, blockIdx.x, t, sh4);
-
-  int par = 0;
-  for (u64 k = blockIdx.x; k < a.n_tiles; k += gridDim.x, par ^= 1) {
-    if (ld_volatile(&a.ctrl->done_tile) < k) break;
-    int* nts = &ntails[par];
+  OT* stage = (OT*)sm.sbuf + wid * 32 * kRow;
+  // one reader, so that every thread takes the same branch
+  if (t == 0) sm.misc[5] = ld_volatile(&a.ctrl->done_tile) < k;
+  __syncthreads();
+  if (sm.misc[5]) return false;
+    int* nts = &sm.ntails[par];
     // ---------------- pass 1: sync point, chain walk with output bitmap
     int s = 0, endp = C;
     bool ok = true;
@@ -270,25 +279,25 @@ __global__ void __launch_bounds__(NT, 8) k_lean(FillArgs a) {
           const u64 u = g.next();
           mw |= (unsigned)(u * a.sp.m >= a.sp.thresh) << j;
         }
-        msk[b][t] = mw;
+        sm.msk[b][t] = mw;
       }
-      msk[kMW - 1][t] = 0;
+      sm.msk[kMW - 1][t] = 0;
     } else {
       {  // first mask word: positions before the sync point belong to the previous chain
         unsigned mw = 0;
 #pragma unroll 4
         for (int j = 0; j < 32; ++j) {
           const u64 u = g.next();
-          if (j >= s) lean_step<NT, S>(u, j, 0, mw, c, tb, z, msk, sbuf, tails, nts, a.ctrl, k);
+          if (j >= s) lean_step<NT, S>(u, j, 0, mw, c, tb, z, sm.msk, sm.sbuf, sm.tails, nts, a.ctrl, k);
         }
-        msk[0][t] = mw;
+        sm.msk[0][t] = mw;
       }
       for (int b = 1; b < C / 32; ++b) {
         unsigned mw = 0;
 #pragma unroll 4
         for (int j = 0; j < 32; ++j)
-          lean_step<NT, S>(g.next(), b * 32 + j, b, mw, c, tb, z, msk, sbuf, tails, nts, a.ctrl, k);
-        msk[b][t] = mw;
+          lean_step<NT, S>(g.next(), b * 32 + j, b, mw, c, tb, z, sm.msk, sm.sbuf, sm.tails, nts, a.ctrl, k);
+        sm.msk[b][t] = mw;
       }
       // the next chunk's sync point by the same rule, while the chain runs on
       {
@@ -299,59 +308,69 @@ __global__ void __launch_bounds__(NT, 8) k_lean(FillArgs a) {
           if (q - C >= S::kG && reach <= q) { endp = q; break; }
           u64 u = g.next();
           reach = max(reach, q + S::len(u, g, tb, z));
-          lean_step<NT, S>(u, q, C / 32, mw, c, tb, z, msk, sbuf, tails, nts, a.ctrl, k);
+          lean_step<NT, S>(u, q, C / 32, mw, c, tb, z, sm.msk, sm.sbuf, sm.tails, nts, a.ctrl, k);
         }
-        msk[kMW - 1][t] = mw;
+        sm.msk[kMW - 1][t] = mw;
         if (endp < 0) { set_err(a.ctrl, E_NOSYNC, k); ok = false; endp = C; }
         else if (c.st != 0) { set_err(a.ctrl, E_LANDING, k); ok = false; }
       }
       // queued wedge tests, all lanes together
       for (int j = 0; j < c.np; ++j) {
-        const u64 u0 = sbuf[(j * NT + t) * 2], u1 = sbuf[(j * NT + t) * 2 + 1];
+        const u64 u0 = sm.sbuf[(j * NT + t) * 2], u1 = sm.sbuf[(j * NT + t) * 2 + 1];
         if (S::wedge(u0, u1, z)) {
           const int q = (int)(u1 & 0x7ff);
-          msk[q >> 5][t] |= 1u << (q & 31);
+          sm.msk[q >> 5][t] |= 1u << (q & 31);
         }
       }
     }
     int cnt = 0;
 #pragma unroll
-    for (int w = 0; w < kMW; ++w) cnt += __popc(msk[w][t]);
+    for (int w = 0; w < kMW; ++w) cnt += __popc(sm.msk[w][t]);
     if (!ok) cnt = 0;
     // ---------------- offsets
-    const int off = block_exclusive_scan<NT>(cnt, wsum, &misc[1]);   // also orders the queue reads before staging
+    const int off = block_exclusive_scan<NT>(cnt, sm.wsum, &sm.misc[1]);   // also orders the queue reads before staging
     if (t < 32) {
-      unsigned long long ex = lookback_warp(a.tile_status, k, (unsigned long long)misc[1], a.ctrl);
+      unsigned long long ex = lookback_warp(a.tile_status, k, (unsigned long long)sm.misc[1], a.ctrl);
       if (t == 0) {
-        misc[2] = (int)(ex & 0x7fffffff);
-        misc[3] = (int)(ex >> 31);
-        misc[4] = (ex == ~0ull);
+        sm.misc[2] = (int)(ex & 0x7fffffff);
+        sm.misc[3] = (int)(ex >> 31);
+        sm.misc[4] = (ex == ~0ull);
       }
     }
     __syncthreads();
-    if (misc[4]) break;
-    const u64 base = (u64)(unsigned)misc[2] | ((u64)(unsigned)misc[3] << 31);
+    if (sm.misc[4]) {
+      if (t == 0) *nts = 0;   // nothing reads this tile's tail list any more
+      return false;
+    }
+    const u64 base = (u64)(unsigned)sm.misc[2] | ((u64)(unsigned)sm.misc[3] << 31);
     const u64 chunk0 = k * (u64)T + (u64)t * C;
     const u64 my0 = base + (u64)off;
-    if (t == NT - 1 && k + 1 == a.n_tiles && base + (u64)misc[1] < a.n) {
+    if (t == NT - 1 && k + 1 == a.n_tiles && base + (u64)sm.misc[1] < a.n) {
       // ran out of tiles: report where the chain continues
-      a.ctrl->total = base + (u64)misc[1];
+      a.ctrl->total = base + (u64)sm.misc[1];
       a.ctrl->next_pos = chunk0 + (u64)endp;
       a.ctrl->last_tile = k;
     }
     // tail outputs of this thread: output index from the bitmap rank
     const int nt_tile = min(*nts, kTileTails);
     for (int j = 0; j < nt_tile; ++j) {
-      const u64 tp = tails[j][2];
+      const u64 tp = sm.tails[j][2];
       if ((int)(tp >> 32) != t) continue;
       const int p = (int)(unsigned)tp;
       int rank = 0;
-      for (int w = 0; w < (p >> 5); ++w) rank += __popc(msk[w][t]);
-      rank += __popc(msk[p >> 5][t] & ((1u << (p & 31)) - 1u));
+      for (int w = 0; w < (p >> 5); ++w) rank += __popc(sm.msk[w][t]);
+      rank += __popc(sm.msk[p >> 5][t] & ((1u << (p & 31)) - 1u));
       const u64 gi = my0 + (u64)rank;
       if (gi < a.n) {
-        unsigned long long qi = atomicAdd(&a.ctrl->n_tail, 1ull);
-        if (qi < a.tail_cap) a.tailq[qi] = TailEntry{gi, tails[j][0], tails[j][1]};
+        unsigned long long qi = atomicAdd(a.tail_count, 1ull);
+        if (qi < a.tail_cap) {
+          TailEntry te{};
+          te.g = a.tail_abs ? (u64)(out + gi) : gi;
+          te.w0 = sm.tails[j][0];
+          te.w1 = sm.tails[j][1];
+          te.x[0] = (u64)a.dist;
+          a.tailq[qi] = te;
+        }
         else set_err(a.ctrl, E_OVERFLOW, k);
       }
     }
@@ -359,7 +378,7 @@ __global__ void __launch_bounds__(NT, 8) k_lean(FillArgs a) {
     if (ok && cnt > 0 && my0 <= a.n - 1 && a.n - 1 < my0 + (u64)cnt) {
       int want = (int)(a.n - 1 - my0), p = 0;
       for (int w = 0; w < kMW; ++w) {
-        const unsigned m = msk[w][t];
+        const unsigned m = sm.msk[w][t];
         const int pc = __popc(m);
         if (want < pc) {
           unsigned mm = m;
@@ -388,7 +407,7 @@ __global__ void __launch_bounds__(NT, 8) k_lean(FillArgs a) {
       for (int hb = 0; hb < 2 * maxblk; ++hb) {   // half blocks of 16 words
         int ns = 0;
         if ((hb >> 1) < nblk) {
-          const unsigned m = msk[hb >> 1][t] >> ((hb & 1) * 16);
+          const unsigned m = sm.msk[hb >> 1][t] >> ((hb & 1) * 16);
 #pragma unroll 8
           for (int j = 0; j < 16; ++j) {
             const u64 u = g2.next();
@@ -406,6 +425,46 @@ __global__ void __launch_bounds__(NT, 8) k_lean(FillArgs a) {
     }
     __syncthreads();
     if (t == 0) *nts = 0;   // next used two tiles on, after another barrier
+    return true;
+}
+
+template <int NT, int C, class E, class S>
+__global__ void __launch_bounds__(NT, 8) k_lean(FillArgs a) {
+  __shared__ LeanSmem<NT, C> sm;
+  __shared__ LeanTab tb;
+  lean_load_tab<S>(tb, NT);
+  if (threadIdx.x == 0) { sm.ntails[0] = 0; sm.ntails[1] = 0; }
+  __syncthreads();
+  E e;
+  e.init_tile(a.eng, blockIdx.x, threadIdx.x, sm.sh4);
+  int par = 0;
+  for (u64 k = blockIdx.x; k < a.n_tiles; k += gridDim.x, par ^= 1) {
+    if (!lean_tile<NT, C, E, S>(a, k, e, sm, tb, par)) break;
     e.advance(a.eng);
+  }
+}
+
+// Batched fills of the ziggurat and bounded samplers: CTAs claim (request,
+// tile) items until the list is exhausted; tables for both ziggurats stay in
+// shared memory.
+template <int NT, int C, class E>
+__global__ void __launch_bounds__(NT, 6) k_lean_batch(BatchArgs b) {
+  __shared__ LeanSmem<NT, C> sm;
+  __shared__ LeanTab tb[2];
+  __shared__ FillArgs fa;
+  __shared__ unsigned long long slot;
+  lean_load_tab<LeanNormal>(tb[0], NT);
+  lean_load_tab<LeanExp>(tb[1], NT);
+  if (threadIdx.x == 0) { sm.ntails[0] = 0; sm.ntails[1] = 0; }
+  __syncthreads();
+  int par = 0;
+  BatchItem bi;
+  while (batch_claim(b, fa, bi, &slot)) {
+    E e;
+    e.init_tile(fa.eng, bi.tile, threadIdx.x, sm.sh4);
+    if (fa.dist == D_NORMAL) lean_tile<NT, C, E, LeanNormal>(fa, bi.tile, e, sm, tb[0], par);
+    else if (fa.dist == D_EXP) lean_tile<NT, C, E, LeanExp>(fa, bi.tile, e, sm, tb[1], par);
+    else lean_tile<NT, C, E, LeanBounded>(fa, bi.tile, e, sm, tb[0], par);
+    par ^= 1;
   }
 }

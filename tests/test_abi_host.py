@@ -84,3 +84,26 @@ def test_argument_errors(rp):
         assert fn(1, 1, rp.NO_STREAM, ctypes.byref(pos), 0, None, None) == 0
     assert pos.value == 77
     assert rp.rp_version().startswith("rp ")
+
+
+@pytest.mark.parametrize("engine", ["xoshiro256pp", "pcg64dxsm", "philox4x32_10"])
+def test_substream_state_matches_oracle(rp, orc, engine):
+    """Substream s of a base seed (Sec. 2.3 recipe): library host code vs the
+    oracle's independent construction (xoshiro: jump polynomial by s 2^128)."""
+    for s in [0, 1, 2, 5, 4095, 2**40 + 7]:
+        w = rp.rp_substream_state(engine, 99, s)
+        ow = orc.state_words(orc.substream(engine, 99, s))
+        assert w == ow[:len(w)], (engine, s)
+
+
+def test_batch_argument_errors_without_device(rp):
+    L = rp.lib()
+    import ctypes
+    assert L.rp_batch_plan_create(None, 0, 1, 99, 0, None, None) == -1
+    assert L.rp_batch_plan_run(None, None, None) == -1
+    assert L.rp_batch_plan_info(None, None, None, None) == -1
+    assert L.rp_fill_state(1, None, None, 3, 5, 0.0, 0.0, 0, None, None) == -1
+    w = (ctypes.c_uint64 * 4)(1, 2, 3, 4)
+    p = ctypes.c_uint64(0)
+    assert L.rp_fill_state(7, w, ctypes.byref(p), 3, 5, 0.0, 0.0, 0, ctypes.c_void_p(0x1000), None) == -3
+    assert L.rp_substream_state(9, 99, 1, w, ctypes.byref(ctypes.c_int())) == -3

@@ -1,0 +1,182 @@
+"""Batched substream fills (one CUDA-graph launch of persistent kernels over
+(request, tile) items) against the oracle's substream fills: every request
+of mixed-distribution batches on all three engines, identical consumed
+words, values bit-exact except where libm enters (ziggurat tails and the
+gamma boost: 2 ulp; beta with a shape below 1: 4 ulp).  Also: autotuned
+plans replay identically, batches equal per-request fills from the same
+state, the full 4096-request workload on sampled requests, and errors."""
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2605_05099_gb300 as rp
+from paper_2605_05099_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+ENGINES = ["xoshiro256pp", "philox4x32_10", "pcg64dxsm"]
+BASE = 99
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def _alloc(reqs):
+    outs = []
+    for r in reqs:
+        dt = torch.uint64 if r["dist"] in ("u64", "bounded") else torch.float64
+        outs.append(torch.empty(r["n"], dtype=dt, device="cuda"))
+    specs = [dict(r, out=o) for r, o in zip(reqs, outs)]
+    return outs, rp.make_requests(specs)
+
+
+def _host(t):
+    if t.dtype == torch.uint64:
+        return t.view(torch.int64).cpu().numpy().view(np.uint64)
+    return t.cpu().numpy()
+
+
+def _params(r):
+    if r["dist"] == "bounded":
+        return (r["m"],)
+    if r["dist"] == "gamma":
+        return (r["p0"],)
+    if r["dist"] == "beta":
+        return (r["p0"], r["p1"])
+    return ()
+
+
+def _oracle(engine, r, n=None):
+    g = oracle.substream(engine, BASE, r["stream"])
+    if r["pos"]:
+        oracle.jump(g, r["pos"])
+    out = oracle.fill(g, r["dist"], r["n"] if n is None else n, *_params(r))
+    return out, int(g.pos)
+
+
+def _tol(r):
+    if r["dist"] in ("normal", "exp"):
+        return 2
+    if r["dist"] == "gamma":
+        return 0 if r["p0"] >= 1.0 else 2
+    if r["dist"] == "beta":
+        return 0 if min(r["p0"], r["p1"]) >= 1.0 else 4
+    return 0
+
+
+def _compare(got, ref, r, tag):
+    assert got.shape == ref.shape
+    if got.dtype == np.uint64:
+        assert np.array_equal(got, ref), tag
+        return
+    ig, io = got.view(np.int64), ref.view(np.int64)
+    bad = np.nonzero(ig != io)[0]
+    tol = _tol(r)
+    if tol == 0:
+        assert len(bad) == 0, (tag, bad[:5], got[bad[:5]], ref[bad[:5]])
+        return
+    if r["dist"] in ("normal", "exp"):
+        assert len(bad) <= max(8, len(got) // 500), (tag, len(bad))
+    assert np.all(np.sign(got[bad]) == np.sign(ref[bad])), tag
+    assert np.all(np.abs(ig[bad] - io[bad]) <= tol), (tag, int(np.abs(ig[bad] - io[bad]).max()))
+
+
+@pytest.mark.parametrize("engine", ENGINES)
+def test_mixed_batch_matches_oracle(engine):
+    reqs = inputs.mixed_requests(40, seed=11)
+    outs, arr = _alloc(reqs)
+    pos = rp.rp_batch_run(arr, engine, BASE)
+    torch.cuda.synchronize()
+    for i, (r, o) in enumerate(zip(reqs, outs)):
+        ref, opos = _oracle(engine, r)
+        assert pos[i] == opos, (engine, i, r, pos[i], opos)
+        _compare(_host(o), ref, r, (engine, i, r["dist"], r["n"]))
+
+
+@pytest.mark.parametrize("engine", ["xoshiro256pp", "philox4x32_10"])
+def test_autotuned_plan_replays_and_matches_state_fills(engine):
+    reqs = inputs.batch_workload(n_req=48, lo=1e2, hi=2e5, seed=5)
+    outs, arr = _alloc(reqs)
+    plan = rp.BatchPlan(arr, engine, BASE, autotune=True)
+    info = plan.info()
+    assert 0 <= info["schedule"] < 8 and info["tuned_ms"] > 0 and info["items"] > 0
+    pos1 = plan.run()
+    first = [_host(o).copy() for o in outs]
+    for o in outs:
+        o.fill_(0) if o.dtype != torch.uint64 else o.view(torch.int64).fill_(0)
+    pos2 = plan.run()
+    plan.close()
+    assert pos1 == pos2
+    for i, (r, o) in enumerate(zip(reqs, outs)):
+        assert np.array_equal(first[i].view(np.uint64), _host(o).view(np.uint64)), (engine, i)
+        # the same request as its own fill from the substream state
+        words = rp.rp_substream_state(engine, BASE, r["stream"])
+        ref = torch.empty_like(o)
+        p = rp.rp_fill_state(engine, words, r["pos"], r["dist"], ref, r["p0"], r["p1"], r["m"])
+        assert p == pos1[i]
+        assert np.array_equal(_host(ref).view(np.uint64), first[i].view(np.uint64)), (engine, i, r["dist"])
+
+
+def test_medium_batch_matches_oracle():
+    reqs = inputs.batch_workload(n_req=64, lo=1e3, hi=1e6, seed=7)
+    outs, arr = _alloc(reqs)
+    pos = rp.rp_batch_run(arr, "philox4x32_10", BASE)
+    for i, (r, o) in enumerate(zip(reqs, outs)):
+        ref, opos = _oracle("philox4x32_10", r)
+        assert pos[i] == opos
+        _compare(_host(o), ref, r, (i, r["dist"], r["n"]))
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("engine", ["xoshiro256pp", "philox4x32_10"])
+def test_full_workload_sampled(engine):
+    """The 4096-request workload (about 4.45e9 variates, 35.6 GB) as the
+    bench runs it (autotuned plan): 12 requests compared whole, plus the
+    first 2048 outputs of 64 more."""
+    reqs = inputs.batch_workload()
+    outs, arr = _alloc(reqs)
+    plan = rp.BatchPlan(arr, engine, BASE, autotune=True)
+    pos = plan.run()
+    plan.close()
+    rng = np.random.default_rng(3)
+    whole = rng.choice(len(reqs), 12, replace=False)
+    for i in whole:
+        r = reqs[i]
+        ref, opos = _oracle(engine, r)
+        assert pos[i] == opos, (i, r)
+        _compare(_host(outs[i]), ref, r, (engine, int(i), r["dist"], r["n"]))
+    for i in rng.choice(len(reqs), 64, replace=False):
+        r = reqs[i]
+        k = min(2048, r["n"])
+        ref, _ = _oracle(engine, r, n=k)
+        _compare(_host(outs[i][:k]), ref, r, (engine, int(i), r["dist"], k))
+    del outs
+    torch.cuda.empty_cache()
+
+
+def test_batch_errors_and_empty():
+    out = torch.empty(10, dtype=torch.float64, device="cuda")
+    with pytest.raises(rp.RPError):
+        rp.rp_batch_run(rp.make_requests([{"stream": 1, "dist": "beta", "p0": 2.0, "p1": 2.0, "out": out}]),
+                        "xoshiro256pp", BASE)
+    arr = rp.make_requests([{"stream": 1, "dist": "normal", "out": out}])
+    arr[0].reserved = 1
+    with pytest.raises(rp.RPError):
+        rp.rp_batch_run(arr, "xoshiro256pp", BASE)
+    arr = rp.make_requests([{"stream": 1, "dist": "normal", "out": out}])
+    arr[0].dist = 9
+    with pytest.raises(rp.RPError):
+        rp.rp_batch_run(arr, "xoshiro256pp", BASE)
+    empty = torch.empty(0, dtype=torch.float64, device="cuda")
+    arr = rp.make_requests([{"stream": 3, "dist": "normal", "out": empty, "pos": 17},
+                            {"stream": 4, "dist": "exp", "out": out}])
+    pos = rp.rp_batch_run(arr, "philox4x32_10", BASE)
+    assert pos[0] == 17
+    ref, opos = _oracle("philox4x32_10", {"stream": 4, "dist": "exp", "n": 10, "pos": 0})
+    assert pos[1] == opos
+    assert rp.lib().rp_batch_run(None, 0, 1, BASE, None) == 0
