@@ -221,6 +221,27 @@ rp_status rp_beta_grad(const double* d_z, double a, double b, const double* d_g,
                        double* d_dzdb, double* h_grad_a, double* h_grad_b, void* cuda_stream);
 
 /* ---------------------------------------------------------------------
+ * Multivariate normal (Sec. 3.1, multivariate normal): x = mu + L z for n
+ * samples of dimension d, z a vector of d standard normals.
+ *   d_mu  device, d entries
+ *   d_L   device, d x d row-major; only the lower triangle (k <= i) is read
+ *   d_Z   device, n x d row-major: receives the n d normals drawn from the
+ *         stream (sample j takes normals j d .. j d + d - 1), kept for the
+ *         backward pass
+ *   d_X   device, n x d row-major: X[j] = mu + L Z[j]
+ * The product runs on the FP64 tensor cores; |x - exact| is within 1e-13
+ * (|mu| + |L| |z|) componentwise.  1 <= d <= 65536.  Returns after the
+ * kernels completed; *pos is set to the next unused word.
+ * ------------------------------------------------------------------- */
+rp_status rp_mvn(rp_engine engine, uint64_t seed, uint64_t stream, uint64_t* pos, int d, size_t n,
+                 const double* d_mu, const double* d_L, double* d_Z, double* d_X, void* cuda_stream);
+/* Gradients of a loss with upstream d_G = dLoss/dX (n x d): d_gmu (d) =
+ * sum_j G[j], d_gL (d x d) = tril(G^T Z) (zero above the diagonal).  Sums
+ * are in a fixed order (deterministic).  Not in the paper. */
+rp_status rp_mvn_grads(int d, size_t n, const double* d_G, const double* d_Z, double* d_gmu, double* d_gL,
+                       void* cuda_stream);
+
+/* ---------------------------------------------------------------------
  * Seeding and stream control (Sec. 2.3), host only.
  * ------------------------------------------------------------------- */
 /* Engine state words from (seed, spawn key): xoshiro s0..s3; PCG64 state

@@ -64,6 +64,8 @@ def lib():
             "rp_ziggurat_tables": [i32, pu64, ctypes.POINTER(dbl), ctypes.POINTER(dbl), ctypes.POINTER(dbl)],
             "rp_gamma_grad": [vp, dbl, vp, sz, vp, ctypes.POINTER(dbl), vp],
             "rp_fill_state": [i32, pu64, pu64, i32, sz, dbl, dbl, u64, vp, vp],
+            "rp_mvn": [i32, u64, u64, pu64, i32, sz, vp, vp, vp, vp, vp],
+            "rp_mvn_grads": [i32, sz, vp, vp, vp, vp, vp],
             "rp_substream_state": [i32, u64, u64, pu64, ctypes.POINTER(i32)],
             "rp_batch_plan_create": [ctypes.POINTER(Request), sz, i32, u64, i32, ctypes.POINTER(vp), vp],
             "rp_batch_plan_run": [vp, pu64, vp],
@@ -308,6 +310,57 @@ def rp_batch_run(reqs, engine, base_seed, cuda_stream=None):
     """One-shot batch: fills every request; returns the next unused words."""
     _check(lib().rp_batch_run(reqs, len(reqs), _engine(engine), base_seed, _stream_handle(cuda_stream)))
     return [reqs[i].pos for i in range(len(reqs))]
+
+
+def _f64(t, shape, name):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous():
+        raise TypeError(f"{name} must be a contiguous float64 CUDA tensor")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+    return ctypes.c_void_p(t.data_ptr()) if t.numel() else None
+
+
+def rp_mvn(engine, seed, stream, pos, mu, L, Z, X, cuda_stream=None):
+    """X = mu + L z per sample, z from the normal stream (Z saved, n x d);
+    returns the next unused word."""
+    n, d = X.shape
+    cpos = ctypes.c_uint64(pos)
+    _check(lib().rp_mvn(_engine(engine), seed, stream, ctypes.byref(cpos), d, n, _f64(mu, (d,), "mu"),
+                        _f64(L, (d, d), "L"), _f64(Z, (n, d), "Z"), _f64(X, (n, d), "X"),
+                        _stream_handle(cuda_stream)))
+    return cpos.value
+
+
+def rp_mvn_grads(G, Z, gmu, gL, cuda_stream=None):
+    """dL/dmu = sum_j G_j, dL/dL = tril(G^T Z)."""
+    n, d = Z.shape
+    _check(lib().rp_mvn_grads(d, n, _f64(G, (n, d), "G"), _f64(Z, (n, d), "Z"), _f64(gmu, (d,), "gmu"),
+                              _f64(gL, (d, d), "gL"), _stream_handle(cuda_stream)))
+
+
+class MVN(torch.autograd.Function):
+    """x = mu + L z (n samples), differentiable in mu and L (lower triangle).
+    MVN.apply(mu, L, n, engine, seed, stream, pos) -> X (n x d); the next
+    stream word is left in MVN.last_pos."""
+    last_pos = None
+
+    @staticmethod
+    def forward(ctx, mu, L, n, engine, seed, stream, pos):
+        d = mu.shape[0]
+        Z = torch.empty((n, d), dtype=torch.float64, device="cuda")
+        X = torch.empty((n, d), dtype=torch.float64, device="cuda")
+        MVN.last_pos = rp_mvn(engine, seed, stream, pos, mu.detach().contiguous(), L.detach().contiguous(), Z, X)
+        ctx.save_for_backward(Z)
+        return X
+
+    @staticmethod
+    def backward(ctx, G):
+        (Z,) = ctx.saved_tensors
+        n, d = Z.shape
+        gmu = torch.empty(d, dtype=torch.float64, device="cuda")
+        gL = torch.empty((d, d), dtype=torch.float64, device="cuda")
+        rp_mvn_grads(G.to(torch.float64).contiguous(), Z, gmu, gL)
+        return gmu, gL, None, None, None, None, None
 
 
 def rp_seed_state(engine, seed, stream=NO_STREAM):

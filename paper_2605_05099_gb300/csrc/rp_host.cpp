@@ -1447,3 +1447,62 @@ extern "C" rp_status rp_batch_run(rp_request* reqs, size_t nreq, rp_engine engin
   rp_batch_plan_destroy(P);
   return st;
 }
+
+// ---------------------------------------------------------------- multivariate normal
+namespace {
+double* g_mvn_part = nullptr;   // backward partial tiles (grown on demand)
+size_t g_mvn_cap = 0;
+
+rp_status mvn_check(int d, size_t n) {
+  if (d < 1 || d > (1 << 16)) return fail(RP_ERR_PARAM, "d must be in [1, 65536]");
+  if (n > ((size_t)1 << 62) / (size_t)d) return fail(RP_ERR_PARAM, "n * d overflows");
+  return RP_OK;
+}
+}  // namespace
+
+extern "C" rp_status rp_mvn(rp_engine engine, uint64_t seed, uint64_t stream, uint64_t* pos, int d, size_t n,
+                            const double* d_mu, const double* d_L, double* d_Z, double* d_X, void* cuda_stream) {
+  rp_status st = mvn_check(d, n);
+  if (st) return st;
+  if (!pos) return fail(RP_ERR_NULL, "pos is NULL");
+  if (n == 0) return RP_OK;
+  if (!d_mu || !d_L || !d_Z || !d_X) return fail(RP_ERR_NULL, "NULL device pointer");
+  st = rp_fill_normal(engine, seed, stream, pos, n * (size_t)d, d_Z, cuda_stream);
+  if (st) return st;
+  int e = rp::launch_mvn_apply(d, n, d_mu, d_L, d_Z, d_X, cuda_stream);
+  if (!e) e = (int)cudaStreamSynchronize((cudaStream_t)cuda_stream);
+  if (e) return cuda_fail(e, "mvn apply");
+  g_launches.fetch_add(1);
+  return RP_OK;
+}
+
+extern "C" rp_status rp_mvn_grads(int d, size_t n, const double* d_G, const double* d_Z, double* d_gmu, double* d_gL,
+                                  void* cuda_stream) {
+  rp_status st = mvn_check(d, n);
+  if (st) return st;
+  if (!d_gmu || !d_gL) return fail(RP_ERR_NULL, "NULL device pointer");
+  if (n && (!d_G || !d_Z)) return fail(RP_ERR_NULL, "NULL device pointer");
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (n == 0) {
+    int e = (int)cudaMemsetAsync(d_gmu, 0, (size_t)d * 8, (cudaStream_t)cuda_stream);
+    if (!e) e = (int)cudaMemsetAsync(d_gL, 0, (size_t)d * d * 8, (cudaStream_t)cuda_stream);
+    if (!e) e = (int)cudaStreamSynchronize((cudaStream_t)cuda_stream);
+    return e ? cuda_fail(e, "mvn grads") : RP_OK;
+  }
+  unsigned long long slice = 0;
+  const size_t slices = (size_t)rp::mvn_grad_slices(d, n, &slice);
+  const size_t need = slices * (size_t)d * (size_t)d;
+  if (need > g_mvn_cap) {
+    if (g_mvn_part) cudaFree(g_mvn_part);
+    g_mvn_part = nullptr;
+    g_mvn_cap = 0;
+    int e = (int)cudaMalloc((void**)&g_mvn_part, need * sizeof(double));
+    if (e) return fail(RP_ERR_NOMEM, "mvn gradient scratch allocation failed");
+    g_mvn_cap = need;
+  }
+  int e = rp::launch_mvn_grads(d, n, d_G, d_Z, d_gmu, d_gL, g_mvn_part, cuda_stream);
+  if (!e) e = (int)cudaStreamSynchronize((cudaStream_t)cuda_stream);
+  if (e) return cuda_fail(e, "mvn grads");
+  g_launches.fetch_add(4);
+  return RP_OK;
+}

@@ -135,6 +135,12 @@ constexpr size_t kStaticWords = kStaticCtrlWords + kStaticTiles + kStaticTailCap
 static_assert(sizeof(Ctrl) <= kStaticCtrlWords * 8, "control block does not fit its slot");
 static_assert(sizeof(TailEntry) % 8 == 0, "tail entries must be whole words");
 int static_scratch_address(void** p);
+// Multivariate normal (rp_mvn.cu).
+int launch_mvn_apply(int d, unsigned long long n, const double* mu, const double* L, const double* Z, double* X,
+                     void* stream);
+int mvn_grad_slices(int d, unsigned long long n, unsigned long long* slice);
+int launch_mvn_grads(int d, unsigned long long n, const double* G, const double* Z, double* gmu, double* gL,
+                     double* part, void* stream);
 // Tile geometry and resources of a (engine, dist) kernel.
 struct TileGeom { int nt, c, tile_words, smem_bytes; };
 TileGeom tile_geom(int engine, int dist);

@@ -62,3 +62,14 @@ def mixed_requests(n_req, seed, max_n=20000):
 def upstream_grads(n, seed=1):
     """Upstream gradients dL/dz ~ N(0, 1)."""
     return np.random.default_rng(seed).standard_normal(n)
+
+
+def mvn_inputs(d, seed=3):
+    """Mean and Cholesky factor of the multivariate-normal workload:
+    Sigma = W W^T / d + 0.1 I with W a d x d standard-normal matrix, mu ~
+    N(0, 1); L = chol(Sigma) (LAPACK through NumPy)."""
+    rng = np.random.default_rng(seed)
+    W = rng.standard_normal((d, d))
+    mu = rng.standard_normal(d)
+    sigma = W @ W.T / d + 0.1 * np.eye(d)
+    return mu, np.linalg.cholesky(sigma)
