@@ -235,6 +235,11 @@ def run_gpu(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args.cpu_sample)
+    extras = None
+    if rank == 0 and not args.no_extras and not args.only and args.log2n == 28:
+        del out_f, out_u
+        torch.cuda.empty_cache()
+        extras = run_extras(rp, stream)
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "variates/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -245,13 +250,127 @@ def run_gpu(args):
                            "parallelism": f"independent streams x{world}",
                            **({"profiling_subset": args.only or f"n=2^{args.log2n}"}
                               if (args.only or args.log2n != 28) else {})},
-                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "extras": extras,
                 "clocks": clk}
         print(json.dumps(line))
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
         dist.destroy_process_group()
+
+
+def _ev_ms(stream, fn, reps=1):
+    """Device time of fn() on `stream` (CUDA events), min over reps."""
+    import torch
+    best = None
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        fn()
+        b.record(stream)
+        b.synchronize()
+        ms = a.elapsed_time(b)
+        best = ms if best is None else min(best, ms)
+    return best
+
+
+def run_extras(rp, stream):
+    """The other workloads, each timed after one untimed run: config 1 (2^20
+    words then 2^20 uniforms, xoshiro seed 12345), gamma/beta at n = 2^26
+    with their pathwise gradients (xoshiro seed 7, upstream g ~ N(0,1)), the
+    batched substream workload (4096 requests, autotuned graph plan, against
+    per-request launches) and the multivariate normal (d = 64, 512; n = 2^20)."""
+    import numpy as np
+    import torch
+
+    from paper_2605_05099_gb300 import inputs
+    ex = {}
+    # config 1
+    w = torch.empty(1 << 20, dtype=torch.uint64, device="cuda")
+    u = torch.empty(1 << 20, dtype=torch.float64, device="cuda")
+
+    def c1():
+        p = rp.rp_fill_u64("xoshiro256pp", 12345, rp.NO_STREAM, 0, w, stream)
+        rp.rp_fill_uniform("xoshiro256pp", 12345, rp.NO_STREAM, p, u, stream)
+    c1()
+    ms = _ev_ms(stream, c1, reps=5)
+    ex["config1_words_then_uniforms"] = {"variates_per_s": 2 * (1 << 20) / (ms / 1e3), "ms": ms}
+    del w, u
+    # gamma / beta forward and gradients (config 3)
+    n = 1 << 26
+    z = torch.empty(n, dtype=torch.float64, device="cuda")
+    g = torch.tensor(inputs.upstream_grads(n), device="cuda")
+    dz = torch.empty_like(z)
+    fwd, grads = {}, {}
+    for a_ in (0.3, 1.0, 2.5, 30.0):
+        f = lambda: rp.rp_fill_gamma("xoshiro256pp", 7, rp.NO_STREAM, 0, a_, z, stream)
+        f()
+        ms = _ev_ms(stream, f)
+        fwd[f"gamma({a_})"] = n / (ms / 1e3)
+        bg = lambda: rp.rp_gamma_grad(z, a_, g, dz, stream)
+        bg()
+        grads[f"gamma({a_})"] = n / (_ev_ms(stream, bg) / 1e3)
+    dz2 = torch.empty_like(z)
+    for ab in ((0.5, 0.5), (2.0, 5.0)):
+        f = lambda: rp.rp_fill_beta("xoshiro256pp", 7, rp.NO_STREAM, 0, ab[0], ab[1], z, stream)
+        f()
+        fwd[f"beta{ab}"] = n / (_ev_ms(stream, f) / 1e3)
+        bg = lambda: rp.rp_beta_grad(z, ab[0], ab[1], g, dz, dz2, stream)
+        bg()
+        grads[f"beta{ab}"] = n / (_ev_ms(stream, bg) / 1e3)
+    ex["gamma_beta_fill"] = {"unit": "variates/s", "n": n, **{k: round(v) for k, v in fwd.items()}}
+    ex["gamma_beta_grads"] = {"unit": "grads/s (per-sample dz/dtheta and the reduced sum)", "n": n,
+                              **{k: round(v) for k, v in grads.items()}}
+    del z, g, dz, dz2
+    torch.cuda.empty_cache()
+    # batched substreams (config 4)
+    reqs = inputs.batch_workload()
+    tot = sum(r["n"] for r in reqs)
+    outs = [torch.empty(r["n"], dtype=torch.float64, device="cuda") for r in reqs]
+    arr = rp.make_requests([dict(r, out=o) for r, o in zip(reqs, outs)])
+    b = {}
+    for eng in ("xoshiro256pp", "philox4x32_10"):
+        plan = rp.BatchPlan(arr, eng, 99, autotune=True, cuda_stream=stream)
+        info = plan.info()
+        ms = _ev_ms(stream, lambda: plan.run(stream), reps=2)
+        plan.close()
+        words = [rp.rp_substream_state(eng, 99, r["stream"]) for r in reqs]
+
+        def per_request():
+            for r, o, wd in zip(reqs, outs, words):
+                rp.rp_fill_state(eng, wd, 0, r["dist"], o, r["p0"], r["p1"], r["m"], stream)
+        ms_pr = _ev_ms(stream, per_request)
+        b[eng] = {"variates_per_s": tot / (ms / 1e3), "ms": ms, "per_request_ms": ms_pr,
+                  "speedup_vs_per_request": ms_pr / ms, "schedule": info["schedule"], "items": info["items"]}
+    ex["batch_substreams"] = {"requests": len(reqs), "variates": tot, **b}
+    del outs, arr
+    torch.cuda.empty_cache()
+    # multivariate normal (config 5)
+    m = {}
+    n = 1 << 20
+    for d in (64, 512):
+        mu_h, L_h = inputs.mvn_inputs(d)
+        mu, L = torch.tensor(mu_h, device="cuda"), torch.tensor(L_h, device="cuda")
+        Z = torch.empty((n, d), dtype=torch.float64, device="cuda")
+        X = torch.empty_like(Z)
+        G = torch.tensor(np.random.default_rng(3).standard_normal((n, d)), device="cuda")
+        gmu = torch.empty(d, dtype=torch.float64, device="cuda")
+        gL = torch.empty((d, d), dtype=torch.float64, device="cuda")
+        f = lambda: rp.rp_mvn("xoshiro256pp", 3, 1, 0, mu, L, Z, X, stream)
+        f()
+        ms_f = _ev_ms(stream, f)
+        bg = lambda: rp.rp_mvn_grads(G, Z, gmu, gL, stream)
+        bg()
+        ms_b = _ev_ms(stream, bg)
+        fl = 2.0 * n * d * (d + 1) / 2  # triangular L: d (d + 1) / 2 multiply-adds per sample
+        m[f"d={d}"] = {"samples_per_s_fwd": n / (ms_f / 1e3), "ms_fwd": ms_f, "ms_bwd": ms_b,
+                       "fwd_fp64_tflops_incl_fill": fl / (ms_f / 1e3) / 1e12,
+                       "bwd_fp64_tflops": fl / (ms_b / 1e3) / 1e12}
+        del Z, X, G
+        torch.cuda.empty_cache()
+    ex["mvn"] = {"n": n, **m}
+    return ex
 
 
 def cpu_baseline(sample):
@@ -308,6 +427,7 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=None,
                     help="oracle variates per fill (default 2^24 for the baseline leg, 2^21 per reference step)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the other workloads (batch, gamma, MVN)")
     ap.add_argument("--only", default=None,
                     help="profiling: run only this fill (e.g. xoshiro256pp/normal); not a bench line")
     ap.add_argument("--log2n", type=int, default=28, help="profiling: n = 2^log2n per fill (bench: 28)")
