@@ -465,6 +465,22 @@ static dd dd_exp(double x) {
 }
 
 static dd dd_log(double y) {
+  if (y > 0.9375 && y < 1.0625) {
+    /* near 1 the Newton step below is accurate only to ~2^-100 absolute,
+     * not relative: sum the series log(1 + r) = r - r^2/2 + r^3/3 - ...
+     * with r = y - 1 exact (Sterbenz), |r| < 2^-4, until the terms fall
+     * below 2^-112 |r| */
+    dd r = {y - 1.0, 0.0};
+    dd pk = r, sum = r;
+    for (int k = 2; k < 60; ++k) {
+      pk = dd_mul(pk, r);
+      dd term = dd_div_d(pk, (double)k);
+      if (k % 2 == 0) term = (dd){-term.hi, -term.lo};
+      sum = dd_add(sum, term);
+      if (fabs(term.hi) < ldexp(fabs(r.hi), -112)) break;
+    }
+    return sum;
+  }
   double y0 = log(y);
   dd t = dd_exp(-y0);
   dd z = dd_mul_d(t, y);

@@ -105,12 +105,22 @@ def test_cr_exp_log_against_mpmath(orc):
     orc.lib().or_cr_reset()
     for x in xs:
         assert orc.cr_exp(x) == float(mp.exp(mp.mpf(float(x)))), x
-    ys = np.concatenate([rng.uniform(0, 1, 3000), rng.uniform(0, 30, 1000), np.exp(rng.uniform(-700, 700, 500))])
+    # near 1 the result is tiny: a log accurate only in absolute terms fails here
+    near1 = np.concatenate([1.0 - rng.integers(1, 2**20, 1500) * 2.0**-53, 1.0 + rng.integers(1, 2**20, 500) * 2.0**-52,
+                            rng.uniform(0.9, 1.1, 1000)])
+    ys = np.concatenate([rng.uniform(0, 1, 3000), rng.uniform(0, 30, 1000), np.exp(rng.uniform(-700, 700, 500)), near1])
     for y in ys:
         if y > 0:
             assert orc.cr_log(y) == float(mp.log(mp.mpf(float(y)))), y
     assert orc.cr_ambiguous() == 0
     assert orc.cr_log(0.0) == -math.inf and orc.cr_exp(0.0) == 1.0
+    # 1 -+ 2^-k put log within 2^-150 of a rounding tie: checked at 150 digits
+    mp.mp.dps = 150
+    for k in range(1, 54):
+        for y in (1.0 - 2.0**-k, 1.0 + 2.0**-k):
+            if y != 1.0:
+                assert orc.cr_log(y) == float(mp.log(mp.mpf(y))), y
+    orc.lib().or_cr_reset()   # these are flagged ambiguous by construction
 
 
 # ------------------------------------------------------------------ ziggurat
@@ -171,6 +181,7 @@ def test_ziggurat_rates_and_distribution(orc, dist):
     paper's printed rates (golden) are recorded; the exponential one agrees,
     the PDF-evaluation rates agree to the printed precision."""
     gold = _gold("paper_ziggurat_rates.json")[dist]
+    orc.lib().or_cr_reset()
     n = 1 << 21
     g = orc.gen("xoshiro256pp", 2024)
     x = orc.fill(g, dist, n)
