@@ -129,7 +129,8 @@ rp_status rp_fill_state(rp_engine engine, const uint64_t* words, uint64_t* pos, 
                         double p0, double p1, uint64_t m, void* d_out, void* cuda_stream);
 
 /* State words of substream s of base_seed, the paper's recipe for parallel
- * simulations (Sec. 2.3, "duplicate, then jump or set the stream"): the
+ * simulations (Sec. 2.3: copy a base generator, then jump it or set its
+ * stream): the
  * base state is seeded from base_seed with no spawn key; xoshiro256++ jumps
  * it by s * 2^128 words, Philox4x32-10 sets its key to s, PCG64-DXSM sets
  * its increment to 2 s + 1.  words must hold 4 entries; *nw receives the
@@ -254,6 +255,11 @@ rp_status rp_seed_state(rp_engine engine, uint64_t seed, uint64_t stream, uint64
  * transition matrix (the same map as the jump polynomial of Sec. 4.4), LCG
  * skip-ahead for PCG64 (Sec. 2.3), counter offset for Philox (delta even). */
 rp_status rp_jump_state(rp_engine engine, uint64_t* words, uint64_t delta_hi, uint64_t delta_lo);
+
+/* The library's correctly rounded natural log of n device doubles (d_y[i] =
+ * RN(log d_x[i])), the routine behind the gamma boost and the ziggurat tail
+ * values (Sec. 4.2 exactness, read as correct rounding).  For checks. */
+rp_status rp_log_cr(const double* d_x, double* d_y, size_t n, void* cuda_stream);
 
 /* Message of the last failed call on this host thread ("" if none). */
 const char* rp_last_error(void);

@@ -66,6 +66,7 @@ def lib():
             "rp_fill_state": [i32, pu64, pu64, i32, sz, dbl, dbl, u64, vp, vp],
             "rp_mvn": [i32, u64, u64, pu64, i32, sz, vp, vp, vp, vp, vp],
             "rp_mvn_grads": [i32, sz, vp, vp, vp, vp, vp],
+            "rp_log_cr": [vp, vp, sz, vp],
             "rp_substream_state": [i32, u64, u64, pu64, ctypes.POINTER(i32)],
             "rp_batch_plan_create": [ctypes.POINTER(Request), sz, i32, u64, i32, ctypes.POINTER(vp), vp],
             "rp_batch_plan_run": [vp, pu64, vp],
@@ -361,6 +362,15 @@ class MVN(torch.autograd.Function):
         gL = torch.empty((d, d), dtype=torch.float64, device="cuda")
         rp_mvn_grads(G.to(torch.float64).contiguous(), Z, gmu, gL)
         return gmu, gL, None, None, None, None, None
+
+
+def rp_log_cr(x, y=None, cuda_stream=None):
+    """Correctly rounded log of a float64 CUDA tensor (element-wise)."""
+    if y is None:
+        y = torch.empty_like(x)
+    n = x.numel()
+    _check(lib().rp_log_cr(_f64(x, x.shape, "x"), _f64(y, x.shape, "y"), n, _stream_handle(cuda_stream)))
+    return y
 
 
 def rp_seed_state(engine, seed, stream=NO_STREAM):

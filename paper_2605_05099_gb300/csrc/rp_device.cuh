@@ -150,8 +150,23 @@ __device__ __noinline__ static dd dd_exp_dev(double x) {
   return {ldexp(p.hi, ki), ldexp(p.lo, ki)};
 }
 
-// log(y), y > 0, by one Newton step on exp from the libm value.
+// log(y), y > 0: near 1 the series r - r^2/2 + r^3/3 - ... in double-double
+// (r = y - 1 exact, |r| < 2^-4; relative accuracy, where a Newton step on
+// exp would only be accurate in absolute terms), elsewhere one Newton step on
+// exp from the libm value.
 __device__ __noinline__ static dd dd_log_dev(double y) {
+  if (y > 0.9375 && y < 1.0625) {
+    const dd r = {__dsub_rn(y, 1.0), 0.0};
+    dd pk = r, sum = r;
+    for (int k = 2; k < 60; ++k) {
+      pk = dd_mulx(pk, r);
+      dd term = dd_scale_inv(pk, (double)k);
+      if (k & 1) sum = dd_addx(sum, term);
+      else sum = dd_addx(sum, {-term.hi, -term.lo});
+      if (fabs(term.hi) < ldexp(fabs(r.hi), -112)) break;
+    }
+    return sum;
+  }
   double y0 = log(y);
   dd e = dd_exp_dev(-y0);
   dd z = dd_addx(dd_mulx(e, {y, 0.0}), {-1.0, 0.0});
@@ -171,6 +186,49 @@ __device__ __forceinline__ double cr_log_dev(double y) {
   if (y == 0.0) return -__longlong_as_double(0x7ff0000000000000ll);
   return dd_log_dev(y).hi;
 }
+
+// Correctly rounded log of a positive normal double, fast path: Tang's
+// table-driven reduction y = 2^e m, r = m inv_j - 1 (exact in one fused
+// multiply-add, |r| <= 2^-10), log y = e ln2 - log(inv_j) + log1p(r) with
+// log1p(r) = r + r^2 q(r) (degree 7, truncation below 2^-83), summed as a
+// double-double whose error is below 2^-69 absolute (below 2^-49 |q| r^2
+// when the result is r + r^2 q(r) alone).  Ziv's rounding test: if both ends
+// of the error interval round to the same double, that double is the
+// correctly rounded log; otherwise the double-double Newton log decides.
+#include "log_table.inc"
+
+__device__ __forceinline__ double cr_log_fast(double y) {
+  const long long b = __double_as_longlong(y);
+  const int be = (int)((b >> 52) & 0x7ff);
+  if (!(y > 0.0) || y == 1.0 || be == 0 || be == 0x7ff) return cr_log_dev(y);   // 0, 1, subnormal, inf: general path
+  const int j = (int)((b >> 42) & 0x3ff);
+  const double m = __longlong_as_double((b & 0x000fffffffffffffll) | 0x3ff0000000000000ll);
+  const double inv = g_log_tab[j][0];
+  const double Lh = g_log_tab[j][1], Ll = g_log_tab[j][2];
+  const double e = (double)(be - 1023 + (j == 1023 ? 1 : 0));
+  const double r = __fma_rn(m, inv, -1.0);
+  const double r2 = __dmul_rn(r, r);
+  double q = __dadd_rn(-1.0 / 6.0, __dmul_rn(r, 1.0 / 7.0));
+  q = __dadd_rn(0.2, __dmul_rn(r, q));
+  q = __dadd_rn(-0.25, __dmul_rn(r, q));
+  q = __dadd_rn(1.0 / 3.0, __dmul_rn(r, q));
+  q = __dadd_rn(-0.5, __dmul_rn(r, q));
+  const double p = __dmul_rn(r2, q);
+  const double LN2_HI = 0x1.62e42fefa3800p-1, LN2_LO = 0x1.ef35793c76730p-45;
+  const double A = __dmul_rn(e, LN2_HI);   // exact: 42-bit constant, |e| < 2^11
+  dd s = dd_two_sum(A, Lh);
+  dd t = dd_two_sum(s.hi, r);
+  const double lo = __dadd_rn(__dadd_rn(s.lo, t.lo), __dadd_rn(__dmul_rn(e, LN2_LO), __dadd_rn(Ll, p)));
+  const dd v = dd_quick(t.hi, lo);
+  const double eps = (e == 0.0 && Lh == 0.0) ? __dadd_rn(__dmul_rn(fabs(p), 0x1.0p-49), 0x1.0p-1070) : 0x1.0p-69;
+  const double up = __dadd_rn(v.hi, __dadd_rn(v.lo, eps));
+  const double dn = __dadd_rn(v.hi, __dsub_rn(v.lo, eps));
+  if (up == dn) return up;
+  return cr_log_dev(y);
+}
+
+// Out-of-line copy for the samplers (keeps their register count down).
+__device__ __noinline__ static double cr_log_nl(double y) { return cr_log_fast(y); }
 
 // Exact decision y < RN(exp(t)): CUDA exp (max error a few ulp) decides
 // unless y lies within 2^-48 relative of it; then the correctly rounded value

@@ -100,8 +100,8 @@ __device__ __forceinline__ bool tail_pair_accept(u64 w1, u64 w2, const ZigDev& z
   double mg = (l2 + r2) * 0x1.0p-48;
   if (l2 > r2 + mg) return true;
   if (l2 < r2 - mg) return false;
-  a = __ddiv_rn(-cr_log_dev(o1), z.R);
-  b = -cr_log_dev(o2);
+  a = __ddiv_rn(-cr_log_nl(o1), z.R);
+  b = -cr_log_nl(o2);
   return __dadd_rn(b, b) > __dmul_rn(a, a);
 }
 
@@ -457,7 +457,7 @@ __device__ bool merge_tile(const FillArgs& a, u64 k, const E& e, MergeSmem<NT>& 
 }
 
 template <int NT, int C, class E, class S>
-__global__ void __launch_bounds__(NT) k_merge(FillArgs a) {
+__global__ void __launch_bounds__(NT, 512 / NT) k_merge(FillArgs a) {
   __shared__ MergeSmem<NT> sm;
   E e;
   e.init_tile(a.eng, blockIdx.x, threadIdx.x, sm.sh4);
@@ -484,7 +484,7 @@ __global__ void __launch_bounds__(NT) k_onepw_batch(BatchArgs b) {
 }
 
 template <int NT, int C, class E>
-__global__ void __launch_bounds__(NT) k_merge_batch(BatchArgs b) {
+__global__ void __launch_bounds__(NT, 512 / NT) k_merge_batch(BatchArgs b) {
   __shared__ MergeSmem<NT> sm;
   __shared__ FillArgs fa;
   __shared__ unsigned long long slot;

@@ -28,7 +28,7 @@ __device__ __forceinline__ double normal_x_exact(int xk, u64 xa, u64 xb, const Z
     int i = (int)(xa & 0xff);
     return neg_if(mul_rn_dmul((xa >> 9) & ((1ull << 52) - 1), z.w[i]), (xa >> 8) & 1);
   }
-  double a = __ddiv_rn(-cr_log_dev(__dsub_rn(1.0, u53_bits(xb))), z.R);
+  double a = __ddiv_rn(-cr_log_nl(__dsub_rn(1.0, u53_bits(xb))), z.R);
   return neg_if(__dadd_rn(z.R, a), (xa >> 8) & 1);
 }
 
@@ -75,8 +75,8 @@ static __device__ bool mt_accept_exact(int xk, u64 xa, u64 xb, u64 u, const MTPa
   double marg = 0x1.0p-48 * (fabs(lu) + p.d * (fabs(lv) + fabs(s)) + fabs(ds) + fabs(rhs));
   if (lu < rhs - marg) return true;
   if (lu > rhs + marg) return false;
-  rhs = __dadd_rn(__dmul_rn(0.5, x2), __dmul_rn(p.d, __dadd_rn(om, cr_log_dev(v))));
-  return cr_log_dev(U) < rhs;
+  rhs = __dadd_rn(__dmul_rn(0.5, x2), __dmul_rn(p.d, __dadd_rn(om, cr_log_nl(v))));
+  return cr_log_nl(U) < rhs;
 }
 
 // Marsaglia-Tsang accept test, FP32 first.  Squeeze: x_f relative 2^-20 so
@@ -116,7 +116,7 @@ __device__ __forceinline__ double gamma_value(int xk, u64 xa, u64 xb, u64 ub, co
   v = __dmul_rn(__dmul_rn(v, v), v);
   double g = __dmul_rn(p.d, v);
   if (p.boost) {
-    double t = __ddiv_rn(cr_log_dev(u53_bits(ub)), p.alpha);
+    double t = __ddiv_rn(cr_log_nl(u53_bits(ub)), p.alpha);
     g = __dmul_rn(g, exp(t));
   }
   return g;

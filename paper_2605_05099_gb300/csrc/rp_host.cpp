@@ -1506,3 +1506,12 @@ extern "C" rp_status rp_mvn_grads(int d, size_t n, const double* d_G, const doub
   g_launches.fetch_add(4);
   return RP_OK;
 }
+
+extern "C" rp_status rp_log_cr(const double* d_x, double* d_y, size_t n, void* cuda_stream) {
+  if (n && (!d_x || !d_y)) return fail(RP_ERR_NULL, "NULL device pointer");
+  int e = rp::launch_log_cr(d_x, d_y, n, cuda_stream);
+  if (!e) e = (int)cudaStreamSynchronize((cudaStream_t)cuda_stream);
+  if (e) return cuda_fail(e, "log");
+  g_launches.fetch_add(1);
+  return RP_OK;
+}

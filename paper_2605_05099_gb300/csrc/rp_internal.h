@@ -135,6 +135,7 @@ constexpr size_t kStaticWords = kStaticCtrlWords + kStaticTiles + kStaticTailCap
 static_assert(sizeof(Ctrl) <= kStaticCtrlWords * 8, "control block does not fit its slot");
 static_assert(sizeof(TailEntry) % 8 == 0, "tail entries must be whole words");
 int static_scratch_address(void** p);
+int launch_log_cr(const double* x, double* y, unsigned long long n, void* stream);
 // Multivariate normal (rp_mvn.cu).
 int launch_mvn_apply(int d, unsigned long long n, const double* mu, const double* L, const double* Z, double* X,
                      void* stream);

@@ -101,6 +101,19 @@ int launch_beta_pairs(const double* g, double* out, unsigned long long m, void* 
   return (int)cudaGetLastError();
 }
 
+// The library's correctly rounded log, element-wise (a check of the value
+// path used by the gamma boost and the normal tails).
+__global__ void k_log_cr(const double* __restrict__ x, double* __restrict__ y, unsigned long long n) {
+  for (unsigned long long i = blockIdx.x * (u64)blockDim.x + threadIdx.x; i < n; i += (u64)gridDim.x * blockDim.x)
+    y[i] = cr_log_fast(x[i]);
+}
+
+int launch_log_cr(const double* x, double* y, unsigned long long n, void* stream) {
+  if (!n) return 0;
+  k_log_cr<<<608, 256, 0, (cudaStream_t)stream>>>(x, y, n);
+  return (int)cudaGetLastError();
+}
+
 int occupancy_blocks(int engine, int dist) {
   FillArgs a{};
   a.eng.engine = engine;

@@ -40,7 +40,7 @@ def check(dist, engine, seed, n, params, ulp, pos=0, stream=None):
 
 
 @pytest.mark.parametrize("engine", ENGINES)
-@pytest.mark.parametrize("alpha", [0.3, 1.0, 2.5, 30.0])
+@pytest.mark.parametrize("alpha", [0.1, 0.3, 1.0, 2.5, 30.0])
 def test_gamma_parity(engine, alpha):
     ulp = 0 if alpha >= 1 else 2
     for n in SIZES:
