@@ -134,7 +134,7 @@ struct LeanChain {
 // multi-word candidate.  Output positions are marked in the bitmap (`mw` is
 // mask word b, still in a register; earlier words are in shared memory).
 template <int NT, class S>
-__device__ __forceinline__ void lean_rare(u64 u, int p, int b, unsigned& mw, LeanChain& c, const ZigDev& z,
+__device__ __forceinline__ void lean_rare(u64 u, int p, int b, unsigned& mw, LeanChain& c, const LeanTab& tb, const ZigDev& z,
                                           unsigned (*msk)[NT], u64* queue, u64 (*tails)[3], int* ntails,
                                           Ctrl* ctrl, u64 k) {
   const int t = threadIdx.x;
@@ -153,7 +153,8 @@ __device__ __forceinline__ void lean_rare(u64 u, int p, int b, unsigned& mw, Lea
     }
   };
   if (c.st == 0) {
-    if (S::fast_exact(u, z)) { mark(p); return; }   // top bits tied with the bound
+    // a candidate that missed the 32-bit test: only equal top bits need the full compare
+    if ((unsigned)(u >> 29) == tb.khi[u & 0xff] && S::fast_exact(u, z)) { mark(p); return; }
     c.pu0 = u;
     c.pp = p;
     c.st = (u & 0xff) ? 1 : (S::kTailPairs ? 2 : 4);
@@ -190,7 +191,7 @@ __device__ __forceinline__ void lean_step(u64 u, int p, int b, unsigned& mw, Lea
                                           int* ntails, Ctrl* ctrl, u64 k) {
   const unsigned rh = (unsigned)(u >> 29), kh = tb.khi[u & 0xff];
   if (c.st == 0 && rh < kh) mw |= 1u << (p & 31);
-  else lean_rare<NT, S>(u, p, b, mw, c, z, msk, queue, tails, ntails, ctrl, k);
+  else lean_rare<NT, S>(u, p, b, mw, c, tb, z, msk, queue, tails, ntails, ctrl, k);
 }
 
 // Staged rows -> output: row r of the warp holds lane r's `cnt` (<= 16)
@@ -429,7 +430,7 @@ __device__ bool lean_tile(const FillArgs& a, u64 k, const E& e, LeanSmem<NT, C>&
 }
 
 template <int NT, int C, class E, class S>
-__global__ void __launch_bounds__(NT, 8) k_lean(FillArgs a) {
+__global__ void __launch_bounds__(NT, 6) k_lean(FillArgs a) {
   __shared__ LeanSmem<NT, C> sm;
   __shared__ LeanTab tb;
   lean_load_tab<S>(tb, NT);
