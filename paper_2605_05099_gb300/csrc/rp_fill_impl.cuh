@@ -111,13 +111,26 @@ __device__ __forceinline__ bool tail_pair_accept(u64 w1, u64 w2, const ZigDev& z
 // One word per variate: raw words and 53-bit uniforms.
 struct SampU64 {
   static constexpr bool kOnePerWord = true;
+  static constexpr bool kCheckReject = false;
   typedef u64 out_t;
   __device__ static __forceinline__ u64 value1(u64 u, const SampArgs&) { return u; }
 };
 struct SampUniform {
   static constexpr bool kOnePerWord = true;
+  static constexpr bool kCheckReject = false;
   typedef double out_t;
   __device__ static __forceinline__ double value1(u64 u, const SampArgs&) { return u53_bits(u); }
+};
+
+// Lemire with no rejection assumed: word p gives output p, hi(u m); every
+// word whose low product falls below 2^64 mod m is reported, and the host
+// keeps the outputs before the first such word (exact: the serial sampler
+// produces the same values up to its first rejection).
+struct SampBoundedOne {
+  static constexpr bool kOnePerWord = true;
+  static constexpr bool kCheckReject = true;
+  typedef u64 out_t;
+  __device__ static __forceinline__ u64 value1(u64 u, const SampArgs& a) { return __umul64hi(u, a.m); }
 };
 
 // Values of ziggurat tail outputs (FP64 libm log, within 2 ulp of the
@@ -262,7 +275,13 @@ __device__ __forceinline__ void onepw_tile(const FillArgs& a, u64 k, const E& e,
   const u64 base = k * (u64)T + (u64)t * C;
   for (int j0 = 0; j0 < C; j0 += kStage) {
 #pragma unroll
-    for (int j = 0; j < kStage; ++j) stage_w[lane * kRow + j] = S::value1(g.next(), a.sp);
+    for (int j = 0; j < kStage; ++j) {
+      const u64 u = g.next();
+      stage_w[lane * kRow + j] = S::value1(u, a.sp);
+      if constexpr (S::kCheckReject) {
+        if (u * a.sp.m < a.sp.thresh && base + j0 + j < a.n) atomicMin(&a.ctrl->first_reject, base + j0 + j);
+      }
+    }
     __syncwarp();
     flush_rows<OT>(out, stage_w, base + j0, kStage, a.n);
     __syncwarp();
@@ -587,6 +606,7 @@ int dispatch_dist(const FillArgs& a, int grid, cudaStream_t s, int* occ) {
     case D_U64: return launch_es<E, SampU64>(a, grid, s, occ);
     case D_UNIFORM: return launch_es<E, SampUniform>(a, grid, s, occ);
     case D_BOUNDED: return launch_lean<E, LeanBounded>(a, grid, s, occ);
+    case D_BOUNDED_ONE: return launch_es<E, SampBoundedOne>(a, grid, s, occ);
     case D_NORMAL: return launch_lean<E, LeanNormal>(a, grid, s, occ);
     case D_EXP: return launch_lean<E, LeanExp>(a, grid, s, occ);
     case D_GAMMA: return launch_merge<E, SampGamma>(a, grid, s, occ);

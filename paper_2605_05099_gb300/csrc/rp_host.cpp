@@ -490,7 +490,22 @@ double words_per_variate(int dist, const rp::SampArgs& sp) {
 // Fill from explicit state words (the engine at word 0 of the stream; *pos
 // words in).  Caller holds g_mu.
 rp_status run_fill_state_locked(int engine, const u64 s_in[4], u64* pos, size_t n, int dist, const rp::SampArgs& sp,
-                                void* d_out, void* cstream) {
+                                void* d_out, void* cstream, u64* first_reject = nullptr) {
+  if (dist == rp::D_BOUNDED && (double)n * ((double)sp.thresh * 0x1.0p-64) < 0.05) {
+    // Rejections are unlikely in this fill: one pass writes word p's value
+    // at output p and reports the first rejected word q.  Outputs before q
+    // are final (the serial sampler gives the same values up to its first
+    // rejection); from word q + 1 the exact two-pass fill takes over.
+    u64 q = ~0ull, p0 = *pos;
+    rp_status st = run_fill_state_locked(engine, s_in, &p0, n, rp::D_BOUNDED_ONE, sp, d_out, cstream, &q);
+    if (st) return st;
+    if (q >= n) { *pos += n; return RP_OK; }
+    u64 p1 = *pos + q + 1;
+    st = run_fill_state_locked(engine, s_in, &p1, n - q, rp::D_BOUNDED, sp, (char*)d_out + q * 8, cstream);
+    if (st) return st;
+    *pos = p1;
+    return RP_OK;
+  }
   u64 s[4] = {s_in[0], s_in[1], s_in[2], s_in[3]};
   int e = ensure_zig();
   if (e) return cuda_fail(e, "ziggurat table upload");
@@ -505,7 +520,8 @@ rp_status run_fill_state_locked(int engine, const u64 s_in[4], u64* pos, size_t 
   auto key = std::make_pair(engine, dist);
   if (!g_occ.count(key)) g_occ[key] = rp::occupancy_blocks(engine, dist);
   int occ = g_occ[key] > 0 ? g_occ[key] : 1;
-  const bool trivial = (dist == rp::D_U64 || dist == rp::D_UNIFORM);
+  const bool trivial = (dist == rp::D_U64 || dist == rp::D_UNIFORM || dist == rp::D_BOUNDED_ONE);
+  const bool one_pass_check = dist == rp::D_BOUNDED_ONE;
 
   u64 cur = *pos;
   size_t done = 0;
@@ -547,7 +563,7 @@ rp_status run_fill_state_locked(int engine, const u64 s_in[4], u64* pos, size_t 
     a.n = left;
     a.n_tiles = tiles;
     a.out = (char*)d_out + done * esz;
-    if (!trivial) {
+    if (!trivial || one_pass_check) {
       e = ensure_scratch(tiles);
       const bool queued = dist == rp::D_NORMAL || dist == rp::D_EXP || dist == rp::D_GAMMA || dist == rp::D_BETA;
       if (!e && queued) e = ensure_tailq(left / 256 + 4096);
@@ -560,6 +576,7 @@ rp_status run_fill_state_locked(int engine, const u64 s_in[4], u64* pos, size_t 
       rp::Ctrl c0;
       memset(&c0, 0, sizeof(c0));
       c0.done_tile = ~0ull;
+      c0.first_reject = ~0ull;
       e = (int)cudaMemsetAsync(g_scr.status, 0, tiles * 8, (cudaStream_t)cstream);
       if (!e) e = (int)cudaMemcpyAsync(g_scr.ctrl, &c0, sizeof(c0), cudaMemcpyHostToDevice, (cudaStream_t)cstream);
       if (e) return cuda_fail(e, "scratch reset");
@@ -573,8 +590,11 @@ rp_status run_fill_state_locked(int engine, const u64 s_in[4], u64* pos, size_t 
       g_launches.fetch_add(1);
     }
     if (trivial) {
-      e = (int)cudaStreamSynchronize((cudaStream_t)cstream);
+      if (one_pass_check)
+        e = (int)cudaMemcpyAsync(g_scr.h_ctrl, g_scr.ctrl, sizeof(rp::Ctrl), cudaMemcpyDeviceToHost, (cudaStream_t)cstream);
+      if (!e) e = (int)cudaStreamSynchronize((cudaStream_t)cstream);
       if (e) return cuda_fail(e, "fill");
+      if (one_pass_check && first_reject) *first_reject = g_scr.h_ctrl->first_reject;
       done = n;
       cur += left;
       break;

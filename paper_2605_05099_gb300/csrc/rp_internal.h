@@ -6,7 +6,8 @@
 
 namespace rp {
 
-enum Dist : int { D_U64 = 0, D_UNIFORM = 1, D_BOUNDED = 2, D_NORMAL = 3, D_EXP = 4, D_GAMMA = 5, D_BETA = 6 };
+enum Dist : int { D_U64 = 0, D_UNIFORM = 1, D_BOUNDED = 2, D_NORMAL = 3, D_EXP = 4, D_GAMMA = 5, D_BETA = 6,
+                  D_BOUNDED_ONE = 7 };   // bounded, one pass that assumes no rejection (records the first one)
 
 // Device error bits (ctrl->err)
 enum : unsigned {
@@ -26,6 +27,7 @@ struct Ctrl {
   unsigned int pad;
   unsigned long long err_info;
   unsigned long long n_tail;      // entries in the tail queue
+  unsigned long long first_reject;   // D_BOUNDED_ONE: first rejected word (relative; init ~0)
 };
 
 // Deferred output whose value needs FP64 libm (ziggurat tails): output

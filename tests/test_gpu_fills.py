@@ -111,3 +111,21 @@ def test_philox_bijection_matches_curand():
             c = (subseq << 64) + i
             ctr = [(c >> (32 * j)) & 0xFFFFFFFF for j in range(4)]
             assert oracle.philox(ctr, key) == [int(x) for x in buf[4 * i: 4 * i + 4]], (seed, subseq, i)
+
+
+# seeds whose first 100003 bounded words (m = 2^43 + 1, one rejection in
+# about 2.1e6 words) contain a rejection, found with the oracle, and seeds
+# without one: both sides of the one-pass shortcut for rare rejections
+REJECT_SEEDS = {"xoshiro256pp": [9, 15], "pcg64dxsm": [30, 99], "philox4x32_10": [16, 33]}
+
+
+@pytest.mark.parametrize("engine", ENGINES)
+def test_bounded_rare_rejection_one_pass_and_fallback(engine):
+    m, n = 2**43 + 1, 100003
+    for seed in REJECT_SEEDS[engine] + [1, 2]:
+        g, gpos = gpu_fill("bounded", engine, seed, None, 0, n, (m,))
+        o, opos = oracle_fill("bounded", engine, seed, None, 0, n, (m,))
+        assert gpos == opos, (engine, seed, gpos, opos)
+        assert np.array_equal(g, o), (engine, seed)
+        if seed in REJECT_SEEDS[engine]:
+            assert opos == n + 1
