@@ -31,14 +31,36 @@ WORKLOAD = "single-stream fills: engines {xoshiro256++, PCG64-DXSM, Philox4x32-1
 
 
 # DRAM bytes (read + write) per launch of the fill kernel at n = 2^28, from
-# one ncu capture at n = 2^26 scaled by outputs (profiles/k_lean_*_n2e26.md).
-# Null for any kernel without a capture of its current version.
-TRAFFIC = {
-    "philox4x32_10/normal": 2129293312,
-    "philox4x32_10/bounded:9223372036854775809": 2277019648,
-    "xoshiro256pp/normal": 2197997568,
-    "xoshiro256pp/exp": 2141146112,
-}
+# one ncu capture at n = 2^26 scaled by outputs (profiles/*_n2e26.md), by fill
+# key.  Only kernels whose current version was captured are listed.
+TRAFFIC = {}
+
+
+# Integer operations per 64-bit word of each engine, counted as 32-bit
+# operations of its definition (each 32 x 32 partial product's low and high
+# halves, adds with carry, shifts (a funnel shift is one), two-input xors):
+#   xoshiro256++  output: two 64-bit adds and a rotate (6); update: a 64-bit
+#                 shift, five 64-bit xors and a rotate (14)              -> 20
+#   PCG64-DXSM    LCG step: 128 x 64-bit multiply mod 2^128 (12 products,
+#                 ~10 carry adds) and the 128-bit increment (4); DXSM
+#                 output: or, two xor-shifts and two 64-bit multiplies  -> 42
+#   Philox4x32-10 per 128-bit block ten rounds of two 32 x 32 -> 64
+#                 products (4), four xors and two key adds              -> 50 per word
+ENGINE_OPS = {"xoshiro256pp": 20, "pcg64dxsm": 42, "philox4x32_10": 50}
+# integer lanes per SM and clock for adds, shifts and multiply-adds on this GPU
+INT_LANES_PER_SM = 64
+SMS = 152
+
+
+def words_per_output(dist, params):
+    """Expected engine words per output: ziggurat geometry (normal 1.0235,
+    exponential 1.036) and Lemire's acceptance 1 - (2^64 mod m)/2^64."""
+    if dist == "normal":
+        return 1.0235
+    if dist == "exp":
+        return 1.036
+    m = params[0]
+    return 1.0 / (1.0 - ((2**64) % m) / 2.0**64)
 
 
 def _peaks():
@@ -199,15 +221,33 @@ def run_gpu(args):
     value = variates / (ms / 1e3)
 
     # ---- roofline of the dominant kernel (the fill with the largest time)
+    # roofline of each fill: the slower of the HBM write time (8 B per
+    # output) and the engine's integer operations at peak issue; the line
+    # reports the dominant fill (largest time)
     peaks, peak_kind = _peaks()
-    key = max(per_fill_ms, key=per_fill_ms.get)
-    avg_ms = per_fill_ms[key] / args.steps
-    bytes_alg = 8.0 * N_FILL
-    achieved = bytes_alg / (avg_ms / 1e3) / 1e9
-    roof = {"bound": "hbm", "kernel": key, "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"],
-            "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4),
-            "traffic": TRAFFIC.get(key) if N_FILL == 1 << 28 else None,
-            "peak_source": peak_kind, "per_fill_ms": {k: round(v / args.steps, 4) for k, v in per_fill_ms.items()}}
+    int_peak = SMS * INT_LANES_PER_SM * peaks.get("sm_max_mhz", 2070.0) * 1e6   # ops/s
+    fracs = {}
+    best = None
+    for (e, d, p), key in zip(fills, per_fill_ms):
+        t = per_fill_ms[key] / args.steps / 1e3
+        ops = N_FILL * words_per_output(d, p) * ENGINE_OPS[e]
+        t_hbm = 8.0 * N_FILL / (peaks["hbm_gbs"] * 1e9)
+        t_alu = ops / int_peak
+        fracs[key] = round(max(t_hbm, t_alu) / t, 4)
+        if best is None or t > best[0]:
+            best = (t, key, t_hbm, t_alu, ops)
+    t, key, t_hbm, t_alu, ops = best
+    if t_alu > t_hbm:
+        roof = {"bound": "alu", "kernel": key, "achieved": round(ops / t / 1e9, 1), "peak": round(int_peak / 1e9, 1),
+                "unit": "Gops/s (32-bit integer engine operations)", "frac": round(t_alu / t, 4),
+                "peak_source": "derived: 152 SMs x 64 integer lanes x max SM clock (MEASURED_PEAKS.json sm_max_mhz)"}
+    else:
+        roof = {"bound": "hbm", "kernel": key, "achieved": round(8.0 * N_FILL / t / 1e9, 1), "peak": peaks["hbm_gbs"],
+                "unit": "GB/s", "frac": round(t_hbm / t, 4), "peak_source": peak_kind}
+    roof.update({"traffic": TRAFFIC.get(key) if N_FILL == 1 << 28 else None,
+                 "hbm_time_ms": round(t_hbm * 1e3, 4), "alu_time_ms": round(t_alu * 1e3, 4),
+                 "per_fill_ms": {k: round(v / args.steps, 4) for k, v in per_fill_ms.items()},
+                 "per_fill_roofline_frac": fracs})
 
     # ---- end to end through the public API with host buffers: each fill's
     # result is copied back to pinned host memory inside the timed region
