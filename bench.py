@@ -159,7 +159,8 @@ def run_gpu(args):
     rp.lib()
     stream = torch.cuda.current_stream()
     # ranks fill independent spawn-key streams (weak scaling, no collective on the data path)
-    spawn = rp.NO_STREAM if world == 1 else rank
+    from paper_2605_05099_gb300 import shard
+    spawn = shard.rank_spawn_key(rank, world)
     out_f = torch.empty(N_FILL, dtype=torch.float64, device="cuda")
     out_u = torch.empty(N_FILL, dtype=torch.uint64, device="cuda")
 
@@ -212,12 +213,7 @@ def run_gpu(args):
     launches = rp.rp_kernel_launches() - launches0
     ms = t0.elapsed_time(t1)
     clk = clocks.stop()
-    if world > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
-    variates = len(fills) * N_FILL * args.steps * world
+    ms, variates = shard.reduce_timing(ms, len(fills) * N_FILL * args.steps, device="cuda")
     value = variates / (ms / 1e3)
 
     # ---- roofline of the dominant kernel (the fill with the largest time)
