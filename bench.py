@@ -33,7 +33,12 @@ WORKLOAD = "single-stream fills: engines {xoshiro256++, PCG64-DXSM, Philox4x32-1
 # DRAM bytes (read + write) per launch of the fill kernel at n = 2^28, from
 # one ncu capture at n = 2^26 scaled by outputs (profiles/*_n2e26.md), by fill
 # key.  Only kernels whose current version was captured are listed.
-TRAFFIC = {}
+TRAFFIC = {
+    "philox4x32_10/bounded:9223372036854775809": 4 * 560522496,
+    "xoshiro256pp/normal": 4 * 558106112,
+    "xoshiro256pp/bounded:6": 4 * 482843392,
+    "xoshiro256pp/bounded:1000000007": 4 * 482843392,
+}
 
 
 # Integer operations per 64-bit word of each engine, counted as 32-bit
@@ -409,6 +414,62 @@ def run_extras(rp, stream):
     return ex
 
 
+def run_profile(args):
+    """One workload alone, for ncu (--profile KIND; not a bench line):
+    gamma:ALPHA, beta:A:B, grad:ALPHA (gamma gradient), mvn:D (forward and
+    backward, n = 2^20) or batch:ENGINE (4096 requests; --log2n scales the
+    request sizes' upper end).  Runs --warmup untimed and --steps timed
+    repetitions and prints their mean time."""
+    import numpy as np
+    import torch
+
+    import paper_2605_05099_gb300 as rp
+    from paper_2605_05099_gb300 import inputs
+    stream = torch.cuda.current_stream()
+    kind, _, rest = args.profile.partition(":")
+    vals = [x for x in rest.split(":") if x]
+    if kind in ("gamma", "beta", "grad"):
+        n = 1 << args.log2n
+        z = torch.empty(n, dtype=torch.float64, device="cuda")
+        if kind == "beta":
+            f = lambda: rp.rp_fill_beta("xoshiro256pp", 7, rp.NO_STREAM, 0, float(vals[0]), float(vals[1]), z, stream)
+        else:
+            a_ = float(vals[0])
+            rp.rp_fill_gamma("xoshiro256pp", 7, rp.NO_STREAM, 0, a_, z, stream)
+            if kind == "gamma":
+                f = lambda: rp.rp_fill_gamma("xoshiro256pp", 7, rp.NO_STREAM, 0, a_, z, stream)
+            else:
+                g = torch.tensor(inputs.upstream_grads(n), device="cuda")
+                dz = torch.empty_like(z)
+                f = lambda: rp.rp_gamma_grad(z, a_, g, dz, stream)
+    elif kind == "mvn":
+        d, n = int(vals[0]), 1 << 20
+        mu_h, L_h = inputs.mvn_inputs(d)
+        mu, L = torch.tensor(mu_h, device="cuda"), torch.tensor(L_h, device="cuda")
+        Z = torch.empty((n, d), dtype=torch.float64, device="cuda")
+        X = torch.empty_like(Z)
+        G = torch.tensor(np.random.default_rng(3).standard_normal((n, d)), device="cuda")
+        gmu = torch.empty(d, dtype=torch.float64, device="cuda")
+        gL = torch.empty((d, d), dtype=torch.float64, device="cuda")
+
+        def f():
+            rp.rp_mvn("xoshiro256pp", 3, 1, 0, mu, L, Z, X, stream)
+            rp.rp_mvn_grads(G, Z, gmu, gL, stream)
+    elif kind == "batch":
+        hi = 1e7 if args.log2n >= 28 else 10.0 ** (7 - (28 - args.log2n) / 2)
+        reqs = inputs.batch_workload(hi=hi)
+        outs = [torch.empty(r["n"], dtype=torch.float64, device="cuda") for r in reqs]
+        arr = rp.make_requests([dict(r, out=o) for r, o in zip(reqs, outs)])
+        plan = rp.BatchPlan(arr, vals[0] if vals else "xoshiro256pp", 99, autotune=False, cuda_stream=stream)
+        f = lambda: plan.run(stream)
+    else:
+        raise SystemExit(f"--profile {args.profile}: unknown workload")
+    for _ in range(args.warmup):
+        f()
+    ms = _ev_ms(stream, lambda: [f() for _ in range(args.steps)]) / max(args.steps, 1)
+    print(json.dumps({"profile": args.profile, "log2n": args.log2n, "ms": ms, "not_a_bench_line": True}))
+
+
 def cpu_baseline(sample):
     """The serial C oracle as it stands, one host core, on a bounded sample of
     the same workload: `sample` variates of each of the 15 fills."""
@@ -467,6 +528,7 @@ def main():
     ap.add_argument("--only", default=None,
                     help="profiling: run only this fill (e.g. xoshiro256pp/normal); not a bench line")
     ap.add_argument("--log2n", type=int, default=28, help="profiling: n = 2^log2n per fill (bench: 28)")
+    ap.add_argument("--profile", default=None, help="profiling: run one other workload alone (see run_profile)")
     args = ap.parse_args()
     global N_FILL
     N_FILL = 1 << args.log2n
@@ -474,6 +536,8 @@ def main():
         args.cpu_sample = (1 << 21) if args.impl == "reference" else (1 << 26)
     if args.impl == "reference":
         run_reference(args)
+    elif args.profile:
+        run_profile(args)
     else:
         run_gpu(args)
 
