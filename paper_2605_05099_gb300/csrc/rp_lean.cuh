@@ -412,10 +412,10 @@ __device__ bool lean_tile(const FillArgs& a, u64 k, const E& e, LeanSmem<NT, C>&
 #pragma unroll 8
           for (int j = 0; j < 16; ++j) {
             const u64 u = g2.next();
-            if ((m >> j) & 1u) {
-              row[ns] = S::value(u, tb, a.sp);
-              ++ns;
-            }
+            // branch-free: every word's value lands in the next free slot
+            // (ns <= j <= 15 < kRow), which advances only for marked words
+            row[ns] = S::value(u, tb, a.sp);
+            ns += (int)((m >> j) & 1u);
           }
         }
         __syncwarp();
