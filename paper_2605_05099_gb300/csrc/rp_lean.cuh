@@ -211,13 +211,161 @@ __device__ __forceinline__ void flush_rows16(OT* __restrict__ outb, const OT* ro
   }
 }
 
+// ------------------------------------------------------------------ bit-parallel chain
+// Pass 1 over 16-word half-blocks.  The words sit in shared memory (wb[j NT
+// + t]) with three 16-bit masks: F (fast accept), I (strip 0) and T (top bits
+// tied with the bound).  With every candidate one or two words long, the
+// positions consumed as second words follow from the non-fast mask N alone:
+// position q is consumed when q - 1 is a candidate start that is not fast,
+// K(q + 1) = N(q) and not K(q).  Inside each maximal run of N bits starting at
+// a candidate start a, the consumed positions are a + 1, a + 3, ...,
+// including the position after the run when the run length is odd.  Runs
+// starting at even and at odd positions are isolated with one addition each
+// (adding the start bit clears exactly that run), and their consumed
+// positions are the run shifted by one, masked to odd or even positions.
+// Candidate starts are the unconsumed positions.  Only normal tails (more
+// than two words) leave the bit-parallel path: the walk goes word by word
+// from the tail's first word until the chain is idle, then the bit-parallel
+// step resumes.
+
+// Wedge test for a candidate at absolute position pos with words u0, u1.
+template <int NT, class S>
+__device__ __forceinline__ void lean_push_wedge(u64 u0, u64 u1, int pos, int b, unsigned& mw, LeanChain& c,
+                                                const ZigDev& z, unsigned (*msk)[NT], u64* queue) {
+  const int t = threadIdx.x;
+  const u64 u1p = (u1 & ~0x7ffull) | (u64)pos;   // U uses bits 11-63: the position rides in the low bits
+  if (c.np < kLPend) {
+    queue[(c.np * NT + t) * 2] = u0;
+    queue[(c.np * NT + t) * 2 + 1] = u1p;
+    ++c.np;
+  } else if (S::wedge(u0, u1p, z)) {
+    if ((pos >> 5) == b) mw |= 1u << (pos & 31);
+    else msk[pos >> 5][t] |= 1u << (pos & 31);
+  }
+}
+
+// A tail output at absolute position pos (exponential: always accepted;
+// normal: its accepted pair's first word is w1).  The value needs libm, so it
+// goes to the tile's tail list.
+template <int NT>
+__device__ __forceinline__ void lean_exp_tail(u64 u0, u64 w1, int pos, int b, unsigned& mw, unsigned (*msk)[NT],
+                                              u64 (*tails)[3], int* ntails, Ctrl* ctrl, u64 k) {
+  const int t = threadIdx.x;
+  if ((pos >> 5) == b) mw |= 1u << (pos & 31);
+  else msk[pos >> 5][t] |= 1u << (pos & 31);
+  const int slot = atomicAdd(ntails, 1);
+  if (slot < kTileTails) {
+    tails[slot][0] = u0;
+    tails[slot][1] = w1;
+    tails[slot][2] = ((u64)t << 32) | (unsigned)pos;
+  } else {
+    set_err(ctrl, E_OVERFLOW, k);
+  }
+}
+
+// One half-block at absolute positions P0 .. P0 + 15, from relative position
+// `from` on (earlier positions belong to the previous chain).  The chain
+// state c carries a candidate that straddles half-blocks.
+template <int NT, class S>
+__device__ __forceinline__ void lean_half(int P0, int from, unsigned F, unsigned I, unsigned T, const u64* wb,
+                                          unsigned& mw, LeanChain& c, const LeanTab& tb, const ZigDev& z,
+                                          unsigned (*msk)[NT], u64* queue, u64 (*tails)[3], int* ntails,
+                                          Ctrl* ctrl, u64 k) {
+  const int t = threadIdx.x;
+  const int b = P0 >> 5, sh = P0 & 31;
+  while (T) {   // equal top bits: the full 52/53-bit compare decides
+    const int j = __ffs(T) - 1;
+    T &= T - 1;
+    if (S::fast_exact(wb[j * NT + t], z)) F |= 1u << j;
+  }
+  unsigned ein = 0;   // position `from` is the second word of a candidate
+  if (from == 0 && c.st != 0) {
+    if (c.st == 1) {          // wedge started on the previous half-block's last word
+      lean_push_wedge<NT, S>(c.pu0, wb[t], c.pp, b, mw, c, z, msk, queue);
+      c.st = 0;
+      ein = 1;
+    } else if (c.st == 4) {   // exponential tail likewise
+      lean_exp_tail<NT>(c.pu0, wb[t], c.pp, b, mw, msk, tails, ntails, ctrl, k);
+      c.st = 0;
+      ein = 1;
+    } else {                  // a normal tail in progress: word by word until idle
+      int j = 0;
+      do {
+        lean_step<NT, S>(wb[j * NT + t], P0 + j, b, mw, c, tb, z, msk, queue, tails, ntails, ctrl, k);
+        ++j;
+      } while (j < 16 && c.st != 0);
+      from = j;
+    }
+  }
+  while (from < 16) {
+    const unsigned range = (0xffffu << from) & 0xffffu;
+    const unsigned N = ~F & range;
+    const unsigned R = N & ~(ein << from);
+    const unsigned RS = R & ~(R << 1);
+    const unsigned Er = R & ~(R + (RS & 0x55555555u));
+    const unsigned Or = R & ~(R + (RS & 0xAAAAAAAAu));
+    const unsigned K = ((Er << 1) & 0xAAAAAAAAu) | ((Or << 1) & 0x55555555u) | (ein << from);
+    const unsigned Sc = ~K & range;   // candidate starts
+    const unsigned NS = Sc & N;       // starts that are not fast accepts
+    unsigned lim = range;
+    int t0 = 16;
+    if constexpr (S::kTailPairs) {
+      const unsigned TT = NS & I;
+      if (TT) {
+        t0 = __ffs(TT) - 1;
+        lim &= (1u << t0) - 1u;
+      }
+    }
+    mw |= (Sc & F & lim) << sh;
+    unsigned Wd = NS & lim;
+    if constexpr (!S::kTailPairs) {
+      unsigned X = Wd & I;   // exponential tails: two words, always accepted
+      Wd &= ~I;
+      while (X) {
+        const int j = __ffs(X) - 1;
+        X &= X - 1;
+        if (j == 15) { c.st = 4; c.pu0 = wb[15 * NT + t]; c.pp = P0 + 15; }
+        else lean_exp_tail<NT>(wb[j * NT + t], wb[(j + 1) * NT + t], P0 + j, b, mw, msk, tails, ntails, ctrl, k);
+      }
+    }
+    while (Wd) {
+      const int j = __ffs(Wd) - 1;
+      Wd &= Wd - 1;
+      if (j == 15) { c.st = 1; c.pu0 = wb[15 * NT + t]; c.pp = P0 + 15; }
+      else lean_push_wedge<NT, S>(wb[j * NT + t], wb[(j + 1) * NT + t], P0 + j, b, mw, c, z, msk, queue);
+    }
+    if (t0 == 16) break;
+    // a normal tail at t0: pairs (t0 + 1, t0 + 2), ... until one is accepted
+    int q = t0 + 1;
+    bool acc = false;
+    for (; q + 1 < 16; q += 2) {
+      if (tail_pair_nl(wb[q * NT + t], wb[(q + 1) * NT + t], z)) {
+        lean_exp_tail<NT>(wb[t0 * NT + t], wb[q * NT + t], P0 + t0, b, mw, msk, tails, ntails, ctrl, k);
+        acc = true;
+        q += 2;
+        break;
+      }
+    }
+    if (!acc) {   // the tail runs into the next half-block
+      c.pu0 = wb[t0 * NT + t];
+      c.pp = P0 + t0;
+      if (q < 16) { c.st = 3; c.pw1 = wb[q * NT + t]; }
+      else c.st = 2;
+      break;
+    }
+    from = q;
+    ein = 0;
+  }
+}
+
 template <int NT, int C>
 struct LeanSmem {
   static constexpr int kMW = C / 32 + 1;   // mask words: the chunk and the overhang into the next one
   static constexpr int kStageW = (NT / 32) * 32 * kRow;
   static constexpr int kQueueW = NT * kLPend * 2;
-  static constexpr int kBufW = kStageW > kQueueW ? kStageW : kQueueW;
-  __align__(16) u64 sbuf[kBufW];   // pass 1: wedge queue; pass 2: staging rows
+  static constexpr int kWordsW = NT * 16;   // pass 1: one half-block of words per thread
+  static constexpr int kBufW = kStageW > kQueueW + kWordsW ? kStageW : kQueueW + kWordsW;
+  __align__(16) u64 sbuf[kBufW];   // pass 1: wedge queue, then the half-block words; pass 2: staging rows
   unsigned msk[kMW][NT];
   u64 tails[kTileTails][3];
   int ntails[2];   // by tile parity: reset one tile after use, behind a barrier
@@ -284,20 +432,27 @@ __device__ bool lean_tile(const FillArgs& a, u64 k, const E& e, LeanSmem<NT, C>&
       }
       sm.msk[kMW - 1][t] = 0;
     } else {
-      {  // first mask word: positions before the sync point belong to the previous chain
+      // positions [s, C): bit-parallel chain over 16-word half-blocks kept in
+      // shared memory (positions before the sync point belong to the previous chain)
+      u64* wb = sm.sbuf + LeanSmem<NT, C>::kQueueW;
+      for (int b = 0; b < C / 32; ++b) {
         unsigned mw = 0;
-#pragma unroll 4
-        for (int j = 0; j < 32; ++j) {
-          const u64 u = g.next();
-          if (j >= s) lean_step<NT, S>(u, j, 0, mw, c, tb, z, sm.msk, sm.sbuf, sm.tails, nts, a.ctrl, k);
+        for (int h = 0; h < 2; ++h) {
+          const int P0 = b * 32 + h * 16;
+          unsigned F = 0, I = 0, T = 0;
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const u64 u = g.next();
+            wb[j * NT + t] = u;
+            const unsigned rh = (unsigned)(u >> 29), kh = tb.khi[u & 0xff];
+            F |= (unsigned)(rh < kh) << j;
+            T |= (unsigned)(rh == kh) << j;
+            I |= (unsigned)((u & 0xff) == 0) << j;
+          }
+          const int from = max(0, min(16, s - P0));
+          if (from < 16)
+            lean_half<NT, S>(P0, from, F, I, T, wb, mw, c, tb, z, sm.msk, sm.sbuf, sm.tails, nts, a.ctrl, k);
         }
-        sm.msk[0][t] = mw;
-      }
-      for (int b = 1; b < C / 32; ++b) {
-        unsigned mw = 0;
-#pragma unroll 4
-        for (int j = 0; j < 32; ++j)
-          lean_step<NT, S>(g.next(), b * 32 + j, b, mw, c, tb, z, sm.msk, sm.sbuf, sm.tails, nts, a.ctrl, k);
         sm.msk[b][t] = mw;
       }
       // the next chunk's sync point by the same rule, while the chain runs on
@@ -430,7 +585,7 @@ __device__ bool lean_tile(const FillArgs& a, u64 k, const E& e, LeanSmem<NT, C>&
 }
 
 template <int NT, int C, class E, class S>
-__global__ void __launch_bounds__(NT, 6) k_lean(FillArgs a) {
+__global__ void __launch_bounds__(NT, 5) k_lean(FillArgs a) {
   __shared__ LeanSmem<NT, C> sm;
   __shared__ LeanTab tb;
   lean_load_tab<S>(tb, NT);
@@ -449,7 +604,7 @@ __global__ void __launch_bounds__(NT, 6) k_lean(FillArgs a) {
 // tile) items until the list is exhausted; tables for both ziggurats stay in
 // shared memory.
 template <int NT, int C, class E>
-__global__ void __launch_bounds__(NT, 6) k_lean_batch(BatchArgs b) {
+__global__ void __launch_bounds__(NT, 5) k_lean_batch(BatchArgs b) {
   __shared__ LeanSmem<NT, C> sm;
   __shared__ LeanTab tb[2];
   __shared__ FillArgs fa;
