@@ -179,13 +179,18 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int* warp_sums, int* 
 }
 
 // Decoupled look-back over tile counts, run by one warp.  Status word:
-// bit 63 aggregate, bit 62 inclusive, low 62 bits value.  Lane l inspects
-// predecessor j - l; the window is consumed up to the nearest inclusive value
-// once every entry before it is at least an aggregate.  Returns the tile's
-// exclusive prefix in all lanes, or ~0 if the bounded wait ran out or the
-// tile became unnecessary.
+// bit 63 aggregate, bit 62 inclusive, low 62 bits value.  Each round the warp
+// inspects the next 32 x kW predecessors, nearest first (lane l, window w:
+// tile j - l - 32 w), and consumes them up to the nearest inclusive value once
+// every entry before it is at least an aggregate.  `kp` is the CTA's own
+// previous tile (-1: none), whose inclusive prefix `incp` the CTA already
+// knows: the walk never goes past it, so a look-back spans at most one grid
+// of predecessors even when a whole round of tiles finishes together.
+// Returns the tile's exclusive prefix in all lanes, or ~0 if the bounded wait
+// ran out or the tile became unnecessary.
 __device__ unsigned long long lookback_warp(unsigned long long* st, unsigned long long k, unsigned long long cnt,
-                                           Ctrl* ctrl) {
+                                           Ctrl* ctrl, long long kp = -1, unsigned long long incp = 0) {
+  constexpr int kW = 1;
   const unsigned long long AGG = 1ull << 63, INC = 1ull << 62, VAL = INC - 1;
   const int lane = threadIdx.x & 31;
   if (k == 0) {
@@ -197,13 +202,28 @@ __device__ unsigned long long lookback_warp(unsigned long long* st, unsigned lon
   long long j = (long long)k - 1;
   unsigned long long spins = 0;
   for (;;) {
-    long long idx = j - lane;
-    unsigned long long v = idx >= 0 ? ld_volatile(st + idx) : INC;
-    unsigned inc_mask = __ballot_sync(0xffffffffu, (v & INC) != 0);
-    unsigned rdy_mask = __ballot_sync(0xffffffffu, (v & (INC | AGG)) != 0);
-    int first = inc_mask ? __ffs(inc_mask) - 1 : 31;
-    unsigned need = first == 31 ? 0xffffffffu : ((2u << first) - 1u);
-    if ((rdy_mask & need) != need) {
+    unsigned long long v[kW];
+    unsigned incm[kW], rdym[kW];
+#pragma unroll
+    for (int w = 0; w < kW; ++w) {
+      const long long idx = j - lane - 32 * w;
+      // at or below the CTA's previous tile: its known inclusive value (or
+      // zero before the first tile), never a load
+      v[w] = idx > kp ? ld_volatile(st + idx) : (INC | (idx == kp ? incp : 0ull));
+      incm[w] = __ballot_sync(0xffffffffu, (v[w] & INC) != 0);
+      rdym[w] = __ballot_sync(0xffffffffu, (v[w] & (INC | AGG)) != 0);
+    }
+    int wi = kW, fi = 31;   // window and lane of the nearest inclusive value
+#pragma unroll
+    for (int w = kW - 1; w >= 0; --w)
+      if (incm[w]) { wi = w; fi = __ffs(incm[w]) - 1; }
+    bool ready = true;
+#pragma unroll
+    for (int w = 0; w < kW; ++w) {
+      const unsigned need = w < wi ? 0xffffffffu : (w == wi ? (2u << fi) - 1u : 0u);
+      ready = ready && (rdym[w] & need) == need;
+    }
+    if (!ready) {
       int stop = 0;
       if (lane == 0) {
         if (ld_volatile(&ctrl->done_tile) < k) stop = 1;
@@ -213,16 +233,26 @@ __device__ unsigned long long lookback_warp(unsigned long long* st, unsigned lon
       __nanosleep(64);
       continue;
     }
-    unsigned long long c = lane <= first ? (v & VAL) : 0ull;
+    unsigned long long c = 0;
+#pragma unroll
+    for (int w = 0; w < kW; ++w)
+      if (w < wi || (w == wi && lane <= fi)) c += v[w] & VAL;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
     excl += c;
-    if (inc_mask) break;
-    j -= 32;
+    if (wi < kW) break;
+    j -= 32 * kW;
   }
   if (lane == 0) *(volatile unsigned long long*)(st + k) = INC | (excl + cnt);
   return excl;
 }
+
+// The CTA's previous tile and its inclusive prefix, kept by the look-back
+// warp across the tiles of a persistent CTA (k = -1: none yet).
+struct LookbackFloor {
+  long long k = -1;
+  unsigned long long inc = 0;
+};
 
 // ------------------------------------------------------------------ staging
 // Lane rows of kStage outputs, flushed by the warp two rows per instruction so
@@ -261,6 +291,7 @@ __device__ __forceinline__ bool batch_claim(const BatchArgs& b, FillArgs& fa, Ba
 }
 
 #include "rp_lean.cuh"
+#include "rp_rej.cuh"
 
 // ------------------------------------------------------------------ kernels
 // One tile of a one-word-per-variate fill: chunk words stream straight to
@@ -547,6 +578,7 @@ constexpr int NT_ = 128;
 constexpr int C_ = 256;
 constexpr int CM_ = 2048;   // chunk words of the merge-seam samplers
 constexpr int NTM_ = 32;    // threads per CTA of the merge-seam samplers
+constexpr int CR_ = 256;    // chunk words of the one-pass bounded fill with rejections
 
 template <class E, class S>
 int launch_merge(const FillArgs& a, int grid, cudaStream_t s, int* occ) {
@@ -565,6 +597,16 @@ int launch_es(const FillArgs& a, int grid, cudaStream_t s, int* occ) {
     return 0;
   }
   k_onepw<NT_, C_, E, S><<<grid, NT_, 0, s>>>(a);
+  return (int)cudaGetLastError();
+}
+
+template <class E>
+int launch_rej(const FillArgs& a, int grid, cudaStream_t s, int* occ) {
+  if (occ) {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k_rej<NT_, CR_, E>, NT_, 0);
+    return 0;
+  }
+  k_rej<NT_, CR_, E><<<grid, NT_, 0, s>>>(a);
   return (int)cudaGetLastError();
 }
 
@@ -605,7 +647,7 @@ int dispatch_dist(const FillArgs& a, int grid, cudaStream_t s, int* occ) {
   switch (a.dist) {
     case D_U64: return launch_es<E, SampU64>(a, grid, s, occ);
     case D_UNIFORM: return launch_es<E, SampUniform>(a, grid, s, occ);
-    case D_BOUNDED: return launch_lean<E, LeanBounded>(a, grid, s, occ);
+    case D_BOUNDED: return launch_rej<E>(a, grid, s, occ);
     case D_BOUNDED_ONE: return launch_es<E, SampBoundedOne>(a, grid, s, occ);
     case D_NORMAL: return launch_lean<E, LeanNormal>(a, grid, s, occ);
     case D_EXP: return launch_lean<E, LeanExp>(a, grid, s, occ);

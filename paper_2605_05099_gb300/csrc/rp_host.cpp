@@ -413,8 +413,20 @@ struct Scratch {
   rp::Ctrl* h_ctrl = nullptr;  // pinned
   rp::TailEntry* tailq = nullptr;
   size_t tail_cap = 0;
+  unsigned long long* park = nullptr;  // one-pass bounded fill: each CTA's parked runs
+  size_t park_cap = 0;
 };
 Scratch g_scr;
+
+int ensure_park(size_t words) {
+  if (words > g_scr.park_cap) {
+    if (g_scr.park) cudaFree(g_scr.park);
+    int e = (int)cudaMalloc((void**)&g_scr.park, words * 8);
+    if (e) { g_scr.park = nullptr; g_scr.park_cap = 0; return e; }
+    g_scr.park_cap = words;
+  }
+  return 0;
+}
 
 int ensure_tailq(size_t cap) {
   if (cap > g_scr.tail_cap) {
@@ -567,12 +579,14 @@ rp_status run_fill_state_locked(int engine, const u64 s_in[4], u64* pos, size_t 
       e = ensure_scratch(tiles);
       const bool queued = dist == rp::D_NORMAL || dist == rp::D_EXP || dist == rp::D_GAMMA || dist == rp::D_BETA;
       if (!e && queued) e = ensure_tailq(left / 256 + 4096);
+      if (!e && dist == rp::D_BOUNDED) e = ensure_park((size_t)(grid * T));
       if (e) return fail(RP_ERR_NOMEM, std::string("scratch allocation: ") + cudaGetErrorString((cudaError_t)e));
       a.tile_status = g_scr.status;
       a.ctrl = g_scr.ctrl;
       a.tailq = g_scr.tailq;
       a.tail_cap = queued ? g_scr.tail_cap : 0;
       a.tail_count = &g_scr.ctrl->n_tail;
+      a.park = g_scr.park;
       rp::Ctrl c0;
       memset(&c0, 0, sizeof(c0));
       c0.done_tile = ~0ull;

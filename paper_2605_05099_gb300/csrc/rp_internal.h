@@ -86,6 +86,7 @@ struct FillArgs {
   unsigned long long* tail_count;   // entries claimed in tailq (&ctrl->n_tail for one fill)
   int tail_abs;                     // 1: TailEntry.g is the output's address (batches), 0: its index
   int req;                          // request index within a batch
+  unsigned long long* park;         // one-pass bounded fill: grid x tile words of parked values
 };
 
 // Batched fills: one work item is one tile of one request.  Items of a

@@ -126,6 +126,7 @@ int occupancy_blocks(int engine, int dist) {
 TileGeom tile_geom(int engine, int dist) {
   (void)engine;
   if (dist == D_GAMMA || dist == D_BETA) return TileGeom{NTM_, CM_, NTM_ * CM_, 0};
+  if (dist == D_BOUNDED) return TileGeom{NT_, CR_, NT_ * CR_, 0};
   return TileGeom{NT_, C_, NT_ * C_, 0};
 }
 
