@@ -213,8 +213,10 @@ __device__ __forceinline__ void flush_rows16(OT* __restrict__ outb, const OT* ro
 
 // ------------------------------------------------------------------ bit-parallel chain
 // Pass 1 over 16-word half-blocks.  The words sit in shared memory (wb[j NT
-// + t]) with three 16-bit masks: F (fast accept), I (strip 0) and T (top bits
-// tied with the bound).  With every candidate one or two words long, the
+// + t]) with one 16-bit mask F: the 32-bit fast test (top significand bits
+// below the bound's), exact except where the top bits tie, which the
+// half-block step checks at the candidate starts that failed it.  With every
+// candidate one or two words long (a tie counted as not fast), the
 // positions consumed as second words follow from the non-fast mask N alone:
 // position q is consumed when q - 1 is a candidate start that is not fast,
 // K(q + 1) = N(q) and not K(q).  Inside each maximal run of N bits starting at
@@ -265,19 +267,17 @@ __device__ __forceinline__ void lean_exp_tail(u64 u0, u64 w1, int pos, int b, un
 
 // One half-block at absolute positions P0 .. P0 + 15, from relative position
 // `from` on (earlier positions belong to the previous chain).  The chain
-// state c carries a candidate that straddles half-blocks.
+// state c carries a candidate that straddles half-blocks.  F holds the
+// 32-bit fast test of every word; everything else is looked up only at the
+// candidate starts that failed it (about one word in 85): a tie of the top
+// bits (the full compare decides; if it says fast, the chain is recomputed
+// from that position), strip 0 (a tail) or a wedge.
 template <int NT, class S>
-__device__ __forceinline__ void lean_half(int P0, int from, unsigned F, unsigned I, unsigned T, const u64* wb,
-                                          unsigned& mw, LeanChain& c, const LeanTab& tb, const ZigDev& z,
-                                          unsigned (*msk)[NT], u64* queue, u64 (*tails)[3], int* ntails,
-                                          Ctrl* ctrl, u64 k) {
+__device__ __forceinline__ void lean_half(int P0, int from, unsigned F, const u64* wb, unsigned& mw, LeanChain& c,
+                                          const LeanTab& tb, const ZigDev& z, unsigned (*msk)[NT], u64* queue,
+                                          u64 (*tails)[3], int* ntails, Ctrl* ctrl, u64 k) {
   const int t = threadIdx.x;
   const int b = P0 >> 5, sh = P0 & 31;
-  while (T) {   // equal top bits: the full 52/53-bit compare decides
-    const int j = __ffs(T) - 1;
-    T &= T - 1;
-    if (S::fast_exact(wb[j * NT + t], z)) F |= 1u << j;
-  }
   unsigned ein = 0;   // position `from` is the second word of a candidate
   if (from == 0 && c.st != 0) {
     if (c.st == 1) {          // wedge started on the previous half-block's last word
@@ -306,36 +306,43 @@ __device__ __forceinline__ void lean_half(int P0, int from, unsigned F, unsigned
     const unsigned Or = R & ~(R + (RS & 0xAAAAAAAAu));
     const unsigned K = ((Er << 1) & 0xAAAAAAAAu) | ((Or << 1) & 0x55555555u) | (ein << from);
     const unsigned Sc = ~K & range;   // candidate starts
-    const unsigned NS = Sc & N;       // starts that are not fast accepts
-    unsigned lim = range;
-    int t0 = 16;
-    if constexpr (S::kTailPairs) {
-      const unsigned TT = NS & I;
-      if (TT) {
-        t0 = __ffs(TT) - 1;
-        lim &= (1u << t0) - 1u;
+    // not-fast starts in order; `stop` ends this pass early (a tie that is
+    // fast after all, or a normal tail)
+    unsigned W = Sc & N;
+    int stop = 16;
+    bool tie = false;
+    while (W) {
+      const int j = __ffs(W) - 1;
+      W &= W - 1;
+      const u64 u0 = wb[j * NT + t];
+      if ((unsigned)(u0 >> 29) == tb.khi[u0 & 0xff] && S::fast_exact(u0, z)) {
+        stop = j;
+        tie = true;
+        break;
       }
-    }
-    mw |= (Sc & F & lim) << sh;
-    unsigned Wd = NS & lim;
-    if constexpr (!S::kTailPairs) {
-      unsigned X = Wd & I;   // exponential tails: two words, always accepted
-      Wd &= ~I;
-      while (X) {
-        const int j = __ffs(X) - 1;
-        X &= X - 1;
-        if (j == 15) { c.st = 4; c.pu0 = wb[15 * NT + t]; c.pp = P0 + 15; }
-        else lean_exp_tail<NT>(wb[j * NT + t], wb[(j + 1) * NT + t], P0 + j, b, mw, msk, tails, ntails, ctrl, k);
+      if ((u0 & 0xff) == 0) {
+        if constexpr (S::kTailPairs) {   // normal tail: walked below
+          stop = j;
+          break;
+        } else {                          // exponential tail: two words, always accepted
+          if (j == 15) { c.st = 4; c.pu0 = u0; c.pp = P0 + 15; }
+          else lean_exp_tail<NT>(u0, wb[(j + 1) * NT + t], P0 + j, b, mw, msk, tails, ntails, ctrl, k);
+          continue;
+        }
       }
+      if (j == 15) { c.st = 1; c.pu0 = u0; c.pp = P0 + 15; }
+      else lean_push_wedge<NT, S>(u0, wb[(j + 1) * NT + t], P0 + j, b, mw, c, z, msk, queue);
     }
-    while (Wd) {
-      const int j = __ffs(Wd) - 1;
-      Wd &= Wd - 1;
-      if (j == 15) { c.st = 1; c.pu0 = wb[15 * NT + t]; c.pp = P0 + 15; }
-      else lean_push_wedge<NT, S>(wb[j * NT + t], wb[(j + 1) * NT + t], P0 + j, b, mw, c, z, msk, queue);
+    mw |= (Sc & F & range & ((2u << stop) - 1u) >> 1) << sh;   // fast starts before `stop`
+    if (stop == 16) break;
+    if (tie) {   // fast after all: the chain from `stop` on changes
+      F |= 1u << stop;
+      from = stop;
+      ein = 0;
+      continue;
     }
-    if (t0 == 16) break;
-    // a normal tail at t0: pairs (t0 + 1, t0 + 2), ... until one is accepted
+    // a normal tail at t0 = stop: pairs (t0 + 1, t0 + 2), ... until one is accepted
+    const int t0 = stop;
     int q = t0 + 1;
     bool acc = false;
     for (; q + 1 < 16; q += 2) {
@@ -439,19 +446,15 @@ __device__ bool lean_tile(const FillArgs& a, u64 k, const E& e, LeanSmem<NT, C>&
         unsigned mw = 0;
         for (int h = 0; h < 2; ++h) {
           const int P0 = b * 32 + h * 16;
-          unsigned F = 0, I = 0, T = 0;
+          unsigned F = 0;
 #pragma unroll
           for (int j = 0; j < 16; ++j) {
             const u64 u = g.next();
             wb[j * NT + t] = u;
-            const unsigned rh = (unsigned)(u >> 29), kh = tb.khi[u & 0xff];
-            F |= (unsigned)(rh < kh) << j;
-            T |= (unsigned)(rh == kh) << j;
-            I |= (unsigned)((u & 0xff) == 0) << j;
+            F |= (unsigned)((unsigned)(u >> 29) < tb.khi[u & 0xff]) << j;
           }
           const int from = max(0, min(16, s - P0));
-          if (from < 16)
-            lean_half<NT, S>(P0, from, F, I, T, wb, mw, c, tb, z, sm.msk, sm.sbuf, sm.tails, nts, a.ctrl, k);
+          if (from < 16) lean_half<NT, S>(P0, from, F, wb, mw, c, tb, z, sm.msk, sm.sbuf, sm.tails, nts, a.ctrl, k);
         }
         sm.msk[b][t] = mw;
       }

@@ -9,7 +9,9 @@ import numpy as np
 import pytest
 import torch
 
-from gpu_util import assert_parity, first_mismatch, gpu_fill, oracle_fill, same_bits
+import oracle
+import paper_2605_05099_gb300 as rp
+from gpu_util import assert_parity, first_mismatch, gpu_fill, oracle_fill, same_bits, ulp_diff
 
 pytestmark = pytest.mark.gpu
 
@@ -129,3 +131,80 @@ def test_bounded_rare_rejection_one_pass_and_fallback(engine):
         assert np.array_equal(g, o), (engine, seed)
         if seed in REJECT_SEEDS[engine]:
             assert opos == n + 1
+
+
+# ------------------------------------------------------------------ ties of the top significand bits
+M64 = 2 ** 64 - 1
+
+
+def _xo_state_with_word(u, j, rng):
+    """xoshiro256++ state words (before word 0) of a stream whose word j is
+    u: the state before word j satisfies rotl(s0 + s3, 23) + s0 = u, and it
+    is moved back j words by a forward jump of (2^256 - 1) - j, the period."""
+    s0, s1, s2 = (int(x) for x in rng.integers(0, 2 ** 64, size=3, dtype=np.uint64))
+    v = (u - s0) & M64
+    s3 = (((v >> 23) | (v << 41)) - s0) & M64
+    return oracle.xoshiro_jump([s0, s1, s2, s3], 2 ** 256 - 1 - j)
+
+
+def _oracle_gen(words):
+    g = oracle.Gen()
+    g.engine = oracle.ENGINES["xoshiro256pp"]
+    for i, w in enumerate(words):
+        g.s[i] = w
+    return g
+
+
+def _tie_word(dist, i, fast, rng):
+    """A word of strip i whose top 32 significand bits equal those of the
+    bound k_i, with r below k_i (a fast accept after the full compare) or
+    equal to it (not fast)."""
+    which, sh, rb = (0, 9, 52) if dist == "normal" else (1, 8, 53)
+    ki = int(oracle.zig_table(which)[0][i])
+    low = rb - 32
+    r = ((ki >> low) << low) | (0 if fast else ki & ((1 << low) - 1))
+    top = int(rng.integers(0, 2 ** (64 - sh - rb)))
+    sign = int(rng.integers(0, 2)) if dist == "normal" else 0
+    return (top << (sh + rb)) | (r << sh) | (sign << 8) | i
+
+
+@pytest.mark.parametrize("dist", ["normal", "exp"])
+def test_top_bit_ties(dist):
+    """Candidates whose top 32 significand bits tie with the bound's occur
+    once in 2^32 words, so streams are built around them: the full compare
+    decides, in both outcomes, for strip 0 and inner strips, at the start,
+    inside and at both ends of a 16-word half-block."""
+    which, low = (0, 20) if dist == "normal" else (1, 21)
+    k = oracle.zig_table(which)[0]
+    rng = np.random.default_rng(31)
+    n = 64
+    checked = 0
+    for i in (0, 1, 77, 255):
+        for fast in (True, False):
+            if fast and int(k[i]) & ((1 << low) - 1) == 0:
+                continue   # no word ties and is still below k_i
+            for j in (0, 6, 15, 16, 33):
+                u = _tie_word(dist, i, fast, rng)
+                for _ in range(20):
+                    words = _xo_state_with_word(u, j, rng)
+                    g = _oracle_gen(words)
+                    o, start = oracle.fill(g, dist, n, with_start=True)
+                    opos = int(g.pos)
+                    # the tie must sit at a candidate start; fast ones are outputs there
+                    if not fast or j in set(int(x) for x in start):
+                        break
+                w = oracle.next_words(_oracle_gen(words), opos)
+                assert int(w[j]) == u
+                out = torch.empty(n, dtype=torch.float64, device="cuda")
+                gpos = rp.rp_fill_state("xoshiro256pp", words, 0, dist, out)
+                torch.cuda.synchronize()
+                g_host = out.cpu().numpy()
+                assert gpos == opos, (dist, i, fast, j, gpos, opos)
+                bad = np.nonzero(g_host.view(np.uint64) != o.view(np.uint64))[0]
+                for b in bad:   # only tail outputs may differ, by at most 2 ulp
+                    s = int(w[int(start[b])])
+                    r = (s >> 9) & (2 ** 52 - 1) if dist == "normal" else (s >> 8) & (2 ** 53 - 1)
+                    assert (s & 0xFF) == 0 and r >= int(k[0]), (dist, i, fast, j, int(b))
+                    assert ulp_diff(g_host[b], o[b]) <= 2
+                checked += 1
+    assert checked >= 30
