@@ -255,18 +255,40 @@ struct LookbackFloor {
 };
 
 // ------------------------------------------------------------------ staging
-// Lane rows of kStage outputs, flushed by the warp two rows per instruction so
-// that each row (a run of consecutive outputs) is written by 16 lanes.
-template <class OT>
-__device__ __forceinline__ void flush_rows(OT* __restrict__ out, const OT* row_base, u64 dst, int cnt, u64 n) {
+// Lane rows of kStage outputs, flushed by the warp so that each row (a run of
+// consecutive outputs) is written by whole groups of lanes.  In the one-word
+// fills every word is an output, so row r's place is fixed, dst0 + r stride,
+// and needs no shuffle.  Rows are kRowW words apart: 16-byte aligned, and
+// 16-byte accesses by eight lanes of a row or of eight rows hit distinct banks.
+constexpr int kRowW = kStage + 2;
+
+__device__ __forceinline__ u64 as_bits(u64 v) { return v; }
+__device__ __forceinline__ u64 as_bits(double v) { return (u64)__double_as_longlong(v); }
+
+// 8-byte stores, two rows per instruction (any output alignment).
+__device__ __forceinline__ void flush_rows(u64* __restrict__ out, const u64* rows, u64 dst0, int stride, u64 n) {
   const int lane = threadIdx.x & 31;
   const int half = lane >> 4, col = lane & 15;
 #pragma unroll 4
   for (int r = 0; r < 32; r += 2) {
-    int rr = r + half;
-    u64 d = __shfl_sync(0xffffffffu, dst, rr);
-    int c = __shfl_sync(0xffffffffu, cnt, rr);
-    if (col < c && d + col < n) out[d + col] = row_base[rr * kRow + col];
+    const int rr = r + half;
+    const u64 d = dst0 + (u64)(rr * stride + col);
+    if (d < n) out[d] = rows[rr * kRowW + col];
+  }
+}
+
+// 16-byte stores, four rows per instruction (output 16-byte aligned; dst0
+// and stride even).
+__device__ __forceinline__ void flush_rows_wide(u64* __restrict__ out, const u64* rows, u64 dst0, int stride, u64 n) {
+  const int lane = threadIdx.x & 31;
+  const int q = lane >> 3, c2 = (lane & 7) * 2;
+#pragma unroll 4
+  for (int r = 0; r < 32; r += 4) {
+    const int rr = r + q;
+    const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(rows + rr * kRowW + c2);
+    const u64 d = dst0 + (u64)(rr * stride + c2);
+    if (d + 1 < n) *reinterpret_cast<ulonglong2*>(out + d) = v;
+    else if (d < n) out[d] = v.x;
   }
 }
 
@@ -297,32 +319,36 @@ __device__ __forceinline__ bool batch_claim(const BatchArgs& b, FillArgs& fa, Ba
 // One tile of a one-word-per-variate fill: chunk words stream straight to
 // the output through the warp's staging rows.
 template <int NT, int C, class E, class S>
-__device__ __forceinline__ void onepw_tile(const FillArgs& a, u64 k, const E& e, typename S::out_t* stage_w) {
-  typedef typename S::out_t OT;
+__device__ __forceinline__ void onepw_tile(const FillArgs& a, u64 k, const E& e, u64* stage_w) {
+  static_assert(kStage % 2 == 0 && C % 2 == 0, "rows are written in pairs of words");
   constexpr int T = NT * C;
   const int t = threadIdx.x, lane = t & 31;
-  OT* out = (OT*)a.out;
+  u64* out = (u64*)a.out;
+  const bool wide = ((unsigned long long)a.out & 15) == 0;
   E g = e;
   const u64 base = k * (u64)T + (u64)t * C;
+  const u64 wbase = k * (u64)T + (u64)(t - lane) * C;   // lane 0's chunk: row r goes to wbase + r C
+  u64* row = stage_w + lane * kRowW;
   for (int j0 = 0; j0 < C; j0 += kStage) {
 #pragma unroll
-    for (int j = 0; j < kStage; ++j) {
-      const u64 u = g.next();
-      stage_w[lane * kRow + j] = S::value1(u, a.sp);
+    for (int j = 0; j < kStage; j += 2) {
+      const u64 u0 = g.next(), u1 = g.next();
+      *reinterpret_cast<ulonglong2*>(row + j) = make_ulonglong2(as_bits(S::value1(u0, a.sp)), as_bits(S::value1(u1, a.sp)));
       if constexpr (S::kCheckReject) {
-        if (u * a.sp.m < a.sp.thresh && base + j0 + j < a.n) atomicMin(&a.ctrl->first_reject, base + j0 + j);
+        if (u0 * a.sp.m < a.sp.thresh && base + j0 + j < a.n) atomicMin(&a.ctrl->first_reject, base + j0 + j);
+        if (u1 * a.sp.m < a.sp.thresh && base + j0 + j + 1 < a.n) atomicMin(&a.ctrl->first_reject, base + j0 + j + 1);
       }
     }
     __syncwarp();
-    flush_rows<OT>(out, stage_w, base + j0, kStage, a.n);
+    if (wide) flush_rows_wide(out, stage_w, wbase + j0, C, a.n);
+    else flush_rows(out, stage_w, wbase + j0, C, a.n);
     __syncwarp();
   }
 }
 
 template <int NT, int C, class E, class S>
 __global__ void __launch_bounds__(NT) k_onepw(FillArgs a) {
-  typedef typename S::out_t OT;
-  __shared__ __align__(16) OT stage[NT / 32][32 * kRow];
+  __shared__ __align__(16) u64 stage[NT / 32][32 * kRowW];
   __shared__ u64 sh4[4];
   const int t = threadIdx.x, wid = t >> 5;
   E e;
@@ -519,7 +545,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_merge(FillArgs a) {
 
 template <int NT, int C, class E>
 __global__ void __launch_bounds__(NT) k_onepw_batch(BatchArgs b) {
-  __shared__ __align__(16) u64 stage[NT / 32][32 * kRow];
+  __shared__ __align__(16) u64 stage[NT / 32][32 * kRowW];
   __shared__ u64 sh4[4];
   __shared__ FillArgs fa;
   __shared__ unsigned long long slot;
@@ -529,7 +555,7 @@ __global__ void __launch_bounds__(NT) k_onepw_batch(BatchArgs b) {
     E e;
     e.init_tile(fa.eng, bi.tile, threadIdx.x, sh4);
     if (fa.dist == D_U64) onepw_tile<NT, C, E, SampU64>(fa, bi.tile, e, stage[wid]);
-    else onepw_tile<NT, C, E, SampUniform>(fa, bi.tile, e, (double*)stage[wid]);
+    else onepw_tile<NT, C, E, SampUniform>(fa, bi.tile, e, stage[wid]);
   }
 }
 

@@ -208,3 +208,28 @@ def test_top_bit_ties(dist):
                     assert ulp_diff(g_host[b], o[b]) <= 2
                 checked += 1
     assert checked >= 30
+
+
+@pytest.mark.parametrize("engine", ENGINES)
+def test_output_offsets(engine):
+    """One-word fills store 16 bytes at a time when the output is 16-byte
+    aligned and 8 bytes otherwise; an output starting 8 bytes past a 16-byte
+    boundary takes the second path.  Both agree with the oracle."""
+    n = 3 * 8192 + 17
+    for dist, params in [("u64", ()), ("uniform", ()), ("bounded", (6,))]:
+        o, opos = oracle_fill(dist, engine, 5, None, 3, n, params)
+        for off in (0, 1):
+            dt = torch.float64 if dist == "uniform" else torch.uint64
+            buf = torch.zeros(n + 2, dtype=dt, device="cuda")
+            out = buf[off:off + n]
+            if dist == "u64":
+                p = rp.rp_fill_u64(engine, 5, rp.NO_STREAM, 3, out)
+            elif dist == "uniform":
+                p = rp.rp_fill_uniform(engine, 5, rp.NO_STREAM, 3, out)
+            else:
+                p = rp.rp_fill_bounded(engine, 5, rp.NO_STREAM, 3, params[0], out)
+            torch.cuda.synchronize()
+            host = buf.view(torch.int64).cpu().numpy().view(np.uint64)
+            assert p == opos
+            assert np.array_equal(host[off:off + n], o.view(np.uint64)), (dist, engine, off)
+            assert host[off + n] == 0 and (off == 0 or host[0] == 0)   # nothing written outside
