@@ -287,6 +287,11 @@ struct XoshiroDev {
     s2 ^= s0; s3 ^= s1; s1 ^= s2; s0 ^= s3; s2 ^= t; s3 = rotl64(s3, 45);
     return r;
   }
+  // Unrolled loops take kStep words per step (one: the chain through the
+  // state is the critical path either way); kLeanCtas resident CTAs per SM
+  // for the bitmap kernel.
+  static constexpr int kStep = 1, kLeanCtas = 4;
+  __device__ __forceinline__ void next_step(u64 (&u)[2]) { u[0] = next(); }
   __device__ void init(const EngineArgs& a, u64 off) {
     s0 = a.s[0]; s1 = a.s[1]; s2 = a.s[2]; s3 = a.s[3];
     const ulonglong4_32a* tab = (const ulonglong4_32a*)a.gf2_pow;
@@ -348,6 +353,8 @@ struct PcgDev {
     st = st * (u128)0xda942042e4dd58b5ull + inc;
     return hi;
   }
+  static constexpr int kStep = 1, kLeanCtas = 5;
+  __device__ __forceinline__ void next_step(u64 (&u)[2]) { u[0] = next(); }
   __device__ void init(const EngineArgs& a, u64 off) {
     st = ((u128)a.s[0] << 64) | a.s[1];
     inc = ((u128)a.s[2] << 64) | a.s[3];
@@ -402,6 +409,20 @@ struct PhiloxDev {
     }
     ++idx;
     return r;
+  }
+  // Unrolled loops take two consecutive words per step, one block and no
+  // branch: the parity of idx is the same for every thread of a fill but
+  // unknown at compile time.  Odd phase: the pending word and the low half
+  // of the next block, whose high half becomes pending.
+  static constexpr int kStep = 2, kLeanCtas = 5;
+  __device__ __forceinline__ void next_step(u64 (&u)[2]) {
+    const bool odd = (idx & 1) != 0;
+    u64 w0, w1;
+    block((idx + 1) >> 1, w0, w1);
+    u[0] = odd ? buf : w0;
+    u[1] = odd ? w0 : w1;
+    buf = w1;
+    idx += 2;
   }
   __device__ void init(const EngineArgs& a, u64 off) {
     c_lo = a.s[0]; c_hi = a.s[1];

@@ -332,7 +332,10 @@ __device__ __forceinline__ void onepw_tile(const FillArgs& a, u64 k, const E& e,
   for (int j0 = 0; j0 < C; j0 += kStage) {
 #pragma unroll
     for (int j = 0; j < kStage; j += 2) {
-      const u64 u0 = g.next(), u1 = g.next();
+      u64 u[2];
+      g.next_step(u);
+      if constexpr (E::kStep == 1) u[1] = g.next();
+      const u64 u0 = u[0], u1 = u[1];
       *reinterpret_cast<ulonglong2*>(row + j) = make_ulonglong2(as_bits(S::value1(u0, a.sp)), as_bits(S::value1(u1, a.sp)));
       if constexpr (S::kCheckReject) {
         if (u0 * a.sp.m < a.sp.thresh && base + j0 + j < a.n) atomicMin(&a.ctrl->first_reject, base + j0 + j);

@@ -431,9 +431,11 @@ __device__ bool lean_tile(const FillArgs& a, u64 k, const E& e, LeanSmem<NT, C>&
       for (int b = 0; b < C / 32; ++b) {
         unsigned mw = 0;
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const u64 u = g.next();
-          mw |= (unsigned)(u * a.sp.m >= a.sp.thresh) << j;
+        for (int j = 0; j < 32; j += E::kStep) {
+          u64 u[2];
+          g.next_step(u);
+#pragma unroll
+          for (int i = 0; i < E::kStep; ++i) mw |= (unsigned)(u[i] * a.sp.m >= a.sp.thresh) << (j + i);
         }
         sm.msk[b][t] = mw;
       }
@@ -448,10 +450,14 @@ __device__ bool lean_tile(const FillArgs& a, u64 k, const E& e, LeanSmem<NT, C>&
           const int P0 = b * 32 + h * 16;
           unsigned F = 0;
 #pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const u64 u = g.next();
-            wb[j * NT + t] = u;
-            F |= (unsigned)((unsigned)(u >> 29) < tb.khi[u & 0xff]) << j;
+          for (int j = 0; j < 16; j += E::kStep) {
+            u64 u[2];
+            g.next_step(u);
+#pragma unroll
+            for (int i = 0; i < E::kStep; ++i) {
+              wb[(j + i) * NT + t] = u[i];
+              F |= (unsigned)((unsigned)(u[i] >> 29) < tb.khi[u[i] & 0xff]) << (j + i);
+            }
           }
           const int from = max(0, min(16, s - P0));
           if (from < 16) lean_half<NT, S>(P0, from, F, wb, mw, c, tb, z, sm.msk, sm.sbuf, sm.tails, nts, a.ctrl, k);
@@ -567,13 +573,17 @@ __device__ bool lean_tile(const FillArgs& a, u64 k, const E& e, LeanSmem<NT, C>&
         int ns = 0;
         if ((hb >> 1) < nblk) {
           const unsigned m = sm.msk[hb >> 1][t] >> ((hb & 1) * 16);
-#pragma unroll 8
-          for (int j = 0; j < 16; ++j) {
-            const u64 u = g2.next();
+#pragma unroll 8 / E::kStep
+          for (int j = 0; j < 16; j += E::kStep) {
+            u64 u[2];
+            g2.next_step(u);
             // branch-free: every word's value lands in the next free slot
             // (ns <= j <= 15 < kRow), which advances only for marked words
-            row[ns] = S::value(u, tb, a.sp);
-            ns += (int)((m >> j) & 1u);
+#pragma unroll
+            for (int i = 0; i < E::kStep; ++i) {
+              row[ns] = S::value(u[i], tb, a.sp);
+              ns += (int)((m >> (j + i)) & 1u);
+            }
           }
         }
         __syncwarp();
@@ -588,7 +598,7 @@ __device__ bool lean_tile(const FillArgs& a, u64 k, const E& e, LeanSmem<NT, C>&
 }
 
 template <int NT, int C, class E, class S>
-__global__ void __launch_bounds__(NT, 5) k_lean(FillArgs a) {
+__global__ void __launch_bounds__(NT, E::kLeanCtas) k_lean(FillArgs a) {
   __shared__ LeanSmem<NT, C> sm;
   __shared__ LeanTab tb;
   lean_load_tab<S>(tb, NT);

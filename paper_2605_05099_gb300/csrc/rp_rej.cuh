@@ -50,12 +50,16 @@ __device__ bool rej_tile(const FillArgs& a, u64 k, const E& e, RejSmem<NT>& sm, 
   for (int hb = 0; hb < C / kStage; ++hb) {
     int ns = 0;
 #pragma unroll
-    for (int j = 0; j < kStage; ++j) {
-      const u64 u = g.next();
+    for (int j = 0; j < kStage; j += E::kStep) {
+      u64 u[2];
+      g.next_step(u);
       // branch-free: every word's value lands in the next free slot (ns <= j
       // < kRow), which advances only for accepted words
-      stage[lane * kRow + ns] = __umul64hi(u, m);
-      ns += (int)(u * m >= thr);
+#pragma unroll
+      for (int i = 0; i < E::kStep; ++i) {
+        stage[lane * kRow + ns] = __umul64hi(u[i], m);
+        ns += (int)(u[i] * m >= thr);
+      }
     }
     __syncwarp();
     const int pk = (cnt << 5) | ns;   // run length so far and new values, one shuffle
