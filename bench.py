@@ -34,11 +34,11 @@ WORKLOAD = "single-stream fills: engines {xoshiro256++, PCG64-DXSM, Philox4x32-1
 # one ncu capture at n = 2^26 scaled by outputs (profiles/*_n2e26.md), by fill
 # key.  Only kernels whose current version was captured are listed.
 TRAFFIC = {
-    "philox4x32_10/normal": 4 * 514791680,
-    "xoshiro256pp/normal": 4 * 526808576,
-    "philox4x32_10/bounded:9223372036854775809": 4 * 1580691952,
-    "xoshiro256pp/bounded:6": 4 * 482843392,
-    "xoshiro256pp/bounded:1000000007": 4 * 482843392,
+    "philox4x32_10/normal": 4 * 513975040,
+    "xoshiro256pp/normal": 4 * 515962880,
+    "philox4x32_10/bounded:9223372036854775809": 4 * 1530964224,
+    "xoshiro256pp/bounded:6": 4 * 482469632,
+    "xoshiro256pp/bounded:1000000007": 4 * 482469632,
 }
 
 
@@ -50,9 +50,11 @@ TRAFFIC = {
 #   PCG64-DXSM    LCG step: 128 x 64-bit multiply mod 2^128 (12 products,
 #                 ~10 carry adds) and the 128-bit increment (4); DXSM
 #                 output: or, two xor-shifts and two 64-bit multiplies  -> 42
-#   Philox4x32-10 per 128-bit block ten rounds of two 32 x 32 -> 64
-#                 products (4), four xors and two key adds              -> 50 per word
-ENGINE_OPS = {"xoshiro256pp": 20, "pcg64dxsm": 42, "philox4x32_10": 50}
+#   Philox4x32-10 per 128-bit block: the counter increment (4) and ten
+#                 rounds of two 32 x 32 -> 64 products (4) and four xors;
+#                 the round keys depend on the key alone, so every block
+#                 of a fill shares them                                 -> 42 per word
+ENGINE_OPS = {"xoshiro256pp": 20, "pcg64dxsm": 42, "philox4x32_10": 42}
 # integer lanes per SM and clock for adds, shifts and multiply-adds on this GPU
 INT_LANES_PER_SM = 64
 SMS = 152
