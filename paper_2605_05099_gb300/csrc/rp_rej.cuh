@@ -72,6 +72,9 @@ __device__ bool rej_tile(const FillArgs& a, u64 k, const E& e, RejSmem<NT>& sm, 
     __syncwarp();
     cnt += ns;
   }
+  // the run was written over the whole pass and has mostly left L2 by now:
+  // start bringing it back while the scan and the look-back run
+  for (int i = 0; i < cnt; i += 16) asm volatile("prefetch.global.L2 [%0];" ::"l"(pw + lane * C + i));
   // ---------------- offsets
   const int off = block_exclusive_scan<NT>(cnt, sm.wsum, &sm.misc[1]);   // also orders the parked runs before pass 2
   if (t < 32) {
