@@ -83,6 +83,8 @@ def lib():
             "or_fill_exp": (None, [P(Gen), sz, vp, vp]),
             "or_fill_gamma": (i32, [P(Gen), sz, dbl, vp, vp]),
             "or_fill_beta": (i32, [P(Gen), sz, dbl, dbl, vp, vp]),
+            "or_fill_derived": (i32, [P(Gen), i32, sz, vp, vp, vp]),
+            "or_cr_pow": (dbl, [dbl, dbl]),
             "or_zig_normal_x": (dbl, [u64]),
             "or_zig_table": (i32, [i32, i32, P(u64), P(dbl), P(dbl)]),
             "or_zig_R": (dbl, [i32]),
@@ -230,6 +232,31 @@ def fill(g, dist, n, *params, with_start=False):
     else:
         raise ValueError(dist)
     return (out, start) if with_start else out
+
+
+# derived distributions (Table "continuous"): name -> (kind, parameter names)
+DERIVED = {"unif": (1, ("a", "b")), "normal_ms": (2, ("mu", "sigma")), "lognormal": (3, ("mu", "sigma")),
+           "exp_scale": (4, ("beta",)), "gamma_scale": (5, ("alpha", "theta")), "chi2": (6, ("nu",)),
+           "gumbel": (7, ("mu", "beta")), "pareto": (8, ("x_m", "alpha")), "weibull": (9, ("k", "lambda")),
+           "gpd": (10, ("mu", "sigma", "xi")), "f": (11, ("nu1", "nu2")), "skew_normal": (12, ("mu", "sigma", "alpha"))}
+
+
+def fill_derived(g, name, n, *params, with_start=False):
+    """One derived-distribution fill on generator g (advances g)."""
+    kind, names = DERIVED[name]
+    if len(params) != len(names):
+        raise ValueError(f"{name} takes {names}")
+    p = np.zeros(4, np.float64)
+    p[: len(params)] = params
+    out = np.empty(n, np.float64)
+    start = np.empty(n, np.uint64) if with_start else None
+    if lib().or_fill_derived(ctypes.byref(g), kind, n, _ptr(p), _ptr(out), _ptr(start)) != 0:
+        raise ValueError(f"bad parameters for {name}")
+    return (out, start) if with_start else out
+
+
+def cr_pow(x, y):
+    return lib().or_cr_pow(float(x), float(y))
 
 
 def zig_counts():

@@ -716,6 +716,112 @@ int or_fill_beta(or_gen* g, size_t n, double a, double b, double* out, uint64_t*
   return 0;
 }
 
+/* ---- derived distributions (Table "continuous"; Sec. 3.1 "Gamma and
+ * related distributions", "Extreme value and Weibull distributions") ----
+ * Each is a transform of the base samplers above, in the stream order of
+ * its draws.  Every arithmetic step is one IEEE operation in the order the
+ * formula is written (no contraction); exp, log and pow are correctly
+ * rounded.  Readings: unif = a + (b - a) u; normal = mu + sigma z;
+ * lognormal = exp(mu + sigma z); Exp(beta) and Gamma(alpha, theta) scale by
+ * beta and theta; chi2(nu) = 2 Gamma(nu / 2); Gumbel = mu - beta log(-log u)
+ * with u = U53; Pareto = x_m exp(E / alpha); Weibull = lambda pow(E, 1 / k);
+ * generalized Pareto from P = Pareto(1, 1 / |xi|) as the paper writes it;
+ * F = (X / nu1) / (Y / nu2) with X ~ Gamma(nu1 / 2) drawn before
+ * Y ~ Gamma(nu2 / 2); skew normal (Azzalini's representation) from two
+ * consecutive normals u0, u1: z = delta |u0| + sqrt(1 - delta^2) u1,
+ * delta = alpha / sqrt(1 + alpha^2), x = mu + sigma z. */
+
+/* pow(x, y) for x > 0, correctly rounded: exp(y log x) in double-double */
+double or_cr_pow(double x, double y) {
+  if (x == 1.0 || y == 0.0) return 1.0;
+  if (x == 0.0) return y > 0.0 ? 0.0 : INFINITY;
+  if (isinf(x)) return y > 0.0 ? INFINITY : 0.0;
+  dd t = dd_mul_d(dd_log(x), y);
+  if (t.hi > 709.0) return INFINITY;
+  if (t.hi < -708.0) return pow(x, y);   /* subnormal results: not reached by the samplers */
+  dd e = dd_exp(t.hi);
+  /* exp(hi + lo) = exp(hi) (1 + lo + lo^2 / 2 + ...), |lo| <= 2^-43 */
+  dd c = two_sum(1.0, t.lo);
+  c = dd_add(c, (dd){0.5 * t.lo * t.lo, 0.0});
+  return dd_round(dd_mul(e, c));
+}
+
+static double derived_value(int kind, double x, const double* p) {
+  switch (kind) {
+    case OR_D_UNIF: return p[0] + (p[1] - p[0]) * x;
+    case OR_D_NORMAL_MS: return p[0] + p[1] * x;
+    case OR_D_LOGNORMAL: return or_cr_exp(p[0] + p[1] * x);
+    case OR_D_EXP_SCALE: return p[0] * x;
+    case OR_D_GAMMA_SCALE: return p[1] * x;
+    case OR_D_CHI2: return 2.0 * x;
+    case OR_D_GUMBEL: return p[0] - p[1] * or_cr_log(-or_cr_log(x));
+    case OR_D_PARETO: return p[0] * or_cr_exp(x / p[1]);
+    case OR_D_WEIBULL: return p[1] * or_cr_pow(x, 1.0 / p[0]);
+    case OR_D_GPD: {
+      double mu = p[0], sigma = p[1], xi = p[2];
+      if (xi == 0.0) return mu + sigma * x;
+      double P = 1.0 * or_cr_exp(x / (1.0 / fabs(xi)));
+      if (xi > 0.0) return mu + sigma * (P - 1.0) / xi;
+      return mu - sigma * (1.0 - 1.0 / P) / xi;
+    }
+    default: return NAN;
+  }
+}
+
+int or_fill_derived(or_gen* g, int kind, size_t n, const double* p, double* out, uint64_t* start) {
+  switch (kind) {
+    case OR_D_UNIF:
+    case OR_D_GUMBEL:
+      or_fill_uniform(g, n, out);
+      if (start) for (size_t i = 0; i < n; ++i) start[i] = g->pos - n + i;
+      break;
+    case OR_D_NORMAL_MS:
+    case OR_D_LOGNORMAL:
+      or_fill_normal(g, n, out, start);
+      break;
+    case OR_D_EXP_SCALE:
+    case OR_D_PARETO:
+    case OR_D_WEIBULL:
+    case OR_D_GPD:
+      or_fill_exp(g, n, out, start);
+      break;
+    case OR_D_GAMMA_SCALE:
+      if (or_fill_gamma(g, n, p[0], out, start)) return -1;
+      break;
+    case OR_D_CHI2:
+      if (or_fill_gamma(g, n, 0.5 * p[0], out, start)) return -1;
+      break;
+    case OR_D_F: {
+      double a = 0.5 * p[0], b = 0.5 * p[1];
+      if (!(a > 0.0) || !(b > 0.0)) return -1;
+      mt_consts ka = mt_setup(a >= 1.0 ? a : a + 1.0), kb = mt_setup(b >= 1.0 ? b : b + 1.0);
+      for (size_t i = 0; i < n; ++i) {
+        double X = gamma_one(g, a, ka, start ? start + i : NULL);
+        double Y = gamma_one(g, b, kb, NULL);
+        out[i] = (X / p[0]) / (Y / p[1]);
+      }
+      return 0;
+    }
+    case OR_D_SKEW_NORMAL: {
+      double al = p[2];
+      double delta = al / sqrt(1.0 + al * al);
+      double omega = sqrt(1.0 - delta * delta);
+      for (size_t i = 0; i < n; ++i) {
+        double u[2];
+        or_fill_normal(g, 1, &u[0], start ? start + i : NULL);
+        or_fill_normal(g, 1, &u[1], NULL);
+        double z = delta * fabs(u[0]) + omega * u[1];
+        out[i] = p[0] + p[1] * z;
+      }
+      return 0;
+    }
+    default:
+      return -1;
+  }
+  for (size_t i = 0; i < n; ++i) out[i] = derived_value(kind, out[i], p);
+  return 0;
+}
+
 /* ======================================================================
  * Pathwise gradients.  For z ~ F(.; theta) drawn as z = F^{-1}(u; theta),
  * dz/dtheta = -(dF/dtheta)(z) / f(z).  Written as integrals whose integrand

@@ -80,6 +80,16 @@ void or_fill_normal(or_gen* g, size_t n, double* out, uint64_t* start);
 void or_fill_exp(or_gen* g, size_t n, double* out, uint64_t* start);
 int  or_fill_gamma(or_gen* g, size_t n, double alpha, double* out, uint64_t* start);
 int  or_fill_beta(or_gen* g, size_t n, double a, double b, double* out, uint64_t* start);
+
+/* derived distributions (Table "continuous"): kinds and parameters p[]
+ *   UNIF (a, b), NORMAL_MS (mu, sigma), LOGNORMAL (mu, sigma), EXP_SCALE (beta),
+ *   GAMMA_SCALE (alpha, theta), CHI2 (nu), GUMBEL (mu, beta), PARETO (x_m, alpha),
+ *   WEIBULL (k, lambda), GPD (mu, sigma, xi), F (nu1, nu2), SKEW_NORMAL (mu, sigma, alpha) */
+enum { OR_D_UNIF = 1, OR_D_NORMAL_MS = 2, OR_D_LOGNORMAL = 3, OR_D_EXP_SCALE = 4, OR_D_GAMMA_SCALE = 5,
+       OR_D_CHI2 = 6, OR_D_GUMBEL = 7, OR_D_PARETO = 8, OR_D_WEIBULL = 9, OR_D_GPD = 10, OR_D_F = 11,
+       OR_D_SKEW_NORMAL = 12 };
+int  or_fill_derived(or_gen* g, int kind, size_t n, const double* p, double* out, uint64_t* start);
+double or_cr_pow(double x, double y);
 /* ziggurat internals for tests */
 double or_zig_normal_x(uint64_t u);              /* candidate x = +-RN(r*w_i) */
 int    or_zig_table(int which, int i, uint64_t* k, double* w, double* f); /* 0 normal, 1 exp */
