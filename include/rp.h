@@ -106,6 +106,39 @@ rp_status rp_fill_gamma(rp_engine engine, uint64_t seed, uint64_t stream, uint64
 rp_status rp_fill_beta(rp_engine engine, uint64_t seed, uint64_t stream, uint64_t* pos,
                        size_t n, double a, double b, double* d_out, void* cuda_stream);
 
+/* Derived distributions (Table "continuous"; Sec. 3.1 "Gamma and related
+ * distributions", "Extreme value and Weibull distributions").  Each output
+ * transforms the base sampler's variate as it is written, in the formula's
+ * order, one IEEE operation per step:
+ *   RP_UNIF         (a, b)          a + (b - a) u, u the 53-bit uniform; a <= b
+ *   RP_NORMAL_MS    (mu, sigma)     mu + sigma z, z standard normal
+ *   RP_LOGNORMAL    (mu, sigma)     exp(mu + sigma z)
+ *   RP_EXP_SCALE    (beta)          beta E, E standard exponential
+ *   RP_GAMMA_SCALE  (alpha, theta)  theta Gamma(alpha)
+ *   RP_CHI2         (nu)            2 Gamma(nu / 2)
+ *   RP_GUMBEL       (mu, beta)      mu - beta log(-log u)
+ *   RP_PARETO       (x_m, alpha)    x_m exp(E / alpha)
+ *   RP_WEIBULL      (k, lambda)     lambda pow(E, 1 / k)
+ *   RP_GPD          (mu, sigma, xi) P = Pareto(1, 1/|xi|): mu + sigma (P - 1) / xi
+ *                                   (xi > 0), mu - sigma (1 - 1/P) / xi (xi < 0),
+ *                                   mu + sigma E (xi = 0)
+ *   RP_F            (nu1, nu2)      (X / nu1) / (Y / nu2), X ~ Gamma(nu1/2) drawn
+ *                                   before Y ~ Gamma(nu2/2)
+ *   RP_SKEW_NORMAL  (mu, sigma, alpha)  two consecutive normals u0, u1:
+ *                                   mu + sigma (delta |u0| + sqrt(1 - delta^2) u1),
+ *                                   delta = alpha / sqrt(1 + alpha^2)
+ * params: 4 doubles (unused ones ignored), host memory.  Scale and shape
+ * parameters must be positive and finite, locations finite; otherwise
+ * RP_ERR_PARAM before any device work.  exp and pow are CUDA's (one and two
+ * ulp), Gumbel's logs correctly rounded; the decisions of the base samplers
+ * are exact as in the base fills.  *pos advances by the base words used. */
+typedef enum {
+  RP_UNIF = 1, RP_NORMAL_MS = 2, RP_LOGNORMAL = 3, RP_EXP_SCALE = 4, RP_GAMMA_SCALE = 5, RP_CHI2 = 6,
+  RP_GUMBEL = 7, RP_PARETO = 8, RP_WEIBULL = 9, RP_GPD = 10, RP_F = 11, RP_SKEW_NORMAL = 12
+} rp_derived;
+rp_status rp_fill_derived(rp_engine engine, uint64_t seed, uint64_t stream, uint64_t* pos, rp_derived kind,
+                          const double* params, size_t n, double* d_out, void* cuda_stream);
+
 /* ---------------------------------------------------------------------
  * Distributions by code, fills from explicit state, substreams and
  * batched fills.

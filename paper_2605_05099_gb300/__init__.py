@@ -59,6 +59,7 @@ def lib():
             "rp_fill_exp": [i32, u64, u64, pu64, sz, vp, vp],
             "rp_fill_gamma": [i32, u64, u64, pu64, sz, dbl, vp, vp],
             "rp_fill_beta": [i32, u64, u64, pu64, sz, dbl, dbl, vp, vp],
+            "rp_fill_derived": [i32, u64, u64, pu64, i32, ctypes.POINTER(dbl), sz, vp, vp],
             "rp_seed_state": [i32, u64, u64, pu64, ctypes.POINTER(i32)],
             "rp_jump_state": [i32, pu64, u64, u64],
             "rp_ziggurat_tables": [i32, pu64, ctypes.POINTER(dbl), ctypes.POINTER(dbl), ctypes.POINTER(dbl)],
@@ -160,6 +161,28 @@ def rp_fill_gamma(engine, seed, stream, pos, alpha, out, cuda_stream=None):
 def rp_fill_beta(engine, seed, stream, pos, a, b, out, cuda_stream=None):
     return _fill(lib().rp_fill_beta, engine, seed, stream, pos, out, torch.float64, (float(a), float(b)),
                  cuda_stream)
+
+
+# Derived distributions (Table "continuous"): name -> (rp_derived code,
+# parameter names); see rp_fill_derived in include/rp.h for the formulas.
+DERIVED = {"unif": (1, ("a", "b")), "normal_ms": (2, ("mu", "sigma")), "lognormal": (3, ("mu", "sigma")),
+           "exp_scale": (4, ("beta",)), "gamma_scale": (5, ("alpha", "theta")), "chi2": (6, ("nu",)),
+           "gumbel": (7, ("mu", "beta")), "pareto": (8, ("x_m", "alpha")), "weibull": (9, ("k", "lambda")),
+           "gpd": (10, ("mu", "sigma", "xi")), "f": (11, ("nu1", "nu2")), "skew_normal": (12, ("mu", "sigma", "alpha"))}
+
+
+def rp_fill_derived(engine, seed, stream, pos, name, params, out, cuda_stream=None):
+    """Fill `out` (float64 CUDA tensor) with a derived distribution `name`
+    (a key of DERIVED) and its parameters; returns the new stream position."""
+    kind, names = DERIVED[name]
+    if len(params) != len(names):
+        raise ValueError(f"{name} takes {names}")
+    p, n = _out(out, torch.float64)
+    q = (ctypes.c_double * 4)(*([float(x) for x in params] + [0.0] * (4 - len(params))))
+    cpos = ctypes.c_uint64(pos)
+    _check(lib().rp_fill_derived(_engine(engine), seed, stream, ctypes.byref(cpos), kind, q, n, p,
+                                 _stream_handle(cuda_stream)))
+    return cpos.value
 
 
 def _ptr_or_null(t, n):

@@ -184,6 +184,7 @@ __device__ __forceinline__ double cr_exp_dev(double x) {
 __device__ __forceinline__ double cr_log_dev(double y) {
   if (y == 1.0) return 0.0;
   if (y == 0.0) return -__longlong_as_double(0x7ff0000000000000ll);
+  if (y == __longlong_as_double(0x7ff0000000000000ll)) return y;   // log(+inf) = +inf
   return dd_log_dev(y).hi;
 }
 

@@ -105,6 +105,31 @@ __device__ __forceinline__ bool tail_pair_accept(u64 w1, u64 w2, const ZigDev& z
   return __dadd_rn(b, b) > __dmul_rn(a, a);
 }
 
+// ------------------------------------------------------------------ derived distributions
+// Output transform of a base variate x (Table "continuous"; Sec. 3.1 "Gamma
+// and related", "Extreme value and Weibull"): one IEEE operation per step,
+// in the order of the formula.  exp and pow are CUDA's (one and two ulp);
+// Gumbel's logs are the library's correctly rounded ones.  Out of line: it
+// runs once per output of a derived fill and stays out of the base fills.
+__device__ __noinline__ double epi_apply(double x, const SampArgs& a) {
+  const double* p = a.ep;
+  switch (a.epi) {
+    case EPI_AFFINE: return __dadd_rn(p[0], __dmul_rn(p[1], x));
+    case EPI_SCALE: return __dmul_rn(p[0], x);
+    case EPI_LOGNORMAL: return exp(__dadd_rn(p[0], __dmul_rn(p[1], x)));
+    case EPI_GUMBEL: return __dsub_rn(p[0], __dmul_rn(p[1], cr_log_nl(-cr_log_nl(x))));
+    case EPI_PARETO: return __dmul_rn(p[0], exp(__ddiv_rn(x, p[1])));
+    case EPI_WEIBULL: return __dmul_rn(p[1], pow(x, p[0]));
+    case EPI_GPD: {
+      if (p[2] == 0.0) return __dadd_rn(p[0], __dmul_rn(p[1], x));
+      const double P = exp(__ddiv_rn(x, p[3]));   // Pareto(1, 1/|xi|) = exp(E / (1/|xi|))
+      if (p[2] > 0.0) return __dadd_rn(p[0], __ddiv_rn(__dmul_rn(p[1], __dsub_rn(P, 1.0)), p[2]));
+      return __dsub_rn(p[0], __ddiv_rn(__dmul_rn(p[1], __dsub_rn(1.0, __ddiv_rn(1.0, P))), p[2]));
+    }
+    default: return x;
+  }
+}
+
 #include "rp_gamma.cuh"
 
 // ------------------------------------------------------------------ samplers
@@ -120,6 +145,13 @@ struct SampUniform {
   static constexpr bool kCheckReject = false;
   typedef double out_t;
   __device__ static __forceinline__ double value1(u64 u, const SampArgs&) { return u53_bits(u); }
+};
+// Uniform base of a derived distribution (unif, Gumbel).
+struct SampUniformE {
+  static constexpr bool kOnePerWord = true;
+  static constexpr bool kCheckReject = false;
+  typedef double out_t;
+  __device__ static __forceinline__ double value1(u64 u, const SampArgs& a) { return epi_apply(u53_bits(u), a); }
 };
 
 // Lemire with no rejection assumed: word p gives output p, hi(u m); every
@@ -598,7 +630,9 @@ __global__ void k_tails(FillArgs a) {
   OT* out = (OT*)a.out;
   for (unsigned long long i = blockIdx.x * (u64)blockDim.x + threadIdx.x; i < n; i += (u64)gridDim.x * blockDim.x) {
     TailEntry te = a.tailq[i];
-    out[te.g] = (OT)S::tail_value(te.w0, te.w1, z);
+    double v = S::tail_value(te.w0, te.w1, z);
+    if (a.sp.epi) v = epi_apply(v, a.sp);
+    out[te.g] = (OT)v;
   }
 }
 
@@ -675,11 +709,11 @@ template <class E>
 int dispatch_dist(const FillArgs& a, int grid, cudaStream_t s, int* occ) {
   switch (a.dist) {
     case D_U64: return launch_es<E, SampU64>(a, grid, s, occ);
-    case D_UNIFORM: return launch_es<E, SampUniform>(a, grid, s, occ);
+    case D_UNIFORM: return a.sp.epi ? launch_es<E, SampUniformE>(a, grid, s, occ) : launch_es<E, SampUniform>(a, grid, s, occ);
     case D_BOUNDED: return launch_rej<E>(a, grid, s, occ);
     case D_BOUNDED_ONE: return launch_es<E, SampBoundedOne>(a, grid, s, occ);
-    case D_NORMAL: return launch_lean<E, LeanNormal>(a, grid, s, occ);
-    case D_EXP: return launch_lean<E, LeanExp>(a, grid, s, occ);
+    case D_NORMAL: return a.sp.epi ? launch_lean<E, LeanNormalE>(a, grid, s, occ) : launch_lean<E, LeanNormal>(a, grid, s, occ);
+    case D_EXP: return a.sp.epi ? launch_lean<E, LeanExpE>(a, grid, s, occ) : launch_lean<E, LeanExp>(a, grid, s, occ);
     case D_GAMMA: return launch_merge<E, SampGamma>(a, grid, s, occ);
     case D_BETA: return launch_merge<E, SampBeta>(a, grid, s, occ);
     default: return (int)cudaErrorInvalidValue;

@@ -191,7 +191,8 @@ struct SampGamma {
   };
   __device__ static __forceinline__ bool needs_tail(const u64* r) { return (r[0] & 0xff) == 2; }
   __device__ static __forceinline__ double value(const u64* r, const SampArgs& a, const ZigDev& z) {
-    return gamma_value((int)(r[0] & 0xff), r[1], r[2], r[3], a.ga, z);
+    const double g = gamma_value((int)(r[0] & 0xff), r[1], r[2], r[3], a.ga, z);
+    return a.epi ? epi_apply(g, a) : g;   // Gamma(alpha, theta), chi2
   }
 };
 
@@ -226,6 +227,7 @@ struct SampBeta {
   __device__ static __forceinline__ double value(const u64* r, const SampArgs& a, const ZigDev& z) {
     double X = gamma_value((int)(r[0] & 0xff), r[1], r[2], r[3], a.ga, z);
     double Y = gamma_value((int)((r[0] >> 8) & 0xff), r[4], r[5], r[6], a.gb, z);
+    if (a.epi == EPI_F) return __ddiv_rn(__ddiv_rn(X, a.ep[0]), __ddiv_rn(Y, a.ep[1]));   // F(nu1, nu2)
     return __ddiv_rn(X, __dadd_rn(X, Y));
   }
 };

@@ -529,8 +529,8 @@ rp_status run_fill_state_locked(int engine, const u64 s_in[4], u64* pos, size_t 
   a.sp = sp;
   rp::TileGeom tg = rp::tile_geom(engine, dist);
   const u64 T = (u64)tg.tile_words;
-  auto key = std::make_pair(engine, dist);
-  if (!g_occ.count(key)) g_occ[key] = rp::occupancy_blocks(engine, dist);
+  auto key = std::make_pair(engine, dist | (sp.epi ? 256 : 0));   // transformed fills run other kernels
+  if (!g_occ.count(key)) g_occ[key] = rp::occupancy_blocks(engine, dist, sp.epi);
   int occ = g_occ[key] > 0 ? g_occ[key] : 1;
   const bool trivial = (dist == rp::D_U64 || dist == rp::D_UNIFORM || dist == rp::D_BOUNDED_ONE);
   const bool one_pass_check = dist == rp::D_BOUNDED_ONE;
@@ -655,6 +655,31 @@ rp_status run_fill(int engine, u64 seed, u64 stream, u64* pos, size_t n, int dis
   return run_fill_state_locked(engine, s, pos, n, dist, sp, d_out, cstream);
 }
 
+// Two base variates per output, consecutive in the stream: a base fill of 2n
+// (in blocks, to bound the scratch) and the pairwise kernel (launch_pairs).
+rp_status pairs_fill(int engine, u64 seed, u64 stream, u64* pos, size_t n, int base, const rp::SampArgs& sb, int mode,
+                     const double* q, double* d_out, void* cuda_stream) {
+  rp_status st = check_fill_args(engine, pos, n, d_out);
+  if (st || n == 0) return st;
+  const size_t blk = (size_t)1 << 24;
+  double* tmp = nullptr;
+  size_t cap = std::min(n, blk);
+  int e = (int)cudaMalloc((void**)&tmp, cap * 2 * sizeof(double));
+  if (e) return fail(RP_ERR_NOMEM, "pair scratch allocation failed");
+  u64 p = *pos;
+  for (size_t done = 0; done < n && st == RP_OK; done += cap) {
+    size_t m = std::min(cap, n - done);
+    st = run_fill(engine, seed, stream, &p, 2 * m, base, sb, tmp, cuda_stream);
+    if (st) break;
+    e = rp::launch_pairs(tmp, d_out + done, m, mode, q, cuda_stream);
+    if (!e) e = (int)cudaStreamSynchronize((cudaStream_t)cuda_stream);
+    if (e) st = cuda_fail(e, "pairwise outputs");
+  }
+  cudaFree(tmp);
+  if (st == RP_OK) *pos = p;
+  return st;
+}
+
 }  // namespace
 
 extern "C" {
@@ -713,31 +738,85 @@ rp_status rp_fill_beta(rp_engine engine, uint64_t seed, uint64_t stream, uint64_
   sp.gb = mt_params(b);
   if (a != b) return run_fill(engine, seed, stream, (u64*)pos, n, rp::D_BETA, sp, d_out, cuda_stream);
   // Equal shapes: X and Y are consecutive Gamma(a) variates of the stream, so
-  // the fill is a gamma fill of 2n followed by the pairwise ratio.  Done in
-  // blocks to bound the scratch buffer.
-  if (!pos) return fail(RP_ERR_NULL, "pos is NULL");
-  if (n == 0) return RP_OK;
-  if (!d_out) return fail(RP_ERR_NULL, "output pointer is NULL");
-  const size_t blk = (size_t)1 << 24;
-  double* tmp = nullptr;
-  size_t cap = std::min(n, blk);
-  int e = (int)cudaMalloc((void**)&tmp, cap * 2 * sizeof(double));
-  if (e) return fail(RP_ERR_NOMEM, "beta scratch allocation failed");
-  u64 p = *pos;
-  rp_status st = RP_OK;
-  for (size_t done = 0; done < n && st == RP_OK; done += cap) {
-    size_t m = std::min(cap, n - done);
-    rp::SampArgs sg{};
-    sg.ga = sp.ga;
-    st = run_fill(engine, seed, stream, &p, 2 * m, rp::D_GAMMA, sg, tmp, cuda_stream);
-    if (st) break;
-    e = rp::launch_beta_pairs(tmp, d_out + done, m, cuda_stream);
-    if (!e) e = (int)cudaStreamSynchronize((cudaStream_t)cuda_stream);
-    if (e) st = cuda_fail(e, "beta pairs");
+  // the fill is a gamma fill of 2n followed by the pairwise ratio.
+  rp::SampArgs sg{};
+  sg.ga = sp.ga;
+  return pairs_fill(engine, seed, stream, (u64*)pos, n, rp::D_GAMMA, sg, 0, nullptr, d_out, cuda_stream);
+}
+
+// Derived distributions (Table "continuous"): a base fill whose outputs are
+// transformed as they are written (see the Epi codes), or, for two draws of
+// one law per output, a base fill of 2n and a pairwise kernel.
+rp_status rp_fill_derived(rp_engine engine, uint64_t seed, uint64_t stream, uint64_t* pos, rp_derived kind,
+                          const double* params, size_t n, double* d_out, void* cuda_stream) {
+  if (!params) return fail(RP_ERR_NULL, "params is NULL");
+  const double p0 = params[0], p1 = params[1], p2 = params[2];
+  auto finite = [](double x) { return std::isfinite(x); };
+  auto positive = [](double x) { return x > 0.0 && std::isfinite(x); };
+  rp::SampArgs sp{};
+  int dist = -1;
+  switch (kind) {
+    case RP_UNIF:
+      if (!finite(p0) || !finite(p1) || !(p0 <= p1) || !finite(p1 - p0)) return fail(RP_ERR_PARAM, "unif needs finite a <= b");
+      dist = rp::D_UNIFORM; sp.epi = rp::EPI_AFFINE; sp.ep[0] = p0; sp.ep[1] = p1 - p0;
+      break;
+    case RP_NORMAL_MS:
+    case RP_LOGNORMAL:
+      if (!finite(p0) || !positive(p1)) return fail(RP_ERR_PARAM, "needs finite mu and sigma > 0");
+      dist = rp::D_NORMAL; sp.epi = kind == RP_NORMAL_MS ? rp::EPI_AFFINE : rp::EPI_LOGNORMAL;
+      sp.ep[0] = p0; sp.ep[1] = p1;
+      break;
+    case RP_EXP_SCALE:
+      if (!positive(p0)) return fail(RP_ERR_PARAM, "exponential scale must be positive");
+      dist = rp::D_EXP; sp.epi = rp::EPI_SCALE; sp.ep[0] = p0;
+      break;
+    case RP_GAMMA_SCALE:
+      if (!positive(p0) || !positive(p1)) return fail(RP_ERR_PARAM, "gamma shape and scale must be positive");
+      dist = rp::D_GAMMA; sp.ga = mt_params(p0); sp.epi = rp::EPI_SCALE; sp.ep[0] = p1;
+      break;
+    case RP_CHI2:
+      if (!positive(p0)) return fail(RP_ERR_PARAM, "chi2 degrees of freedom must be positive");
+      dist = rp::D_GAMMA; sp.ga = mt_params(0.5 * p0); sp.epi = rp::EPI_SCALE; sp.ep[0] = 2.0;
+      break;
+    case RP_GUMBEL:
+      if (!finite(p0) || !positive(p1)) return fail(RP_ERR_PARAM, "gumbel needs finite mu and beta > 0");
+      dist = rp::D_UNIFORM; sp.epi = rp::EPI_GUMBEL; sp.ep[0] = p0; sp.ep[1] = p1;
+      break;
+    case RP_PARETO:
+      if (!positive(p0) || !positive(p1)) return fail(RP_ERR_PARAM, "pareto x_m and alpha must be positive");
+      dist = rp::D_EXP; sp.epi = rp::EPI_PARETO; sp.ep[0] = p0; sp.ep[1] = p1;
+      break;
+    case RP_WEIBULL:
+      if (!positive(p0) || !positive(p1)) return fail(RP_ERR_PARAM, "weibull k and lambda must be positive");
+      dist = rp::D_EXP; sp.epi = rp::EPI_WEIBULL; sp.ep[0] = 1.0 / p0; sp.ep[1] = p1;
+      break;
+    case RP_GPD:
+      if (!finite(p0) || !positive(p1) || !finite(p2)) return fail(RP_ERR_PARAM, "gpd needs finite mu, xi and sigma > 0");
+      dist = rp::D_EXP; sp.epi = rp::EPI_GPD; sp.ep[0] = p0; sp.ep[1] = p1; sp.ep[2] = p2;
+      sp.ep[3] = p2 != 0.0 ? 1.0 / std::fabs(p2) : 0.0;
+      break;
+    case RP_F: {
+      if (!positive(p0) || !positive(p1)) return fail(RP_ERR_PARAM, "F degrees of freedom must be positive");
+      sp.ga = mt_params(0.5 * p0);
+      sp.gb = mt_params(0.5 * p1);
+      sp.epi = rp::EPI_F; sp.ep[0] = p0; sp.ep[1] = p1;
+      if (0.5 * p0 != 0.5 * p1) return run_fill(engine, seed, stream, (u64*)pos, n, rp::D_BETA, sp, d_out, cuda_stream);
+      rp::SampArgs sg{};
+      sg.ga = sp.ga;
+      const double q[4] = {p0, p1, 0.0, 0.0};
+      return pairs_fill(engine, seed, stream, (u64*)pos, n, rp::D_GAMMA, sg, 1, q, d_out, cuda_stream);
+    }
+    case RP_SKEW_NORMAL: {
+      if (!finite(p0) || !positive(p1) || !finite(p2)) return fail(RP_ERR_PARAM, "skew normal needs finite mu, alpha and sigma > 0");
+      const double delta = p2 / std::sqrt(1.0 + p2 * p2);
+      const double q[4] = {p0, p1, delta, std::sqrt(1.0 - delta * delta)};
+      rp::SampArgs sn{};
+      return pairs_fill(engine, seed, stream, (u64*)pos, n, rp::D_NORMAL, sn, 2, q, d_out, cuda_stream);
+    }
+    default:
+      return fail(RP_ERR_PARAM, "unknown derived distribution " + std::to_string((int)kind));
   }
-  cudaFree(tmp);
-  if (st == RP_OK) *pos = p;
-  return st;
+  return run_fill(engine, seed, stream, (u64*)pos, n, dist, sp, d_out, cuda_stream);
 }
 
 namespace {
@@ -866,7 +945,7 @@ rp_status static_setup(int dev, StaticDev& D) {
   int sms = 0;
   e = (int)cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e) return cuda_fail(e, "device attribute");
-  int occ = rp::occupancy_blocks(RP_PHILOX4X32_10, rp::D_NORMAL);
+  int occ = rp::occupancy_blocks(RP_PHILOX4X32_10, rp::D_NORMAL, 0);
   D.base = (unsigned long long*)p;
   D.grid_cap = (u64)(sms > 0 ? sms : 1) * (u64)(occ > 0 ? occ : 1);
   D.ready = true;
@@ -1016,7 +1095,7 @@ rp_status beta_equal_state_locked(int engine, const u64 s[4], u64* pos, size_t n
     sg.ga = sp.ga;
     st = run_fill_state_locked(engine, s, &p, 2 * m, rp::D_GAMMA, sg, tmp, cstream);
     if (st) break;
-    e = rp::launch_beta_pairs(tmp, d_out + done, m, cstream);
+    e = rp::launch_pairs(tmp, d_out + done, m, 0, nullptr, cstream);
     if (!e) e = (int)cudaStreamSynchronize((cudaStream_t)cstream);
     if (e) st = cuda_fail(e, "beta pairs");
   }

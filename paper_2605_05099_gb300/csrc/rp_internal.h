@@ -66,10 +66,26 @@ struct MTParams {
   int pad;
 };
 
+// Output transforms of the derived distributions (Table "continuous"),
+// applied to each base variate as it is written.  Parameters ep[]:
+//   EPI_AFFINE   ep0 + ep1 x                 unif (a, b - a), normal (mu, sigma)
+//   EPI_SCALE    ep0 x                       Exp(beta), Gamma(alpha, theta), chi2 (2)
+//   EPI_LOGNORMAL exp(ep0 + ep1 x)           (mu, sigma)
+//   EPI_GUMBEL   ep0 - ep1 log(-log x)       (mu, beta), correctly rounded logs
+//   EPI_PARETO   ep0 exp(x / ep1)            (x_m, alpha)
+//   EPI_WEIBULL  ep1 pow(x, ep0)             (1/k, lambda)
+//   EPI_GPD      generalized Pareto          (mu, sigma, xi, 1/|xi|)
+//   EPI_F        (X / ep0) / (Y / ep1)       beta record of Gamma(nu1/2), Gamma(nu2/2)
+enum Epi : int { EPI_NONE = 0, EPI_AFFINE = 1, EPI_SCALE = 2, EPI_LOGNORMAL = 3, EPI_GUMBEL = 4, EPI_PARETO = 5,
+                 EPI_WEIBULL = 6, EPI_GPD = 7, EPI_F = 8 };
+
 struct SampArgs {
   unsigned long long m;       // bounded: modulus (0 = full range)
   unsigned long long thresh;  // bounded: 2^64 mod m
   MTParams ga, gb;            // gamma: ga; beta: X ~ ga, Y ~ gb
+  double ep[4];               // output transform parameters
+  int epi;                    // output transform (Epi), 0 for the base distributions
+  int pad;
 };
 
 struct FillArgs {
@@ -118,7 +134,9 @@ struct TileGeom;
 TileGeom batch_geom(int cls, int cvar);
 int launch_fill(const FillArgs& a, int grid, void* stream);
 int launch_tails(const FillArgs& a, void* stream);
-int launch_beta_pairs(const double* g, double* out, unsigned long long m, void* stream);
+// Pairwise outputs from 2m base variates g: mode 0 beta X/(X+Y), 1 F
+// (X/p0)/(Y/p1), 2 skew normal p0 + p1 (p2 |u0| + p3 u1).
+int launch_pairs(const double* g, double* out, unsigned long long m, int mode, const double* p, void* stream);
 // gradients (rp_grad.cu)
 int grad_blocks();
 int launch_gamma_grad(const double* z, const double* g, size_t n, double alpha, double* dz, double* part, double* out,
@@ -148,7 +166,7 @@ int launch_mvn_grads(int d, unsigned long long n, const double* G, const double*
 // Tile geometry and resources of a (engine, dist) kernel.
 struct TileGeom { int nt, c, tile_words, smem_bytes; };
 TileGeom tile_geom(int engine, int dist);
-int occupancy_blocks(int engine, int dist);   // resident CTAs per SM
+int occupancy_blocks(int engine, int dist, int epi);   // resident CTAs per SM
 // One-time upload of ziggurat tables into device constant/global memory.
 int upload_tables();
 

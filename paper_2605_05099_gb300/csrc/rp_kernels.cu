@@ -86,18 +86,27 @@ int launch_tails(const FillArgs& a, void* stream) {
 }
 
 // Beta(a, a) from consecutive Gamma(a) draws: out[j] = X / (X + Y) with
-// X = g[2j], Y = g[2j+1] (the serial definition draws X then Y from the same
-// stream, so with equal shapes they are consecutive gamma variates).
-__global__ void k_beta_pairs(const double* __restrict__ g, double* __restrict__ out, u64 m) {
+// Outputs from consecutive pairs of base variates, u0 = g[2j], u1 = g[2j+1]
+// (the serial definitions draw them in this order from one stream):
+//   mode 0  beta with equal shapes, X / (X + Y);
+//   mode 1  F with equal degrees of freedom, (X / p0) / (Y / p1);
+//   mode 2  skew normal, p0 + p1 (p2 |u0| + p3 u1), p2 = delta, p3 = sqrt(1 - delta^2).
+__global__ void k_pairs(const double* __restrict__ g, double* __restrict__ out, u64 m, int mode, double p0,
+                        double p1, double p2, double p3) {
   for (u64 j = blockIdx.x * (u64)blockDim.x + threadIdx.x; j < m; j += (u64)gridDim.x * blockDim.x) {
-    double2 xy = reinterpret_cast<const double2*>(g)[j];
-    out[j] = __ddiv_rn(xy.x, __dadd_rn(xy.x, xy.y));
+    const double2 xy = reinterpret_cast<const double2*>(g)[j];
+    double v;
+    if (mode == 0) v = __ddiv_rn(xy.x, __dadd_rn(xy.x, xy.y));
+    else if (mode == 1) v = __ddiv_rn(__ddiv_rn(xy.x, p0), __ddiv_rn(xy.y, p1));
+    else v = __dadd_rn(p0, __dmul_rn(p1, __dadd_rn(__dmul_rn(p2, fabs(xy.x)), __dmul_rn(p3, xy.y))));
+    out[j] = v;
   }
 }
 
-int launch_beta_pairs(const double* g, double* out, unsigned long long m, void* stream) {
+int launch_pairs(const double* g, double* out, unsigned long long m, int mode, const double* p, void* stream) {
   if (!m) return 0;
-  k_beta_pairs<<<608, 256, 0, (cudaStream_t)stream>>>(g, out, m);
+  const double q[4] = {p ? p[0] : 0.0, p ? p[1] : 0.0, p ? p[2] : 0.0, p ? p[3] : 0.0};
+  k_pairs<<<608, 256, 0, (cudaStream_t)stream>>>(g, out, m, mode, q[0], q[1], q[2], q[3]);
   return (int)cudaGetLastError();
 }
 
@@ -114,10 +123,11 @@ int launch_log_cr(const double* x, double* y, unsigned long long n, void* stream
   return (int)cudaGetLastError();
 }
 
-int occupancy_blocks(int engine, int dist) {
+int occupancy_blocks(int engine, int dist, int epi) {
   FillArgs a{};
   a.eng.engine = engine;
   a.dist = dist;
+  a.sp.epi = epi;
   int occ = 0;
   dispatch(a, 0, 0, &occ);
   return occ;

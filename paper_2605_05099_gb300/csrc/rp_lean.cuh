@@ -41,7 +41,9 @@ __device__ __forceinline__ double mul_rn_fma(u64 r, double w) {
 }
 
 // Normal ziggurat (Sec. 3.1): bits 0-7 strip, bit 8 sign, bits 9-60 r.
-struct LeanNormal {
+// kEpi: the base of a derived distribution, each value transformed as written.
+template <bool kEpi>
+struct LeanNormalT {
   static constexpr bool kSync = true;
   static constexpr int kWhich = 0;
   static constexpr int kKShift = 20;
@@ -54,9 +56,11 @@ struct LeanNormal {
     if (rh != kh) return rh < kh;
     return fast_exact(u, z);
   }
-  __device__ static __forceinline__ double value(u64 u, const LeanTab& tb, const SampArgs&) {
+  __device__ static __forceinline__ double value(u64 u, const LeanTab& tb, const SampArgs& a) {
     const double x = mul_rn_fma((u >> 9) & M52, tb.w[u & 0xff]);
-    return __longlong_as_double(__double_as_longlong(x) ^ (long long)((u >> 8 & 1) << 63));
+    const double v = __longlong_as_double(__double_as_longlong(x) ^ (long long)((u >> 8 & 1) << 63));
+    if constexpr (kEpi) return epi_apply(v, a);
+    else return v;
   }
   __device__ static __forceinline__ bool wedge(u64 u0, u64 u1, const ZigDev& z) {
     return wedge_nl<true>((u0 >> 9) & M52, (int)(u0 & 0xff), u1, z);
@@ -74,10 +78,14 @@ struct LeanNormal {
   }
 };
 
+using LeanNormal = LeanNormalT<false>;
+using LeanNormalE = LeanNormalT<true>;
+
 // Exponential ziggurat (Sec. 3.1): bits 0-7 strip, bits 8-60 r; the tail
 // takes one more word and always accepts, so every candidate is 1 or 2 words
 // and a sync window of 2 suffices.
-struct LeanExp {
+template <bool kEpi>
+struct LeanExpT {
   static constexpr bool kSync = true;
   static constexpr int kWhich = 1;
   static constexpr int kKShift = 21;
@@ -90,8 +98,10 @@ struct LeanExp {
     if (rh != kh) return rh < kh;
     return fast_exact(u, z);
   }
-  __device__ static __forceinline__ double value(u64 u, const LeanTab& tb, const SampArgs&) {
-    return mul_rn_fma((u >> 8) & M53, tb.w[u & 0xff]);
+  __device__ static __forceinline__ double value(u64 u, const LeanTab& tb, const SampArgs& a) {
+    const double v = mul_rn_fma((u >> 8) & M53, tb.w[u & 0xff]);
+    if constexpr (kEpi) return epi_apply(v, a);
+    else return v;
   }
   __device__ static __forceinline__ bool wedge(u64 u0, u64 u1, const ZigDev& z) {
     return wedge_nl<false>((u0 >> 8) & M53, (int)(u0 & 0xff), u1, z);
@@ -101,6 +111,9 @@ struct LeanExp {
     return fast(u, tb, z) ? 1 : 2;
   }
 };
+
+using LeanExp = LeanExpT<false>;
+using LeanExpE = LeanExpT<true>;
 
 // Lemire (Sec. 3.2): one word per attempt, no seams to synchronise.
 struct LeanBounded {

@@ -107,3 +107,23 @@ def test_batch_argument_errors_without_device(rp):
     p = ctypes.c_uint64(0)
     assert L.rp_fill_state(7, w, ctypes.byref(p), 3, 5, 0.0, 0.0, 0, ctypes.c_void_p(0x1000), None) == -3
     assert L.rp_substream_state(9, 99, 1, w, ctypes.byref(ctypes.c_int())) == -3
+
+
+def test_derived_argument_errors_without_device(rp):
+    """rp_fill_derived refuses bad parameters and unknown kinds before any
+    device work; its codes match the header's enum and the binding's table."""
+    import ctypes
+    import re
+    L = rp.lib()
+    p = ctypes.c_uint64(0)
+    q = (ctypes.c_double * 4)(1.0, 0.0, 0.0, 0.0)
+    assert L.rp_fill_derived(1, 1, 0, ctypes.byref(p), 1, q, 5, None, None) == -2      # unif with a > b
+    assert L.rp_fill_derived(1, 1, 0, ctypes.byref(p), 2, q, 5, None, None) == -2      # sigma = 0
+    assert L.rp_fill_derived(1, 1, 0, ctypes.byref(p), 99, q, 5, None, None) == -2     # unknown kind
+    assert L.rp_fill_derived(1, 1, 0, ctypes.byref(p), 1, None, 5, None, None) == -1   # no parameters
+    hdr = open(os.path.join(ROOT, "include", "rp.h")).read()
+    body = re.search(r"typedef enum \{([^}]*)\} rp_derived;", hdr).group(1)
+    codes = {m.group(1): int(m.group(2)) for m in re.finditer(r"RP_(\w+) = (\d+)", body)}
+    import oracle
+    for name, (kind, _) in rp.DERIVED.items():
+        assert codes[name.upper()] == kind and oracle.DERIVED[name][0] == kind, name
