@@ -238,7 +238,8 @@ def fill(g, dist, n, *params, with_start=False):
 DERIVED = {"unif": (1, ("a", "b")), "normal_ms": (2, ("mu", "sigma")), "lognormal": (3, ("mu", "sigma")),
            "exp_scale": (4, ("beta",)), "gamma_scale": (5, ("alpha", "theta")), "chi2": (6, ("nu",)),
            "gumbel": (7, ("mu", "beta")), "pareto": (8, ("x_m", "alpha")), "weibull": (9, ("k", "lambda")),
-           "gpd": (10, ("mu", "sigma", "xi")), "f": (11, ("nu1", "nu2")), "skew_normal": (12, ("mu", "sigma", "alpha"))}
+           "gpd": (10, ("mu", "sigma", "xi")), "f": (11, ("nu1", "nu2")), "skew_normal": (12, ("mu", "sigma", "alpha")),
+           "t": (13, ("nu",))}
 
 
 def fill_derived(g, name, n, *params, with_start=False):

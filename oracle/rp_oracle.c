@@ -729,7 +729,8 @@ int or_fill_beta(or_gen* g, size_t n, double a, double b, double* out, uint64_t*
  * F = (X / nu1) / (Y / nu2) with X ~ Gamma(nu1 / 2) drawn before
  * Y ~ Gamma(nu2 / 2); skew normal (Azzalini's representation) from two
  * consecutive normals u0, u1: z = delta |u0| + sqrt(1 - delta^2) u1,
- * delta = alpha / sqrt(1 + alpha^2), x = mu + sigma z. */
+ * delta = alpha / sqrt(1 + alpha^2), x = mu + sigma z; Student t =
+ * Z / sqrt(V / nu) with Z ~ N(0, 1) drawn before V ~ chi2_nu. */
 
 /* pow(x, y) for x > 0, correctly rounded: exp(y log x) in double-double */
 double or_cr_pow(double x, double y) {
@@ -799,6 +800,18 @@ int or_fill_derived(or_gen* g, int kind, size_t n, const double* p, double* out,
         double X = gamma_one(g, a, ka, start ? start + i : NULL);
         double Y = gamma_one(g, b, kb, NULL);
         out[i] = (X / p[0]) / (Y / p[1]);
+      }
+      return 0;
+    }
+    case OR_D_T: {
+      /* Z / sqrt(V / nu), Z ~ N(0, 1) drawn before V ~ chi2_nu = 2 Gamma(nu / 2) */
+      double a = 0.5 * p[0];
+      if (!(a > 0.0)) return -1;
+      mt_consts k = mt_setup(a >= 1.0 ? a : a + 1.0);
+      for (size_t i = 0; i < n; ++i) {
+        double z = normal_one(g, start ? start + i : NULL);
+        double v = 2.0 * gamma_one(g, a, k, NULL);
+        out[i] = z / sqrt(v / p[0]);
       }
       return 0;
     }

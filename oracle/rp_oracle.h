@@ -84,10 +84,10 @@ int  or_fill_beta(or_gen* g, size_t n, double a, double b, double* out, uint64_t
 /* derived distributions (Table "continuous"): kinds and parameters p[]
  *   UNIF (a, b), NORMAL_MS (mu, sigma), LOGNORMAL (mu, sigma), EXP_SCALE (beta),
  *   GAMMA_SCALE (alpha, theta), CHI2 (nu), GUMBEL (mu, beta), PARETO (x_m, alpha),
- *   WEIBULL (k, lambda), GPD (mu, sigma, xi), F (nu1, nu2), SKEW_NORMAL (mu, sigma, alpha) */
+ *   WEIBULL (k, lambda), GPD (mu, sigma, xi), F (nu1, nu2), SKEW_NORMAL (mu, sigma, alpha), T (nu) */
 enum { OR_D_UNIF = 1, OR_D_NORMAL_MS = 2, OR_D_LOGNORMAL = 3, OR_D_EXP_SCALE = 4, OR_D_GAMMA_SCALE = 5,
        OR_D_CHI2 = 6, OR_D_GUMBEL = 7, OR_D_PARETO = 8, OR_D_WEIBULL = 9, OR_D_GPD = 10, OR_D_F = 11,
-       OR_D_SKEW_NORMAL = 12 };
+       OR_D_SKEW_NORMAL = 12, OR_D_T = 13 };
 int  or_fill_derived(or_gen* g, int kind, size_t n, const double* p, double* out, uint64_t* start);
 double or_cr_pow(double x, double y);
 /* ziggurat internals for tests */

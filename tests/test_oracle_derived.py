@@ -37,6 +37,9 @@ def _fill(orc, name, *params, seed=7, n=N, engine="xoshiro256pp"):
     ("f", (3.0, 3.0), stats.f(3.0, 3.0)),
     ("skew_normal", (1.0, 2.0, 4.0), stats.skewnorm(a=4.0, loc=1.0, scale=2.0)),
     ("skew_normal", (0.0, 1.0, -2.0), stats.skewnorm(a=-2.0)),
+    ("t", (3.0,), stats.t(3.0)),
+    ("t", (0.8,), stats.t(0.8)),
+    ("t", (1.0,), stats.cauchy()),
 ], ids=lambda x: str(x) if not hasattr(x, "dist") else x.dist.name)
 def test_derived_against_law(orc, name, params, law):
     x = _fill(orc, name, *params)
@@ -124,3 +127,13 @@ def test_bad_parameters_are_refused(orc):
         orc.fill_derived(g, "chi2", 4, -1.0)
     with pytest.raises(ValueError):
         orc.fill_derived(g, "f", 4, 2.0, 0.0)
+
+
+def test_t_draws_the_normal_first(orc):
+    """With nu huge, V / nu -> 1 and t -> Z: the first output follows the
+    first normal of the stream (Z is drawn before V)."""
+    t = _fill(orc, "t", 1e10, seed=29, n=1)
+    z = orc.fill(orc.gen("xoshiro256pp", 29), "normal", 1)
+    assert abs(t[0] - z[0]) <= 1e-4 * abs(z[0])
+    big = _fill(orc, "t", 1e8, seed=31)
+    assert stats.kstest(big, "norm").pvalue > P_MIN
