@@ -335,7 +335,7 @@ def run_extras(rp, stream):
     """The other workloads, each timed after one untimed run: config 1 (2^20
     words then 2^20 uniforms, xoshiro seed 12345), gamma/beta at n = 2^26
     with their pathwise gradients (xoshiro seed 7, upstream g ~ N(0,1)), the
-    batched substream workload (4096 requests, autotuned graph plan, against
+    derived distributions at n = 2^26, the batched substream workload (4096 requests, autotuned graph plan, against
     per-request launches) and the multivariate normal (d = 64, 512; n = 2^20)."""
     import numpy as np
     import torch
@@ -378,6 +378,17 @@ def run_extras(rp, stream):
     ex["gamma_beta_fill"] = {"unit": "variates/s", "n": n, **{k: round(v) for k, v in fwd.items()}}
     ex["gamma_beta_grads"] = {"unit": "grads/s (per-sample dz/dtheta and the reduced sum)", "n": n,
                               **{k: round(v) for k, v in grads.items()}}
+    # derived distributions (Table "continuous"), fused output transforms of
+    # the base fills; xoshiro seed 7, n = 2^26
+    dv = {}
+    for name, par in (("unif", (-2.0, 3.0)), ("normal_ms", (1.5, 2.0)), ("lognormal", (0.3, 0.7)),
+                      ("exp_scale", (2.5,)), ("gamma_scale", (2.5, 0.5)), ("chi2", (5.0,)), ("gumbel", (1.0, 2.0)),
+                      ("pareto", (2.0, 3.0)), ("weibull", (1.7, 2.0)), ("gpd", (0.5, 1.5, 0.3)), ("f", (5.0, 7.0)),
+                      ("skew_normal", (1.0, 2.0, 4.0))):
+        f = lambda: rp.rp_fill_derived("xoshiro256pp", 7, rp.NO_STREAM, 0, name, par, z, stream)
+        f()
+        dv[f"{name}{par}"] = round(n / (_ev_ms(stream, f) / 1e3))
+    ex["derived_fill"] = {"unit": "variates/s", "n": n, **dv}
     del z, g, dz, dz2
     torch.cuda.empty_cache()
     # batched substreams (config 4)

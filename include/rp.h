@@ -127,6 +127,8 @@ rp_status rp_fill_beta(rp_engine engine, uint64_t seed, uint64_t stream, uint64_
  *   RP_SKEW_NORMAL  (mu, sigma, alpha)  two consecutive normals u0, u1:
  *                                   mu + sigma (delta |u0| + sqrt(1 - delta^2) u1),
  *                                   delta = alpha / sqrt(1 + alpha^2)
+ *   RP_T            (nu)            Z / sqrt(V / nu), Z ~ N(0, 1) drawn before
+ *                                   V ~ chi2_nu = 2 Gamma(nu / 2)
  * params: 4 doubles (unused ones ignored), host memory.  Scale and shape
  * parameters must be positive and finite, locations finite; otherwise
  * RP_ERR_PARAM before any device work.  exp and pow are CUDA's (one and two
@@ -134,7 +136,7 @@ rp_status rp_fill_beta(rp_engine engine, uint64_t seed, uint64_t stream, uint64_
  * are exact as in the base fills.  *pos advances by the base words used. */
 typedef enum {
   RP_UNIF = 1, RP_NORMAL_MS = 2, RP_LOGNORMAL = 3, RP_EXP_SCALE = 4, RP_GAMMA_SCALE = 5, RP_CHI2 = 6,
-  RP_GUMBEL = 7, RP_PARETO = 8, RP_WEIBULL = 9, RP_GPD = 10, RP_F = 11, RP_SKEW_NORMAL = 12
+  RP_GUMBEL = 7, RP_PARETO = 8, RP_WEIBULL = 9, RP_GPD = 10, RP_F = 11, RP_SKEW_NORMAL = 12, RP_T = 13
 } rp_derived;
 rp_status rp_fill_derived(rp_engine engine, uint64_t seed, uint64_t stream, uint64_t* pos, rp_derived kind,
                           const double* params, size_t n, double* d_out, void* cuda_stream);

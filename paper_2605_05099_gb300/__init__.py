@@ -168,7 +168,8 @@ def rp_fill_beta(engine, seed, stream, pos, a, b, out, cuda_stream=None):
 DERIVED = {"unif": (1, ("a", "b")), "normal_ms": (2, ("mu", "sigma")), "lognormal": (3, ("mu", "sigma")),
            "exp_scale": (4, ("beta",)), "gamma_scale": (5, ("alpha", "theta")), "chi2": (6, ("nu",)),
            "gumbel": (7, ("mu", "beta")), "pareto": (8, ("x_m", "alpha")), "weibull": (9, ("k", "lambda")),
-           "gpd": (10, ("mu", "sigma", "xi")), "f": (11, ("nu1", "nu2")), "skew_normal": (12, ("mu", "sigma", "alpha"))}
+           "gpd": (10, ("mu", "sigma", "xi")), "f": (11, ("nu1", "nu2")), "skew_normal": (12, ("mu", "sigma", "alpha")),
+           "t": (13, ("nu",))}
 
 
 def rp_fill_derived(engine, seed, stream, pos, name, params, out, cuda_stream=None):

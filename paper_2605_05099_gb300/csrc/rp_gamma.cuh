@@ -175,6 +175,36 @@ struct GammaMach {
   }
 };
 
+// One standard normal by the ziggurat, fed word by word: feed() returns 1
+// when a normal is accepted; its record is (xk, xa, xb) as in GammaMach.
+struct NormalMach {
+  int ns;   // 0 idle, 1 wedge waiting for U, 2 tail waiting for U1, 3 tail waiting for U2
+  int xk;
+  u64 nu0, nw1, xa, xb;
+  __device__ __forceinline__ void reset() { ns = 0; }
+  __device__ __forceinline__ bool idle() const { return ns == 0; }
+  __device__ __forceinline__ int feed(u64 u, const ZigDev& z) {
+    if (ns == 0) {
+      const int i = (int)(u & 0xff);
+      if (((u >> 9) & ((1ull << 52) - 1)) < z.k[i]) { xk = 1; xa = u; return 1; }
+      nu0 = u;
+      ns = i ? 1 : 2;
+      return 0;
+    }
+    if (ns == 1) {
+      ns = 0;
+      if (!wedge_accept<true>((nu0 >> 9) & ((1ull << 52) - 1), (int)(nu0 & 0xff), u, z)) return 0;
+      xk = 1; xa = nu0;
+      return 1;
+    }
+    if (ns == 2) { nw1 = u; ns = 3; return 0; }
+    if (!tail_pair_accept(nw1, u, z)) { ns = 2; return 0; }
+    ns = 0;
+    xk = 2; xa = nu0; xb = nw1;
+    return 1;
+  }
+};
+
 // Record words of a variate: r[0] = kinds (xk | yk << 8), r[1..3] = X (xa,
 // xb, ub), r[4..6] = Y (beta only).
 struct SampGamma {
@@ -229,5 +259,42 @@ struct SampBeta {
     double Y = gamma_value((int)((r[0] >> 8) & 0xff), r[4], r[5], r[6], a.gb, z);
     if (a.epi == EPI_F) return __ddiv_rn(__ddiv_rn(X, a.ep[0]), __ddiv_rn(Y, a.ep[1]));   // F(nu1, nu2)
     return __ddiv_rn(X, __dadd_rn(X, Y));
+  }
+};
+
+// Student t (Table "continuous": the normal-gamma mixture Z / sqrt(V / nu)),
+// Z ~ N(0, 1) drawn before V ~ chi2_nu = 2 Gamma(nu / 2) from the same
+// stream.  Record: r[0] = kinds (Z | V << 8), r[1..2] = Z (xa, xb), r[4..6]
+// = the gamma record of V.  ep[0] = nu.
+struct SampT {
+  static constexpr bool kBeta = true;   // two sub-variates per output
+  struct M {
+    NormalMach nm;
+    GammaMach g;
+    int ph;        // 0 drawing Z, 1 drawing V
+    __device__ __forceinline__ void reset() { nm.reset(); g.reset(); ph = 0; }
+    __device__ __forceinline__ bool idle() const { return ph == 0 && nm.idle(); }
+    __device__ __forceinline__ int feed(u64 u, const SampArgs& a, const ZigDev& z) {
+      if (ph == 0) {
+        if (nm.feed(u, z)) ph = 1;
+        return 0;
+      }
+      if (!g.feed(u, a.ga, z)) return 0;
+      ph = 0;
+      return 1;
+    }
+    __device__ __forceinline__ void record(u64* r) const {
+      r[0] = (u64)nm.xk | ((u64)g.xk << 8);
+      r[1] = nm.xa; r[2] = nm.xb; r[3] = 0;
+      r[4] = g.xa; r[5] = g.xb; r[6] = g.ub;
+    }
+  };
+  __device__ static __forceinline__ bool needs_tail(const u64* r) {
+    return (r[0] & 0xff) == 2 || ((r[0] >> 8) & 0xff) == 2;
+  }
+  __device__ static __forceinline__ double value(const u64* r, const SampArgs& a, const ZigDev& z) {
+    const double Z = normal_x_exact((int)(r[0] & 0xff), r[1], r[2], z);
+    const double V = __dmul_rn(2.0, gamma_value((int)((r[0] >> 8) & 0xff), r[4], r[5], r[6], a.ga, z));
+    return __ddiv_rn(Z, __dsqrt_rn(__ddiv_rn(V, a.ep[0])));
   }
 };

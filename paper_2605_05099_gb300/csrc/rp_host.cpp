@@ -495,6 +495,7 @@ double words_per_variate(int dist, const rp::SampArgs& sp) {
     case rp::D_EXP: return 1.036;
     case rp::D_GAMMA: return gamma_wpv(sp.ga);
     case rp::D_BETA: return gamma_wpv(sp.ga) + gamma_wpv(sp.gb);
+    case rp::D_T: return 1.0235 + gamma_wpv(sp.ga);
     default: return 1.0;
   }
 }
@@ -577,7 +578,8 @@ rp_status run_fill_state_locked(int engine, const u64 s_in[4], u64* pos, size_t 
     a.out = (char*)d_out + done * esz;
     if (!trivial || one_pass_check) {
       e = ensure_scratch(tiles);
-      const bool queued = dist == rp::D_NORMAL || dist == rp::D_EXP || dist == rp::D_GAMMA || dist == rp::D_BETA;
+      const bool queued = dist == rp::D_NORMAL || dist == rp::D_EXP || dist == rp::D_GAMMA || dist == rp::D_BETA ||
+                          dist == rp::D_T;
       if (!e && queued) e = ensure_tailq(left / 256 + 4096);
       if (!e && dist == rp::D_BOUNDED) e = ensure_park((size_t)(grid * T));
       if (e) return fail(RP_ERR_NOMEM, std::string("scratch allocation: ") + cudaGetErrorString((cudaError_t)e));
@@ -806,6 +808,10 @@ rp_status rp_fill_derived(rp_engine engine, uint64_t seed, uint64_t stream, uint
       const double q[4] = {p0, p1, 0.0, 0.0};
       return pairs_fill(engine, seed, stream, (u64*)pos, n, rp::D_GAMMA, sg, 1, q, d_out, cuda_stream);
     }
+    case RP_T:
+      if (!positive(p0)) return fail(RP_ERR_PARAM, "t degrees of freedom must be positive");
+      dist = rp::D_T; sp.ga = mt_params(0.5 * p0); sp.ep[0] = p0;
+      break;
     case RP_SKEW_NORMAL: {
       if (!finite(p0) || !positive(p1) || !finite(p2)) return fail(RP_ERR_PARAM, "skew normal needs finite mu, alpha and sigma > 0");
       const double delta = p2 / std::sqrt(1.0 + p2 * p2);

@@ -81,6 +81,7 @@ int launch_tails(const FillArgs& a, void* stream) {
   else if (a.dist == D_EXP) k_tails<SampExp><<<304, 256, 0, s>>>(a);
   else if (a.dist == D_GAMMA) k_tails_rec<SampGamma><<<304, 256, 0, s>>>(a);
   else if (a.dist == D_BETA) k_tails_rec<SampBeta><<<304, 256, 0, s>>>(a);
+  else if (a.dist == D_T) k_tails_rec<SampT><<<304, 256, 0, s>>>(a);
   else return 0;
   return (int)cudaGetLastError();
 }
@@ -135,7 +136,7 @@ int occupancy_blocks(int engine, int dist, int epi) {
 
 TileGeom tile_geom(int engine, int dist) {
   (void)engine;
-  if (dist == D_GAMMA || dist == D_BETA) return TileGeom{NTM_, CM_, NTM_ * CM_, 0};
+  if (dist == D_GAMMA || dist == D_BETA || dist == D_T) return TileGeom{NTM_, CM_, NTM_ * CM_, 0};
   if (dist == D_BOUNDED) return TileGeom{NT_, CR_, NT_ * CR_, 0};
   return TileGeom{NT_, C_, NT_ * C_, 0};
 }

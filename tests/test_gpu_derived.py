@@ -3,8 +3,8 @@ C ABI against the oracle, element by element, with the consumed words.
 
 Bars, from the arithmetic:
 - shift and scale (unif, normal(mu, sigma), Exp(beta), Gamma(alpha >= 1,
-  theta), chi2 with nu >= 2, F with both nu >= 2, skew normal) and Gumbel
-  (correctly rounded logs on both sides): bit-exact;
+  theta), chi2 with nu >= 2, F with both nu >= 2, skew normal), Student t
+  with nu >= 2 and Gumbel (correctly rounded logs on both sides): bit-exact;
 - a CUDA exp or pow in the transform: within 1 ulp (lognormal), 2 ulp
   (Pareto: exp, then a product) and 3 ulp (Weibull: pow, then a product);
 - the gamma boost for shapes below 1 (libm exp): within 4 ulp;
@@ -48,6 +48,8 @@ CASES = [
     ("f", (1.0, 4.0), 4),
     ("skew_normal", (1.0, 2.0, 4.0), "skew"),
     ("skew_normal", (0.0, 1.0, -2.0), "skew"),
+    ("t", (3.0,), 0),
+    ("t", (1.5,), 4),
 ]
 
 
@@ -119,7 +121,7 @@ def test_derived_parity(name, params, tol):
 
 
 @pytest.mark.parametrize("engine", ["pcg64dxsm", "philox4x32_10"])
-@pytest.mark.parametrize("name,params,tol", [c for c in CASES if c[0] in ("unif", "lognormal", "pareto", "chi2", "f", "skew_normal")][:7],
+@pytest.mark.parametrize("name,params,tol", [c for c in CASES if c[0] in ("unif", "lognormal", "pareto", "chi2", "f", "t")][:8],
                          ids=lambda x: str(x))
 def test_derived_parity_engines(engine, name, params, tol):
     check(name, params, tol, engine=engine, seed=2024, pos=12345)
