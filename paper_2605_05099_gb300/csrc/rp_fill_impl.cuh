@@ -130,6 +130,13 @@ __device__ __noinline__ double epi_apply(double x, const SampArgs& a) {
   }
 }
 
+// Shift and scale inline; the transcendental transforms out of line.
+__device__ __forceinline__ double epi_value(double x, const SampArgs& a) {
+  if (a.epi == EPI_AFFINE) return __dadd_rn(a.ep[0], __dmul_rn(a.ep[1], x));
+  if (a.epi == EPI_SCALE) return __dmul_rn(a.ep[0], x);
+  return epi_apply(x, a);
+}
+
 #include "rp_gamma.cuh"
 
 // ------------------------------------------------------------------ samplers
@@ -151,7 +158,7 @@ struct SampUniformE {
   static constexpr bool kOnePerWord = true;
   static constexpr bool kCheckReject = false;
   typedef double out_t;
-  __device__ static __forceinline__ double value1(u64 u, const SampArgs& a) { return epi_apply(u53_bits(u), a); }
+  __device__ static __forceinline__ double value1(u64 u, const SampArgs& a) { return epi_value(u53_bits(u), a); }
 };
 
 // Lemire with no rejection assumed: word p gives output p, hi(u m); every
@@ -631,7 +638,7 @@ __global__ void k_tails(FillArgs a) {
   for (unsigned long long i = blockIdx.x * (u64)blockDim.x + threadIdx.x; i < n; i += (u64)gridDim.x * blockDim.x) {
     TailEntry te = a.tailq[i];
     double v = S::tail_value(te.w0, te.w1, z);
-    if (a.sp.epi) v = epi_apply(v, a.sp);
+    if (a.sp.epi) v = epi_value(v, a.sp);
     out[te.g] = (OT)v;
   }
 }

@@ -222,7 +222,7 @@ struct SampGamma {
   __device__ static __forceinline__ bool needs_tail(const u64* r) { return (r[0] & 0xff) == 2; }
   __device__ static __forceinline__ double value(const u64* r, const SampArgs& a, const ZigDev& z) {
     const double g = gamma_value((int)(r[0] & 0xff), r[1], r[2], r[3], a.ga, z);
-    return a.epi ? epi_apply(g, a) : g;   // Gamma(alpha, theta), chi2
+    return a.epi ? epi_value(g, a) : g;   // Gamma(alpha, theta), chi2
   }
 };
 

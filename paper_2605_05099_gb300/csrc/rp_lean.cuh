@@ -59,7 +59,7 @@ struct LeanNormalT {
   __device__ static __forceinline__ double value(u64 u, const LeanTab& tb, const SampArgs& a) {
     const double x = mul_rn_fma((u >> 9) & M52, tb.w[u & 0xff]);
     const double v = __longlong_as_double(__double_as_longlong(x) ^ (long long)((u >> 8 & 1) << 63));
-    if constexpr (kEpi) return epi_apply(v, a);
+    if constexpr (kEpi) return epi_value(v, a);
     else return v;
   }
   __device__ static __forceinline__ bool wedge(u64 u0, u64 u1, const ZigDev& z) {
@@ -100,7 +100,7 @@ struct LeanExpT {
   }
   __device__ static __forceinline__ double value(u64 u, const LeanTab& tb, const SampArgs& a) {
     const double v = mul_rn_fma((u >> 8) & M53, tb.w[u & 0xff]);
-    if constexpr (kEpi) return epi_apply(v, a);
+    if constexpr (kEpi) return epi_value(v, a);
     else return v;
   }
   __device__ static __forceinline__ bool wedge(u64 u0, u64 u1, const ZigDev& z) {
