@@ -22,8 +22,9 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SO = os.path.join(_HERE, "liboracle.so")
 
-XOSHIRO256PP, PCG64DXSM, PHILOX4X32_10 = 1, 2, 3
-ENGINES = {"xoshiro256pp": XOSHIRO256PP, "pcg64dxsm": PCG64DXSM, "philox4x32_10": PHILOX4X32_10}
+XOSHIRO256PP, PCG64DXSM, PHILOX4X32_10, PHILOX4X64_10 = 1, 2, 3, 4
+ENGINES = {"xoshiro256pp": XOSHIRO256PP, "pcg64dxsm": PCG64DXSM, "philox4x32_10": PHILOX4X32_10,
+           "philox4x64_10": PHILOX4X64_10}
 
 
 def build(force=False):
@@ -45,7 +46,7 @@ def build(force=False):
 class Gen(ctypes.Structure):
     _fields_ = [("engine", ctypes.c_int), ("s", ctypes.c_uint64 * 4), ("pos", ctypes.c_uint64),
                 ("blk_idx", ctypes.c_uint64), ("blk_valid", ctypes.c_int),
-                ("blk", ctypes.c_uint64 * 2)]
+                ("blk", ctypes.c_uint64 * 4)]
 
 
 _lib = None
@@ -72,6 +73,8 @@ def lib():
             "or_xoshiro_charpoly": (None, [vp]),
             "or_pcg_advance": (None, [vp, u64, u64]),
             "or_philox4x32_10": (None, [vp, vp, vp]),
+            "or_philox4x64_10": (None, [vp, vp, vp]),
+            "or_fill_uniform52": (None, [P(Gen), sz, vp]),
             "or_cr_exp": (dbl, [dbl]),
             "or_cr_log": (dbl, [dbl]),
             "or_cr_ambiguous": (u64, []),
@@ -187,6 +190,14 @@ def pcg_advance(state4, delta):
     return [int(x) for x in s]
 
 
+def philox4x64(ctr4, key2):
+    c = np.array(ctr4, np.uint64)
+    k = np.array(key2, np.uint64)
+    o = np.empty(4, np.uint64)
+    lib().or_philox4x64_10(_ptr(c), _ptr(k), _ptr(o))
+    return [int(x) for x in o]
+
+
 def philox(ctr4, key2):
     c = np.array(ctr4, np.uint32)
     k = np.array(key2, np.uint32)
@@ -210,6 +221,11 @@ def fill(g, dist, n, *params, with_start=False):
     elif dist == "uniform":
         out = np.empty(n, np.float64)
         L.or_fill_uniform(gp, n, _ptr(out))
+        if with_start:
+            start[:] = np.arange(n, dtype=np.uint64) + np.uint64(g.pos - n)
+    elif dist == "uniform52":
+        out = np.empty(n, np.float64)
+        L.or_fill_uniform52(gp, n, _ptr(out))
         if with_start:
             start[:] = np.arange(n, dtype=np.uint64) + np.uint64(g.pos - n)
     elif dist == "bounded":

@@ -180,11 +180,52 @@ static uint64_t philox_word(or_gen* g, uint64_t p) {
   return g->blk[p & 1];
 }
 
+/* Philox4x64-10 (the paper's Philox; Salmon, Moraes, Dror & Shaw 2011):
+ * ten rounds of two 64x64->128 multiplies with a Weyl-sequence key
+ * schedule; a block gives four 64-bit words. */
+#define PHILOX64_M0 0xD2E7470EE14C6C93ull
+#define PHILOX64_M1 0xCA5A826395121157ull
+#define PHILOX64_W0 0x9E3779B97F4A7C15ull
+#define PHILOX64_W1 0xBB67AE8584CAA73Bull
+
+void or_philox4x64_10(const uint64_t ctr[4], const uint64_t key[2], uint64_t out[4]) {
+  uint64_t x0 = ctr[0], x1 = ctr[1], x2 = ctr[2], x3 = ctr[3];
+  uint64_t k0 = key[0], k1 = key[1];
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) { k0 += PHILOX64_W0; k1 += PHILOX64_W1; }
+    u128 p0 = (u128)PHILOX64_M0 * x0;
+    u128 p1 = (u128)PHILOX64_M1 * x2;
+    uint64_t y0 = (uint64_t)(p1 >> 64) ^ x1 ^ k0;
+    uint64_t y1 = (uint64_t)p1;
+    uint64_t y2 = (uint64_t)(p0 >> 64) ^ x3 ^ k1;
+    uint64_t y3 = (uint64_t)p0;
+    x0 = y0; x1 = y1; x2 = y2; x3 = y3;
+  }
+  out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
+}
+
+/* Word p of a Philox4x64 stream = word p mod 4 of block (counter + 1 +
+ * p / 4): the counter is incremented before each block, as NumPy's Philox
+ * does (the seeded counter itself is never a block). */
+static uint64_t philox64_word(or_gen* g, uint64_t p) {
+  uint64_t b = p >> 2;
+  if (!g->blk_valid || g->blk_idx != b) {
+    u128 c = (((u128)g->s[1] << 64) | g->s[0]) + (u128)b + 1u;
+    uint64_t ctr[4] = {(uint64_t)c, (uint64_t)(c >> 64), 0, 0};
+    uint64_t key[2] = {g->s[2], g->s[3]};
+    or_philox4x64_10(ctr, key, g->blk);
+    g->blk_idx = b;
+    g->blk_valid = 1;
+  }
+  return g->blk[p & 3];
+}
+
 uint64_t or_next(or_gen* g) {
   uint64_t w;
   switch (g->engine) {
     case OR_XOSHIRO256PP: w = xoshiro_next(g->s); break;
     case OR_PCG64DXSM: w = pcg_next(g->s); break;
+    case OR_PHILOX4X64_10: w = philox64_word(g, g->pos); break;
     default: w = philox_word(g, g->pos); break;
   }
   g->pos++;
@@ -221,6 +262,13 @@ int or_gen_seed(or_gen* g, int engine, uint64_t seed, int has_key, uint64_t key)
     pcg_put(g->s, st);
     g->s[2] = (uint64_t)(inc >> 64);
     g->s[3] = (uint64_t)inc;
+  } else if (engine == OR_PHILOX4X64_10) {
+    /* NumPy's Philox seeding: key = two words of the seed sequence, counter 0 */
+    seed_words64(seed, has_key, key, w, 2);
+    g->s[0] = 0;
+    g->s[1] = 0;
+    g->s[2] = w[0];
+    g->s[3] = w[1];
   } else {
     /* Philox: every state word is seeded (Table "stream-select": counter +
      * key).  Reading for 4x32: w0 = counter low, w1 = counter high, w2 = key. */
@@ -385,6 +433,8 @@ void or_substream(or_gen* g, int engine, uint64_t base_seed, uint64_t s) {
     if (s) or_xoshiro_jump_poly(g->s, nl, 3);
   } else if (engine == OR_PHILOX4X32_10) {
     g->s[2] = s;  /* key := s (stream setter) */
+  } else if (engine == OR_PHILOX4X64_10) {
+    g->s[2] = s;  /* key word 0 := s (stream setter); key word 1 stays seeded */
   } else {
     /* PCG64: stream selector = increment; inc := 2 s + 1 */
     g->s[2] = (uint64_t)((((u128)s << 1) | 1u) >> 64);
@@ -535,6 +585,18 @@ void or_fill_u64(or_gen* g, size_t n, uint64_t* out) {
 
 void or_fill_uniform(or_gen* g, size_t n, double* out) {
   for (size_t i = 0; i < n; ++i) out[i] = u53(or_next(g));
+}
+
+/* 52-bit uniform, the paper's default (Sec. 3.1, method 2): the word's top
+ * 52 bits as the fraction of a double in [1, 2), minus 1; exactly
+ * floor(u / 2^12) 2^-52. */
+void or_fill_uniform52(or_gen* g, size_t n, double* out) {
+  for (size_t i = 0; i < n; ++i) {
+    uint64_t bits = (or_next(g) >> 12) | 0x3ff0000000000000ull;
+    double x;
+    memcpy(&x, &bits, 8);
+    out[i] = x - 1.0;
+  }
 }
 
 /* Bounded integers in [0, m) by Lemire's multiply-and-reject (Sec. 3.2):

@@ -20,18 +20,20 @@
 extern "C" {
 #endif
 
-enum { OR_XOSHIRO256PP = 1, OR_PCG64DXSM = 2, OR_PHILOX4X32_10 = 3 };
+enum { OR_XOSHIRO256PP = 1, OR_PCG64DXSM = 2, OR_PHILOX4X32_10 = 3, OR_PHILOX4X64_10 = 4 };
 
 typedef struct {
   int engine;
   /* xoshiro256++: s[0..3].
    * PCG64-DXSM:   s[0]=state hi, s[1]=state lo, s[2]=inc hi, s[3]=inc lo.
    * Philox4x32-10: s[0]=counter lo 64, s[1]=counter hi 64,
-   *                s[2]=key (k0 = low 32 bits, k1 = high 32 bits). */
+   *                s[2]=key (k0 = low 32 bits, k1 = high 32 bits).
+   * Philox4x64-10: s[0]=counter lo 64, s[1]=counter hi 64 (counter words
+   *                2, 3 are zero), s[2]=k0, s[3]=k1. */
   uint64_t s[4];
   uint64_t pos;          /* words consumed since the seeded state */
   /* Philox block cache (block index relative to the seeded counter) */
-  uint64_t blk_idx; int blk_valid; uint64_t blk[2];
+  uint64_t blk_idx; int blk_valid; uint64_t blk[4];
 } or_gen;
 
 /* ---- seeding (Sec. 2.3; seed_seq_fe128-style mixer, NumPy SeedSequence
@@ -61,6 +63,8 @@ void or_xoshiro_charpoly(uint64_t p[5]);         /* degree-256 polynomial, bit k
 void or_pcg_advance(uint64_t s[4], uint64_t d_hi, uint64_t d_lo);
 /* Philox4x32-10 bijection: ctr[4], key[2] -> out[4] */
 void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+void or_philox4x64_10(const uint64_t ctr[4], const uint64_t key[2], uint64_t out[4]);
+void or_fill_uniform52(or_gen* g, size_t n, double* out);
 
 /* ---- correctly rounded elementary functions used in accept tests
  *      (double-double evaluation, rounded once).  Sec. 4.2. ---- */

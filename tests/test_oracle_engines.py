@@ -165,3 +165,47 @@ def test_philox_structure(orc):
     outs = np.array([orc.philox([i, 0, 0, 0], [5, 6]) for i in range(4096)], np.uint32)
     bits = np.unpackbits(outs.view(np.uint8)).mean()
     assert abs(bits - 0.5) < 6 * 0.5 / np.sqrt(outs.size * 32)
+
+
+# ------------------------------------------------------------------ Philox4x64-10
+def test_philox4x64_matches_numpy(orc):
+    """The paper's Philox (4x64-10) with NumPy's Philox seeding and counter
+    convention: key = two SeedSequence words, counter 0, incremented before
+    each block; every word equals numpy.random.Philox's random_raw."""
+    for seed, key in ((2024, None), (7, 0), (99, 5), (2 ** 63 + 11, 123456789)):
+        g = orc.gen("philox4x64_10", seed, key)
+        ss = np.random.SeedSequence(seed) if key is None else np.random.SeedSequence(seed, spawn_key=(key,))
+        ref = np.random.Philox(ss).random_raw(40_001)
+        assert np.array_equal(orc.next_words(g, 40_001), ref), (seed, key)
+
+
+def test_philox4x64_block_function(orc):
+    """Word p is word p mod 4 of the block at counter + 1 + p/4 (a 128-bit
+    counter, carry into the second word), through the bijection itself."""
+    g = orc.gen("philox4x64_10", 31)
+    key = [int(g.s[2]), int(g.s[3])]
+    w = orc.next_words(g, 4 * 20)
+    for b in range(20):
+        assert [int(x) for x in w[4 * b:4 * b + 4]] == orc.philox4x64([b + 1, 0, 0, 0], key)
+    assert orc.philox4x64([2 ** 64 - 1, 0, 0, 0], [1, 2]) != orc.philox4x64([0, 1, 0, 0], [1, 2])
+
+
+def test_philox4x64_seek_and_substreams(orc):
+    g = orc.gen("philox4x64_10", 31337)
+    w = orc.next_words(g, 3000)
+    for p in (0, 1, 3, 4, 5, 777, 2999):
+        h = orc.gen("philox4x64_10", 31337, pos=p)
+        assert int(orc.next_words(h, 1)[0]) == int(w[p]), p
+    base = orc.state_words(orc.gen("philox4x64_10", 99))
+    for s in (0, 1, 4095):
+        st = orc.state_words(orc.substream("philox4x64_10", 99, s))
+        assert st == [0, 0, s, base[3]], s
+
+
+def test_uniform52_closed_form(orc):
+    """Sec. 3.1 method 2 (the paper's default): the word's top 52 bits in the
+    fraction of a double in [1, 2), minus 1, is exactly floor(u/2^12) 2^-52."""
+    w = orc.next_words(orc.gen("philox4x64_10", 5), 1 << 16)
+    u = orc.fill(orc.gen("philox4x64_10", 5), "uniform52", 1 << 16)
+    assert np.array_equal((u * 2.0 ** 52).astype(np.uint64), w >> np.uint64(12))
+    assert u.min() >= 0.0 and u.max() < 1.0
