@@ -335,7 +335,8 @@ def run_extras(rp, stream):
     """The other workloads, each timed after one untimed run: config 1 (2^20
     words then 2^20 uniforms, xoshiro seed 12345), gamma/beta at n = 2^26
     with their pathwise gradients (xoshiro seed 7, upstream g ~ N(0,1)), the
-    derived distributions at n = 2^26, the batched substream workload (4096 requests, autotuned graph plan, against
+    derived distributions at n = 2^26, the paper's Philox4x64-10 fills at
+    n = 2^28, the batched substream workload (4096 requests, autotuned graph plan, against
     per-request launches) and the multivariate normal (d = 64, 512; n = 2^20)."""
     import numpy as np
     import torch
@@ -390,6 +391,22 @@ def run_extras(rp, stream):
         dv[f"{name}{par}"] = round(n / (_ev_ms(stream, f) / 1e3))
     ex["derived_fill"] = {"unit": "variates/s", "n": n, **dv}
     del z, g, dz, dz2
+    torch.cuda.empty_cache()
+    # the paper's own Philox (4x64-10) and its default 52-bit uniform, n = 2^28
+    n28 = 1 << 28
+    of = torch.empty(n28, dtype=torch.float64, device="cuda")
+    ph = {}
+    for key, f in (("uniform52", lambda: rp.rp_fill_uniform52("philox4x64_10", SEED, rp.NO_STREAM, 0, of, stream)),
+                   ("normal", lambda: rp.rp_fill_normal("philox4x64_10", SEED, rp.NO_STREAM, 0, of, stream)),
+                   ("exp", lambda: rp.rp_fill_exp("philox4x64_10", SEED, rp.NO_STREAM, 0, of, stream)),
+                   ("bounded:6", lambda: rp.rp_fill_bounded("philox4x64_10", SEED, rp.NO_STREAM, 0, 6, of.view(torch.uint64), stream)),
+                   ("bounded:9223372036854775809",
+                    lambda: rp.rp_fill_bounded("philox4x64_10", SEED, rp.NO_STREAM, 0, 2 ** 63 + 1, of.view(torch.uint64), stream))):
+        f()
+        ms = _ev_ms(stream, f)
+        ph[key] = {"ms": round(ms, 4), "variates_per_s": round(n28 / (ms / 1e3))}
+    ex["philox4x64_10_fills"] = {"n": n28, **ph}
+    del of
     torch.cuda.empty_cache()
     # batched substreams (config 4)
     reqs = inputs.batch_workload()

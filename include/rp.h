@@ -42,7 +42,8 @@ extern "C" {
 typedef enum {
   RP_XOSHIRO256PP = 1,   /* Blackman & Vigna 2019, 4 x 64-bit state */
   RP_PCG64DXSM = 2,      /* O'Neill 2019, 128-bit LCG + DXSM output */
-  RP_PHILOX4X32_10 = 3   /* Salmon et al. 2011, 128-bit counter, 64-bit key */
+  RP_PHILOX4X32_10 = 3,  /* Salmon et al. 2011, 128-bit counter, 64-bit key */
+  RP_PHILOX4X64_10 = 4   /* the paper's Philox: 4 x 64-bit words per block, NumPy's Philox seeding */
 } rp_engine;
 
 typedef int rp_status;
@@ -77,6 +78,12 @@ rp_status rp_fill_u64(rp_engine engine, uint64_t seed, uint64_t stream, uint64_t
  * method 1), one word per variate, bit-exact. */
 rp_status rp_fill_uniform(rp_engine engine, uint64_t seed, uint64_t stream, uint64_t* pos,
                           size_t n, double* d_out, void* cuda_stream);
+
+/* 52-bit uniform in [0, 1), the paper's default (Sec. 3.1, method 2): the
+ * word's top 52 bits in the fraction of a double in [1, 2), minus 1, which
+ * is exactly floor(u / 2^12) 2^-52.  One word per variate. */
+rp_status rp_fill_uniform52(rp_engine engine, uint64_t seed, uint64_t stream, uint64_t* pos,
+                            size_t n, double* d_out, void* cuda_stream);
 
 /* Unbiased integers in [0, m) by Lemire's multiply-and-reject (Sec. 3.2):
  * one word per attempt, reject while low64(u m) < 2^64 mod m, output

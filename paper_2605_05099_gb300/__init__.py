@@ -13,9 +13,10 @@ import os
 
 import torch
 
-XOSHIRO256PP, PCG64DXSM, PHILOX4X32_10 = 1, 2, 3
+XOSHIRO256PP, PCG64DXSM, PHILOX4X32_10, PHILOX4X64_10 = 1, 2, 3, 4
 DISTS = {"u64": 0, "uniform": 1, "bounded": 2, "normal": 3, "exp": 4, "gamma": 5, "beta": 6}
-ENGINES = {"xoshiro256pp": XOSHIRO256PP, "pcg64dxsm": PCG64DXSM, "philox4x32_10": PHILOX4X32_10}
+ENGINES = {"xoshiro256pp": XOSHIRO256PP, "pcg64dxsm": PCG64DXSM, "philox4x32_10": PHILOX4X32_10,
+           "philox4x64_10": PHILOX4X64_10}
 NO_STREAM = (1 << 64) - 1
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -53,6 +54,7 @@ def lib():
         sig = {
             "rp_fill_u64": [i32, u64, u64, pu64, sz, vp, vp],
             "rp_fill_uniform": [i32, u64, u64, pu64, sz, vp, vp],
+            "rp_fill_uniform52": [i32, u64, u64, pu64, sz, vp, vp],
             "rp_fill_bounded": [i32, u64, u64, pu64, sz, u64, vp, vp],
             "rp_fill_normal": [i32, u64, u64, pu64, sz, vp, vp],
             "rp_fill_normal_philox_static": [u64, u64, pu64, sz, vp, vp],
@@ -128,6 +130,10 @@ def rp_fill_u64(engine, seed, stream, pos, out, cuda_stream=None):
 
 def rp_fill_uniform(engine, seed, stream, pos, out, cuda_stream=None):
     return _fill(lib().rp_fill_uniform, engine, seed, stream, pos, out, torch.float64, cuda_stream=cuda_stream)
+
+
+def rp_fill_uniform52(engine, seed, stream, pos, out, cuda_stream=None):
+    return _fill(lib().rp_fill_uniform52, engine, seed, stream, pos, out, torch.float64, cuda_stream=cuda_stream)
 
 
 def rp_fill_bounded(engine, seed, stream, pos, m, out, cuda_stream=None):

@@ -292,7 +292,7 @@ struct XoshiroDev {
   // state is the critical path either way); kLeanCtas resident CTAs per SM
   // for the bitmap kernel.
   static constexpr int kStep = 1, kLeanCtas = 4;
-  __device__ __forceinline__ void next_step(u64 (&u)[2]) { u[0] = next(); }
+  __device__ __forceinline__ void next_step(u64 (&u)[kStep]) { u[0] = next(); }
   __device__ void init(const EngineArgs& a, u64 off) {
     s0 = a.s[0]; s1 = a.s[1]; s2 = a.s[2]; s3 = a.s[3];
     const ulonglong4_32a* tab = (const ulonglong4_32a*)a.gf2_pow;
@@ -355,7 +355,7 @@ struct PcgDev {
     return hi;
   }
   static constexpr int kStep = 1, kLeanCtas = 5;
-  __device__ __forceinline__ void next_step(u64 (&u)[2]) { u[0] = next(); }
+  __device__ __forceinline__ void next_step(u64 (&u)[kStep]) { u[0] = next(); }
   __device__ void init(const EngineArgs& a, u64 off) {
     st = ((u128)a.s[0] << 64) | a.s[1];
     inc = ((u128)a.s[2] << 64) | a.s[3];
@@ -416,7 +416,7 @@ struct PhiloxDev {
   // unknown at compile time.  Odd phase: the pending word and the low half
   // of the next block, whose high half becomes pending.
   static constexpr int kStep = 2, kLeanCtas = 5;
-  __device__ __forceinline__ void next_step(u64 (&u)[2]) {
+  __device__ __forceinline__ void next_step(u64 (&u)[kStep]) {
     const bool odd = (idx & 1) != 0;
     u64 w0, w1;
     block((idx + 1) >> 1, w0, w1);
@@ -439,6 +439,65 @@ struct PhiloxDev {
     u64 start = idx;  // callers advance a saved chunk-start copy
     idx = start + a.stride;
     if (idx & 1) { u64 w0; block(idx >> 1, w0, buf); }
+  }
+};
+
+// Philox4x64-10 (Salmon, Moraes, Dror & Shaw 2011; the paper's Philox): ten
+// rounds of two 64 x 64 -> 128 products with a Weyl key schedule; word p is
+// word p mod 4 of the block at counter + 1 + p / 4 (the counter is
+// incremented before each block).  State: 128-bit counter (c_lo, c_hi), key
+// (k0, k1).  The unrolled loops take four words per step, one block: the
+// word index's phase within a block is the same for every thread of a fill
+// but unknown at compile time, so the held block and the new one are
+// combined by selects.
+struct Philox64Dev {
+  u64 c_lo, c_hi, k0, k1;
+  u64 idx;              // next word index relative to the seeded counter
+  u64 b0, b1, b2, b3;   // the block that holds word idx - 1 (when idx % 4 != 0)
+  __device__ __forceinline__ void block(u64 b, u64& w0, u64& w1, u64& w2, u64& w3) const {
+    const u128 c = (((u128)c_hi << 64) | c_lo) + (u128)b + 1u;
+    u64 x0 = (u64)c, x1 = (u64)(c >> 64), x2 = 0, x3 = 0;
+    u64 ka = k0, kb = k1;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+      const u64 h0 = __umul64hi(0xD2E7470EE14C6C93ull, x0), l0 = 0xD2E7470EE14C6C93ull * x0;
+      const u64 h1 = __umul64hi(0xCA5A826395121157ull, x2), l1 = 0xCA5A826395121157ull * x2;
+      const u64 y0 = h1 ^ x1 ^ ka, y2 = h0 ^ x3 ^ kb;
+      x0 = y0; x1 = l1; x2 = y2; x3 = l0;
+      ka += 0x9E3779B97F4A7C15ull; kb += 0xBB67AE8584CAA73Bull;
+    }
+    w0 = x0; w1 = x1; w2 = x2; w3 = x3;
+  }
+  __device__ __forceinline__ u64 next() {
+    const int q = (int)(idx & 3);
+    if (q == 0) block(idx >> 2, b0, b1, b2, b3);
+    const u64 r = q == 0 ? b0 : q == 1 ? b1 : q == 2 ? b2 : b3;
+    ++idx;
+    return r;
+  }
+  static constexpr int kStep = 4, kLeanCtas = 5;
+  __device__ __forceinline__ void next_step(u64 (&u)[kStep]) {
+    const int q = (int)(idx & 3);
+    u64 n0, n1, n2, n3;
+    block((idx + 3) >> 2, n0, n1, n2, n3);   // phase 0: this block; else the next one
+    // words idx .. idx + 3: positions q .. 3 of the held block, then 0 .. q - 1 of the new one
+    u[0] = q == 0 ? n0 : q == 1 ? b1 : q == 2 ? b2 : b3;
+    u[1] = q == 0 ? n1 : q == 1 ? b2 : q == 2 ? b3 : n0;
+    u[2] = q == 0 ? n2 : q == 1 ? b3 : q == 2 ? n0 : n1;
+    u[3] = q == 0 ? n3 : q == 1 ? n0 : q == 2 ? n1 : n2;
+    b0 = n0; b1 = n1; b2 = n2; b3 = n3;
+    idx += 4;
+  }
+  __device__ void init(const EngineArgs& a, u64 off) {
+    c_lo = a.s[0]; c_hi = a.s[1];
+    k0 = a.s[2]; k1 = a.s[3];
+    idx = a.word0 + off;
+    if (idx & 3) block(idx >> 2, b0, b1, b2, b3);
+  }
+  __device__ void init_tile(const EngineArgs& a, unsigned c, int t, u64*) { init(a, (u64)c * a.tile_words + (u64)t * a.chunk_words); }
+  __device__ __forceinline__ void advance(const EngineArgs& a) {
+    idx += a.stride;   // callers advance a saved chunk-start copy
+    if (idx & 3) block(idx >> 2, b0, b1, b2, b3);
   }
 };
 

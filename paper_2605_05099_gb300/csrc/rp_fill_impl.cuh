@@ -105,6 +105,19 @@ __device__ __forceinline__ bool tail_pair_accept(u64 w1, u64 w2, const ZigDev& z
   return __dadd_rn(b, b) > __dmul_rn(a, a);
 }
 
+// W consecutive words from the engine, in steps of its width (W a multiple).
+template <class E, int W>
+__device__ __forceinline__ void take_words(E& g, u64 (&u)[W]) {
+  static_assert(W % E::kStep == 0, "whole engine steps");
+#pragma unroll
+  for (int i = 0; i < W; i += E::kStep) {
+    u64 t[E::kStep];
+    g.next_step(t);
+#pragma unroll
+    for (int k = 0; k < E::kStep; ++k) u[i + k] = t[k];
+  }
+}
+
 // ------------------------------------------------------------------ derived distributions
 // Output transform of a base variate x (Table "continuous"; Sec. 3.1 "Gamma
 // and related", "Extreme value and Weibull"): one IEEE operation per step,
@@ -152,6 +165,16 @@ struct SampUniform {
   static constexpr bool kCheckReject = false;
   typedef double out_t;
   __device__ static __forceinline__ double value1(u64 u, const SampArgs&) { return u53_bits(u); }
+};
+// 52-bit uniform, the paper's default (Sec. 3.1, method 2): the word's top
+// 52 bits as the fraction of a double in [1, 2), minus 1 (exact).
+struct SampUniform52 {
+  static constexpr bool kOnePerWord = true;
+  static constexpr bool kCheckReject = false;
+  typedef double out_t;
+  __device__ static __forceinline__ double value1(u64 u, const SampArgs&) {
+    return __dsub_rn(__longlong_as_double((long long)((u >> 12) | 0x3ff0000000000000ull)), 1.0);
+  }
 };
 // Uniform base of a derived distribution (unif, Gumbel).
 struct SampUniformE {
@@ -369,16 +392,22 @@ __device__ __forceinline__ void onepw_tile(const FillArgs& a, u64 k, const E& e,
   const u64 wbase = k * (u64)T + (u64)(t - lane) * C;   // lane 0's chunk: row r goes to wbase + r C
   u64* row = stage_w + lane * kRowW;
   for (int j0 = 0; j0 < C; j0 += kStage) {
+    constexpr int W = E::kStep > 2 ? E::kStep : 2;   // words per step, in pairs
 #pragma unroll
-    for (int j = 0; j < kStage; j += 2) {
-      u64 u[2];
-      g.next_step(u);
-      if constexpr (E::kStep == 1) u[1] = g.next();
-      const u64 u0 = u[0], u1 = u[1];
-      *reinterpret_cast<ulonglong2*>(row + j) = make_ulonglong2(as_bits(S::value1(u0, a.sp)), as_bits(S::value1(u1, a.sp)));
-      if constexpr (S::kCheckReject) {
-        if (u0 * a.sp.m < a.sp.thresh && base + j0 + j < a.n) atomicMin(&a.ctrl->first_reject, base + j0 + j);
-        if (u1 * a.sp.m < a.sp.thresh && base + j0 + j + 1 < a.n) atomicMin(&a.ctrl->first_reject, base + j0 + j + 1);
+    for (int j = 0; j < kStage; j += W) {
+      u64 u[W];
+      take_words<E, W>(g, u);
+#pragma unroll
+      for (int i = 0; i < W; i += 2) {
+        *reinterpret_cast<ulonglong2*>(row + j + i) =
+            make_ulonglong2(as_bits(S::value1(u[i], a.sp)), as_bits(S::value1(u[i + 1], a.sp)));
+        if constexpr (S::kCheckReject) {
+#pragma unroll
+          for (int k = 0; k < 2; ++k) {
+            const u64 p = base + j0 + j + i + k;
+            if (u[i + k] * a.sp.m < a.sp.thresh && p < a.n) atomicMin(&a.ctrl->first_reject, p);
+          }
+        }
       }
     }
     __syncwarp();
@@ -719,6 +748,7 @@ int dispatch_dist(const FillArgs& a, int grid, cudaStream_t s, int* occ) {
     case D_UNIFORM: return a.sp.epi ? launch_es<E, SampUniformE>(a, grid, s, occ) : launch_es<E, SampUniform>(a, grid, s, occ);
     case D_BOUNDED: return launch_rej<E>(a, grid, s, occ);
     case D_BOUNDED_ONE: return launch_es<E, SampBoundedOne>(a, grid, s, occ);
+    case D_UNIFORM52: return launch_es<E, SampUniform52>(a, grid, s, occ);
     case D_NORMAL: return a.sp.epi ? launch_lean<E, LeanNormalE>(a, grid, s, occ) : launch_lean<E, LeanNormal>(a, grid, s, occ);
     case D_EXP: return a.sp.epi ? launch_lean<E, LeanExpE>(a, grid, s, occ) : launch_lean<E, LeanExp>(a, grid, s, occ);
     case D_GAMMA: return launch_merge<E, SampGamma>(a, grid, s, occ);

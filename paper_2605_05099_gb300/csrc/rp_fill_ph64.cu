@@ -1,0 +1,5 @@
+// Philox64Dev instantiations of the fill kernels (one translation unit per
+// engine keeps the build parallel).
+#include "rp_fill_impl.cuh"
+
+RP_ENGINE_TU(ph64, Philox64Dev)

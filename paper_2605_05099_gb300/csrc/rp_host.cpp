@@ -315,6 +315,10 @@ int pcg_device_pow(u64** out) {
 }
 
 // ---------------------------------------------------------------- engine states
+// Counter-based engines address words directly: a fill starts at a word
+// offset instead of jumping its state.
+bool counter_engine(int engine) { return engine == RP_PHILOX4X32_10 || engine == RP_PHILOX4X64_10; }
+
 constexpr u128 kPcgMult128 = ((u128)0x2360ED051FC65DA4ull << 64) | 0x4385DF649FCCF645ull;
 
 rp_status seed_state(int engine, u64 seed, u64 stream, u64 s[4]) {
@@ -333,6 +337,10 @@ rp_status seed_state(int engine, u64 seed, u64 stream, u64 s[4]) {
   } else if (engine == RP_PHILOX4X32_10) {
     seed_words(seed, stream, w, 3);
     s[0] = w[0]; s[1] = w[1]; s[2] = w[2]; s[3] = 0;
+  } else if (engine == RP_PHILOX4X64_10) {
+    // NumPy's Philox seeding: key = two seed-sequence words, counter 0
+    seed_words(seed, stream, w, 2);
+    s[0] = 0; s[1] = 0; s[2] = w[0]; s[3] = w[1];
   } else {
     return fail(RP_ERR_ENGINE, "unknown engine id " + std::to_string(engine));
   }
@@ -348,9 +356,10 @@ void jump_state(int engine, u64 s[4], u128 delta) {
     st = a.A * st + a.G * inc;
     s[0] = (u64)(st >> 64); s[1] = (u64)st;
   } else {
-    u128 c = (((u128)s[1] << 64) | s[0]) + delta / 2;
-    // an odd delta cannot be expressed in the state words of a block engine;
+    // blocks of two (Philox4x32) or four (Philox4x64) words: a delta that is
+    // not a whole number of blocks cannot be expressed in the state words;
     // callers use the word offset instead (rp_fill_* take pos)
+    u128 c = (((u128)s[1] << 64) | s[0]) + delta / (engine == RP_PHILOX4X64_10 ? 4 : 2);
     s[0] = (u64)c; s[1] = (u64)(c >> 64);
   }
 }
@@ -533,7 +542,7 @@ rp_status run_fill_state_locked(int engine, const u64 s_in[4], u64* pos, size_t 
   auto key = std::make_pair(engine, dist | (sp.epi ? 256 : 0));   // transformed fills run other kernels
   if (!g_occ.count(key)) g_occ[key] = rp::occupancy_blocks(engine, dist, sp.epi);
   int occ = g_occ[key] > 0 ? g_occ[key] : 1;
-  const bool trivial = (dist == rp::D_U64 || dist == rp::D_UNIFORM || dist == rp::D_BOUNDED_ONE);
+  const bool trivial = (dist == rp::D_U64 || dist == rp::D_UNIFORM || dist == rp::D_BOUNDED_ONE || dist == rp::D_UNIFORM52);
   const bool one_pass_check = dist == rp::D_BOUNDED_ONE;
 
   u64 cur = *pos;
@@ -550,7 +559,7 @@ rp_status run_fill_state_locked(int engine, const u64 s_in[4], u64* pos, size_t 
     u64 s0[4];
     memcpy(s0, s, sizeof(s0));
     a.eng.word0 = 0;
-    if (engine == RP_PHILOX4X32_10) {
+    if (counter_engine(engine)) {
       a.eng.word0 = cur;
     } else {
       jump_state(engine, s0, (u128)cur);
@@ -642,7 +651,7 @@ rp_status check_fill_args(int engine, u64* pos, size_t n, void* d_out) {
   if (n == 0) return RP_OK;
   if (!d_out) return fail(RP_ERR_NULL, "output pointer is NULL");
   if ((uintptr_t)d_out & 7) return fail(RP_ERR_PARAM, "output pointer must be 8-byte aligned");
-  if (engine < 1 || engine > 3) return fail(RP_ERR_ENGINE, "unknown engine id " + std::to_string(engine));
+  if (engine < 1 || engine > 4) return fail(RP_ERR_ENGINE, "unknown engine id " + std::to_string(engine));
   return RP_OK;
 }
 
@@ -700,6 +709,12 @@ rp_status rp_fill_uniform(rp_engine engine, uint64_t seed, uint64_t stream, uint
                           void* cuda_stream) {
   rp::SampArgs sp{};
   return run_fill(engine, seed, stream, (u64*)pos, n, rp::D_UNIFORM, sp, d_out, cuda_stream);
+}
+
+rp_status rp_fill_uniform52(rp_engine engine, uint64_t seed, uint64_t stream, uint64_t* pos, size_t n, double* d_out,
+                            void* cuda_stream) {
+  rp::SampArgs sp{};
+  return run_fill(engine, seed, stream, (u64*)pos, n, rp::D_UNIFORM52, sp, d_out, cuda_stream);
 }
 
 rp_status rp_fill_bounded(rp_engine engine, uint64_t seed, uint64_t stream, uint64_t* pos, size_t n, uint64_t m,
@@ -899,10 +914,11 @@ rp_status rp_seed_state(rp_engine engine, uint64_t seed, uint64_t stream, uint64
 
 rp_status rp_jump_state(rp_engine engine, uint64_t* words, uint64_t delta_hi, uint64_t delta_lo) {
   if (!words) return fail(RP_ERR_NULL, "words is NULL");
-  if (engine < 1 || engine > 3) return fail(RP_ERR_ENGINE, "unknown engine id " + std::to_string((int)engine));
+  if (engine < 1 || engine > 4) return fail(RP_ERR_ENGINE, "unknown engine id " + std::to_string((int)engine));
   std::lock_guard<std::mutex> lk(g_mu);
   u128 d = ((u128)delta_hi << 64) | delta_lo;
-  if (engine == RP_PHILOX4X32_10 && (d & 1)) return fail(RP_ERR_PARAM, "Philox state jumps must be even (two words per block)");
+  if (engine == RP_PHILOX4X32_10 && (d & 1)) return fail(RP_ERR_PARAM, "Philox4x32 state jumps must be even (two words per block)");
+  if (engine == RP_PHILOX4X64_10 && (d & 3)) return fail(RP_ERR_PARAM, "Philox4x64 state jumps must be multiples of 4 (four words per block)");
   jump_state(engine, (u64*)words, d);
   return RP_OK;
 }
@@ -1116,8 +1132,8 @@ rp_status substream_words(int engine, u64 base_seed, u64 sidx, u64 w[4]) {
   if (engine == RP_XOSHIRO256PP) {
     const u64 limbs[3] = {0, 0, sidx};   // s * 2^128
     xo_jump_limbs(w, limbs, 3);
-  } else if (engine == RP_PHILOX4X32_10) {
-    w[2] = sidx;
+  } else if (engine == RP_PHILOX4X32_10 || engine == RP_PHILOX4X64_10) {
+    w[2] = sidx;   // (first) key word := s, the stream setter
   } else {
     const u128 inc = ((u128)sidx << 1) | 1u;
     w[2] = (u64)(inc >> 64);
@@ -1146,7 +1162,7 @@ extern "C" rp_status rp_fill_state(rp_engine engine, const uint64_t* words, uint
 
 extern "C" rp_status rp_substream_state(rp_engine engine, uint64_t base_seed, uint64_t s, uint64_t* words, int* nw) {
   if (!words || !nw) return fail(RP_ERR_NULL, "words/nw is NULL");
-  if (engine < 1 || engine > 3) return fail(RP_ERR_ENGINE, "unknown engine id " + std::to_string((int)engine));
+  if (engine < 1 || engine > 4) return fail(RP_ERR_ENGINE, "unknown engine id " + std::to_string((int)engine));
   std::lock_guard<std::mutex> lk(g_mu);
   u64 w[4] = {0, 0, 0, 0};
   rp_status st = substream_words(engine, base_seed, s, w);
@@ -1257,7 +1273,7 @@ rp_status batch_build(rp_batch_plan& P, int schedule, BatchBuild& B) {
     a.eng.engine = P.engine;
     u64 s0[4];
     memcpy(s0, P.sub[r].data(), sizeof(s0));
-    if (P.engine == RP_PHILOX4X32_10) a.eng.word0 = P.req[r].pos;
+    if (counter_engine(P.engine)) a.eng.word0 = P.req[r].pos;
     else jump_state(P.engine, s0, (u128)P.req[r].pos);
     memcpy(a.eng.s, s0, sizeof(s0));
     a.eng.gf2_pow = gpow;
@@ -1422,7 +1438,7 @@ extern "C" rp_status rp_batch_plan_create(const rp_request* reqs, size_t nreq, r
   if (!plan) return fail(RP_ERR_NULL, "plan is NULL");
   *plan = nullptr;
   if (nreq && !reqs) return fail(RP_ERR_NULL, "reqs is NULL");
-  if (engine < 1 || engine > 3) return fail(RP_ERR_ENGINE, "unknown engine id " + std::to_string((int)engine));
+  if (engine < 1 || engine > 4) return fail(RP_ERR_ENGINE, "unknown engine id " + std::to_string((int)engine));
   std::lock_guard<std::mutex> lk(g_mu);
   int e = ensure_zig();
   if (e) return cuda_fail(e, "ziggurat table upload");

@@ -445,7 +445,7 @@ __device__ bool lean_tile(const FillArgs& a, u64 k, const E& e, LeanSmem<NT, C>&
         unsigned mw = 0;
 #pragma unroll
         for (int j = 0; j < 32; j += E::kStep) {
-          u64 u[2];
+          u64 u[E::kStep];
           g.next_step(u);
 #pragma unroll
           for (int i = 0; i < E::kStep; ++i) mw |= (unsigned)(u[i] * a.sp.m >= a.sp.thresh) << (j + i);
@@ -464,7 +464,7 @@ __device__ bool lean_tile(const FillArgs& a, u64 k, const E& e, LeanSmem<NT, C>&
           unsigned F = 0;
 #pragma unroll
           for (int j = 0; j < 16; j += E::kStep) {
-            u64 u[2];
+            u64 u[E::kStep];
             g.next_step(u);
 #pragma unroll
             for (int i = 0; i < E::kStep; ++i) {
@@ -588,7 +588,7 @@ __device__ bool lean_tile(const FillArgs& a, u64 k, const E& e, LeanSmem<NT, C>&
           const unsigned m = sm.msk[hb >> 1][t] >> ((hb & 1) * 16);
 #pragma unroll 8 / E::kStep
           for (int j = 0; j < 16; j += E::kStep) {
-            u64 u[2];
+            u64 u[E::kStep];
             g2.next_step(u);
             // branch-free: every word's value lands in the next free slot
             // (ns <= j <= 15 < kRow), which advances only for marked words

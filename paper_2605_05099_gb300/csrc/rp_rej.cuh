@@ -51,7 +51,7 @@ __device__ bool rej_tile(const FillArgs& a, u64 k, const E& e, RejSmem<NT>& sm, 
     int ns = 0;
 #pragma unroll
     for (int j = 0; j < kStage; j += E::kStep) {
-      u64 u[2];
+      u64 u[E::kStep];
       g.next_step(u);
       // branch-free: every word's value lands in the next free slot (ns <= j
       // < kRow), which advances only for accepted words

@@ -6,7 +6,7 @@ import torch
 import oracle
 import paper_2605_05099_gb300 as rp
 
-DTYPE = {"u64": torch.uint64, "uniform": torch.float64, "bounded": torch.uint64, "normal": torch.float64,
+DTYPE = {"u64": torch.uint64, "uniform": torch.float64, "uniform52": torch.float64, "bounded": torch.uint64, "normal": torch.float64,
          "exp": torch.float64, "gamma": torch.float64, "beta": torch.float64}
 
 
@@ -17,6 +17,8 @@ def gpu_fill(dist, engine, seed, stream, pos, n, params=()):
         newpos = rp.rp_fill_u64(engine, seed, s, pos, out)
     elif dist == "uniform":
         newpos = rp.rp_fill_uniform(engine, seed, s, pos, out)
+    elif dist == "uniform52":
+        newpos = rp.rp_fill_uniform52(engine, seed, s, pos, out)
     elif dist == "bounded":
         newpos = rp.rp_fill_bounded(engine, seed, s, pos, params[0], out)
     elif dist == "normal":

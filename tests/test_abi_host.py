@@ -31,7 +31,7 @@ def test_exports_every_declared_symbol(rp):
         assert hasattr(L, s), s
 
 
-@pytest.mark.parametrize("engine", ["xoshiro256pp", "pcg64dxsm", "philox4x32_10"])
+@pytest.mark.parametrize("engine", ["xoshiro256pp", "pcg64dxsm", "philox4x32_10", "philox4x64_10"])
 def test_seed_state_matches_oracle(rp, orc, engine):
     rng = np.random.default_rng(5)
     for seed in [0, 1, 7, 99, 2024, 12345, 2 ** 40 + 3, 2 ** 64 - 1] + [int(x) for x in rng.integers(0, 2 ** 62, 20)]:
@@ -53,6 +53,11 @@ def test_jump_state_matches_oracle(rp, orc):
     j = rp.rp_jump_state("philox4x32_10", ph, 2 ** 65 + 10)
     c0, c1 = ph[0] | ph[1] << 64, j[0] | j[1] << 64
     assert c1 - c0 == 2 ** 64 + 5 and j[2] == ph[2]
+    q = rp.rp_seed_state("philox4x64_10", 3)
+    j = rp.rp_jump_state("philox4x64_10", q, 2 ** 66 + 12)   # four words per block
+    assert (j[0] | j[1] << 64) - (q[0] | q[1] << 64) == 2 ** 64 + 3 and j[2:] == q[2:]
+    with pytest.raises(rp.RPError):
+        rp.rp_jump_state("philox4x64_10", q, 6)
 
 
 def test_ziggurat_tables_match_oracle(rp, orc):
@@ -86,7 +91,7 @@ def test_argument_errors(rp):
     assert rp.rp_version().startswith("rp ")
 
 
-@pytest.mark.parametrize("engine", ["xoshiro256pp", "pcg64dxsm", "philox4x32_10"])
+@pytest.mark.parametrize("engine", ["xoshiro256pp", "pcg64dxsm", "philox4x32_10", "philox4x64_10"])
 def test_substream_state_matches_oracle(rp, orc, engine):
     """Substream s of a base seed (Sec. 2.3 recipe): library host code vs the
     oracle's independent construction (xoshiro: jump polynomial by s 2^128)."""
