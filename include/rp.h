@@ -313,6 +313,24 @@ const char* rp_version(void);
  * diagnostic counter for benchmarks). */
 uint64_t rp_kernel_launches(void);
 
+/* Checkpointing (Sec. 5, "Thread safety and checkpointing"): a stream's
+ * exact state -- engine, the state words before word 0 (as rp_seed_state,
+ * rp_substream_state and rp_fill_state use them) and the position -- as an
+ * opaque, self-checking buffer of RP_STATE_BYTES bytes, and back.  A fill
+ * resumed from a restored state continues the stream exactly.
+ *   rp_state_serialize    buf: RP_STATE_BYTES writable host bytes
+ *   rp_state_deserialize  refuses (RP_ERR_PARAM) a short buffer, a wrong
+ *                         magic or version, an unknown engine, a corrupted
+ *                         checksum or an all-zero xoshiro256++ state;
+ *                         words receives 4 words. */
+#define RP_STATE_BYTES 64
+rp_status rp_state_serialize(rp_engine engine, const uint64_t* words, uint64_t pos, uint8_t* buf, size_t buflen);
+rp_status rp_state_deserialize(const uint8_t* buf, size_t buflen, rp_engine* engine, uint64_t* words, uint64_t* pos);
+
+/* Engine query: the canonical identifier of engine id (1 ..), or NULL for
+ * an unknown id. */
+const char* rp_engine_name(int engine);
+
 /* Ziggurat tables used by the kernels (which: 0 normal, 1 exponential):
  * k[256], w[256], f[256] and R.  For inspection and tests. */
 rp_status rp_ziggurat_tables(int which, uint64_t* k, double* w, double* f, double* R);

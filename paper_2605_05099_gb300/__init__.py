@@ -88,6 +88,12 @@ def lib():
         L.rp_version.argtypes = []
         L.rp_kernel_launches.restype = ctypes.c_uint64
         L.rp_kernel_launches.argtypes = []
+        L.rp_state_serialize.restype = i32
+        L.rp_state_serialize.argtypes = [i32, pu64, u64, ctypes.c_char_p, sz]
+        L.rp_state_deserialize.restype = i32
+        L.rp_state_deserialize.argtypes = [ctypes.c_char_p, sz, ctypes.POINTER(i32), pu64, pu64]
+        L.rp_engine_name.restype = ctypes.c_char_p
+        L.rp_engine_name.argtypes = [i32]
         _lib = L
     return _lib
 
@@ -279,6 +285,32 @@ def rp_fill_state(engine, words, pos, dist, out, p0=0.0, p1=0.0, m=0, cuda_strea
     _check(lib().rp_fill_state(_engine(engine), w, ctypes.byref(cpos), d, n, float(p0), float(p1), int(m), p,
                                _stream_handle(cuda_stream)))
     return cpos.value
+
+
+STATE_BYTES = 64
+
+
+def rp_state_serialize(engine, words, pos):
+    """A stream's state (engine, state words before word 0, position) as the
+    library's opaque checkpoint bytes."""
+    w = (ctypes.c_uint64 * 4)(*[int(x) for x in list(words) + [0] * (4 - len(words))])
+    buf = ctypes.create_string_buffer(STATE_BYTES)
+    _check(lib().rp_state_serialize(_engine(engine), w, pos, buf, STATE_BYTES))
+    return buf.raw
+
+
+def rp_state_deserialize(data):
+    """(engine id, four state words, position) from checkpoint bytes."""
+    e = ctypes.c_int()
+    w = (ctypes.c_uint64 * 4)()
+    p = ctypes.c_uint64()
+    _check(lib().rp_state_deserialize(bytes(data), len(data), ctypes.byref(e), w, ctypes.byref(p)))
+    return e.value, [w[i] for i in range(4)], p.value
+
+
+def rp_engine_name(engine):
+    r = lib().rp_engine_name(int(engine))
+    return None if r is None else r.decode()
 
 
 def rp_substream_state(engine, base_seed, s):

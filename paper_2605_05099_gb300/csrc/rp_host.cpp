@@ -923,6 +923,67 @@ rp_status rp_jump_state(rp_engine engine, uint64_t* words, uint64_t delta_hi, ui
   return RP_OK;
 }
 
+// Checkpoint buffer: "RPST", version 1 (u16), engine (u16), four state
+// words, the position, eight zero bytes and an FNV-1a 64-bit checksum of
+// the first 56 bytes; every integer little-endian, written byte by byte.
+namespace {
+constexpr uint64_t kFnvOffset = 0xcbf29ce484222325ull, kFnvPrime = 0x100000001b3ull;
+uint64_t fnv1a(const uint8_t* p, size_t n) {
+  uint64_t h = kFnvOffset;
+  for (size_t i = 0; i < n; ++i) { h ^= p[i]; h *= kFnvPrime; }
+  return h;
+}
+void put_le(uint8_t* p, uint64_t v, int bytes) {
+  for (int i = 0; i < bytes; ++i) p[i] = (uint8_t)(v >> (8 * i));
+}
+uint64_t get_le(const uint8_t* p, int bytes) {
+  uint64_t v = 0;
+  for (int i = 0; i < bytes; ++i) v |= (uint64_t)p[i] << (8 * i);
+  return v;
+}
+}  // namespace
+
+rp_status rp_state_serialize(rp_engine engine, const uint64_t* words, uint64_t pos, uint8_t* buf, size_t buflen) {
+  if (!words || !buf) return fail(RP_ERR_NULL, "words/buf is NULL");
+  if (buflen < RP_STATE_BYTES) return fail(RP_ERR_PARAM, "state buffer shorter than RP_STATE_BYTES");
+  if (engine < 1 || engine > 4) return fail(RP_ERR_ENGINE, "unknown engine id " + std::to_string((int)engine));
+  memset(buf, 0, RP_STATE_BYTES);
+  memcpy(buf, "RPST", 4);
+  put_le(buf + 4, 1, 2);
+  put_le(buf + 6, (uint64_t)engine, 2);
+  for (int i = 0; i < 4; ++i) put_le(buf + 8 + 8 * i, words[i], 8);
+  put_le(buf + 40, pos, 8);
+  put_le(buf + 56, fnv1a(buf, 56), 8);
+  return RP_OK;
+}
+
+rp_status rp_state_deserialize(const uint8_t* buf, size_t buflen, rp_engine* engine, uint64_t* words, uint64_t* pos) {
+  if (!buf || !engine || !words || !pos) return fail(RP_ERR_NULL, "a pointer is NULL");
+  if (buflen < RP_STATE_BYTES) return fail(RP_ERR_PARAM, "state buffer shorter than RP_STATE_BYTES");
+  if (memcmp(buf, "RPST", 4) != 0 || get_le(buf + 4, 2) != 1) return fail(RP_ERR_PARAM, "not a version-1 state buffer");
+  if (get_le(buf + 56, 8) != fnv1a(buf, 56)) return fail(RP_ERR_PARAM, "state buffer checksum mismatch");
+  if (get_le(buf + 48, 8) != 0) return fail(RP_ERR_PARAM, "state buffer reserved bytes are not zero");
+  const uint64_t e = get_le(buf + 6, 2);
+  if (e < 1 || e > 4) return fail(RP_ERR_PARAM, "state buffer names an unknown engine");
+  uint64_t w[4];
+  for (int i = 0; i < 4; ++i) w[i] = get_le(buf + 8 + 8 * i, 8);
+  if (e == RP_XOSHIRO256PP && (w[0] | w[1] | w[2] | w[3]) == 0) return fail(RP_ERR_PARAM, "all-zero xoshiro256++ state");
+  *engine = (rp_engine)e;
+  memcpy(words, w, sizeof(w));
+  *pos = get_le(buf + 40, 8);
+  return RP_OK;
+}
+
+const char* rp_engine_name(int engine) {
+  switch (engine) {
+    case RP_XOSHIRO256PP: return "xoshiro256pp";
+    case RP_PCG64DXSM: return "pcg64dxsm";
+    case RP_PHILOX4X32_10: return "philox4x32_10";
+    case RP_PHILOX4X64_10: return "philox4x64_10";
+    default: return nullptr;
+  }
+}
+
 rp_status rp_ziggurat_tables(int which, uint64_t* k, double* w, double* f, double* R) {
   if (!k || !w || !f || !R) return fail(RP_ERR_NULL, "NULL table pointer");
   if (which != 0 && which != 1) return fail(RP_ERR_PARAM, "which must be 0 (normal) or 1 (exponential)");

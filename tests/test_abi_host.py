@@ -132,3 +132,25 @@ def test_derived_argument_errors_without_device(rp):
     import oracle
     for name, (kind, _) in rp.DERIVED.items():
         assert codes[name.upper()] == kind and oracle.DERIVED[name][0] == kind, name
+
+
+@pytest.mark.parametrize("engine", ["xoshiro256pp", "pcg64dxsm", "philox4x32_10", "philox4x64_10"])
+def test_state_checkpoint_round_trip(rp, orc, engine):
+    """A serialised state (Sec. 5 checkpointing) restores exactly, and any
+    single corrupted byte, a short buffer or an unknown engine is refused."""
+    words = rp.rp_seed_state(engine, 2024, 3)
+    for pos in (0, 1, 2 ** 40 + 7, 2 ** 64 - 1):
+        buf = rp.rp_state_serialize(engine, words, pos)
+        assert len(buf) == rp.STATE_BYTES
+        e, w, p = rp.rp_state_deserialize(buf)
+        assert e == rp.ENGINES[engine] and w[:len(words)] == words and p == pos
+        for i in range(rp.STATE_BYTES):
+            bad = bytearray(buf)
+            bad[i] ^= 0x10
+            with pytest.raises(rp.RPError):
+                rp.rp_state_deserialize(bytes(bad))
+    with pytest.raises(rp.RPError):
+        rp.rp_state_deserialize(buf[:-1])
+    with pytest.raises(rp.RPError):
+        rp.rp_state_serialize(9, words, 0)
+    assert rp.rp_engine_name(rp.ENGINES[engine]) == engine and rp.rp_engine_name(0) is None

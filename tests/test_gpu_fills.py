@@ -233,3 +233,18 @@ def test_output_offsets(engine):
             assert p == opos
             assert np.array_equal(host[off:off + n], o.view(np.uint64)), (dist, engine, off)
             assert host[off + n] == 0 and (off == 0 or host[0] == 0)   # nothing written outside
+
+
+@pytest.mark.parametrize("engine", ENGINES)
+def test_checkpoint_resume_continues_the_stream(engine):
+    """Fill, checkpoint the state through the serialised buffer, restore it
+    and fill on: the two parts equal one uninterrupted fill (and the oracle)."""
+    words = rp.rp_seed_state(engine, 77, rp.NO_STREAM)
+    a = torch.empty(12_345, dtype=torch.float64, device="cuda")
+    p1 = rp.rp_fill_state(engine, words, 0, "normal", a)
+    e, w, p = rp.rp_state_deserialize(rp.rp_state_serialize(engine, words, p1))
+    b = torch.empty(54_321, dtype=torch.float64, device="cuda")
+    p2 = rp.rp_fill_state(e, w, p, "normal", b)
+    c, p3 = gpu_fill("normal", engine, 77, None, 0, 12_345 + 54_321)
+    torch.cuda.synchronize()
+    assert p2 == p3 and same_bits(np.concatenate([a.cpu().numpy(), b.cpu().numpy()]), c)
