@@ -470,15 +470,16 @@ def rp_kernel_launches():
 
 
 # ---- convenience: allocate and fill
-_DIST_DTYPE = {"u64": torch.uint64, "uniform": torch.float64, "bounded": torch.uint64, "normal": torch.float64,
-               "exp": torch.float64, "gamma": torch.float64, "beta": torch.float64}
+_DIST_DTYPE = {"u64": torch.uint64, "uniform": torch.float64, "uniform52": torch.float64, "bounded": torch.uint64,
+               "normal": torch.float64, "exp": torch.float64, "gamma": torch.float64, "beta": torch.float64}
 
 
 def fill(dist, n, engine="xoshiro256pp", seed=0, stream=NO_STREAM, pos=0, params=(), out=None, cuda_stream=None):
     """Allocate (unless `out` is given) and fill n variates; returns (out, new_pos)."""
     if out is None:
-        out = torch.empty(n, dtype=_DIST_DTYPE[dist], device="cuda")
-    f = {"u64": rp_fill_u64, "uniform": rp_fill_uniform, "normal": rp_fill_normal, "exp": rp_fill_exp}
+        out = torch.empty(n, dtype=_DIST_DTYPE.get(dist, torch.float64), device="cuda")
+    f = {"u64": rp_fill_u64, "uniform": rp_fill_uniform, "uniform52": rp_fill_uniform52, "normal": rp_fill_normal,
+         "exp": rp_fill_exp}
     if dist in f:
         newpos = f[dist](engine, seed, stream, pos, out, cuda_stream)
     elif dist == "bounded":
@@ -487,6 +488,8 @@ def fill(dist, n, engine="xoshiro256pp", seed=0, stream=NO_STREAM, pos=0, params
         newpos = rp_fill_gamma(engine, seed, stream, pos, params[0], out, cuda_stream)
     elif dist == "beta":
         newpos = rp_fill_beta(engine, seed, stream, pos, params[0], params[1], out, cuda_stream)
+    elif dist in DERIVED:
+        newpos = rp_fill_derived(engine, seed, stream, pos, dist, params, out, cuda_stream)
     else:
         raise ValueError(dist)
     return out, newpos
