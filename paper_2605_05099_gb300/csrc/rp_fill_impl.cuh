@@ -675,17 +675,17 @@ __global__ void k_tails(FillArgs a) {
 // ------------------------------------------------------------------ per-engine entry
 constexpr int NT_ = 128;
 constexpr int C_ = 256;
-constexpr int CM_ = 2048;   // chunk words of the merge-seam samplers
+constexpr int CM_ = 2048;   // chunk words of the merge-seam samplers in batches (single fills: S::kChunk)
 constexpr int NTM_ = 32;    // threads per CTA of the merge-seam samplers
 constexpr int CR_ = 256;    // chunk words of the one-pass bounded fill with rejections
 
 template <class E, class S>
 int launch_merge(const FillArgs& a, int grid, cudaStream_t s, int* occ) {
   if (occ) {
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k_merge<NTM_, CM_, E, S>, NTM_, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k_merge<NTM_, S::kChunk, E, S>, NTM_, 0);
     return 0;
   }
-  k_merge<NTM_, CM_, E, S><<<grid, NTM_, 0, s>>>(a);
+  k_merge<NTM_, S::kChunk, E, S><<<grid, NTM_, 0, s>>>(a);
   return (int)cudaGetLastError();
 }
 

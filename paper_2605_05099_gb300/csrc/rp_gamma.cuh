@@ -208,7 +208,7 @@ struct NormalMach {
 // Record words of a variate: r[0] = kinds (xk | yk << 8), r[1..3] = X (xa,
 // xb, ub), r[4..6] = Y (beta only).
 struct SampGamma {
-  static constexpr bool kBeta = false;
+  static constexpr int kChunk = 2048;   // words per thread chunk in a single fill
   struct M {
     GammaMach g;
     __device__ __forceinline__ void reset() { g.reset(); }
@@ -227,7 +227,8 @@ struct SampGamma {
 };
 
 struct SampBeta {
-  static constexpr bool kBeta = true;
+  // two gamma chains coalesce more slowly at a seam: longer chunks amortise the search
+  static constexpr int kChunk = 4096;
   struct M {
     GammaMach g;
     int ph;        // 0 drawing X, 1 drawing Y
@@ -267,7 +268,7 @@ struct SampBeta {
 // stream.  Record: r[0] = kinds (Z | V << 8), r[1..2] = Z (xa, xb), r[4..6]
 // = the gamma record of V.  ep[0] = nu.
 struct SampT {
-  static constexpr bool kBeta = true;   // two sub-variates per output
+  static constexpr int kChunk = 4096;   // two sub-variates per output, as beta
   struct M {
     NormalMach nm;
     GammaMach g;

@@ -141,7 +141,9 @@ int occupancy_blocks(int engine, int dist, int epi) {
 
 TileGeom tile_geom(int engine, int dist) {
   (void)engine;
-  if (dist == D_GAMMA || dist == D_BETA || dist == D_T) return TileGeom{NTM_, CM_, NTM_ * CM_, 0};
+  if (dist == D_GAMMA) return TileGeom{NTM_, SampGamma::kChunk, NTM_ * SampGamma::kChunk, 0};
+  if (dist == D_BETA) return TileGeom{NTM_, SampBeta::kChunk, NTM_ * SampBeta::kChunk, 0};
+  if (dist == D_T) return TileGeom{NTM_, SampT::kChunk, NTM_ * SampT::kChunk, 0};
   if (dist == D_BOUNDED) return TileGeom{NT_, CR_, NT_ * CR_, 0};
   return TileGeom{NT_, C_, NT_ * C_, 0};
 }
