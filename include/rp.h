@@ -313,7 +313,7 @@ const char* rp_version(void);
  * diagnostic counter for benchmarks). */
 uint64_t rp_kernel_launches(void);
 
-/* Checkpointing (Sec. 5, "Thread safety and checkpointing"): a stream's
+/* Checkpointing (Sec. 4.4, "Thread safety and checkpointing"): a stream's
  * exact state -- engine, the state words before word 0 (as rp_seed_state,
  * rp_substream_state and rp_fill_state use them) and the position -- as an
  * opaque, self-checking buffer of RP_STATE_BYTES bytes, and back.  A fill

@@ -136,7 +136,7 @@ def test_derived_argument_errors_without_device(rp):
 
 @pytest.mark.parametrize("engine", ["xoshiro256pp", "pcg64dxsm", "philox4x32_10", "philox4x64_10"])
 def test_state_checkpoint_round_trip(rp, orc, engine):
-    """A serialised state (Sec. 5 checkpointing) restores exactly, and any
+    """A serialised state (Sec. 4.4 checkpointing) restores exactly, and any
     single corrupted byte, a short buffer or an unknown engine is refused."""
     words = rp.rp_seed_state(engine, 2024, 3)
     for pos in (0, 1, 2 ** 40 + 7, 2 ** 64 - 1):
