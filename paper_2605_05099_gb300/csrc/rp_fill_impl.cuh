@@ -674,7 +674,7 @@ __global__ void k_tails(FillArgs a) {
 
 // ------------------------------------------------------------------ per-engine entry
 constexpr int NT_ = 128;
-constexpr int C_ = 256;
+constexpr int C_ = 384;     // chunk words of the one-word and ziggurat fills (measured best of 256, 384, 512)
 constexpr int CM_ = 2048;   // chunk words of the merge-seam samplers in batches (single fills: S::kChunk)
 constexpr int NTM_ = 32;    // threads per CTA of the merge-seam samplers
 constexpr int CR_ = 256;    // chunk words of the one-pass bounded fill with rejections

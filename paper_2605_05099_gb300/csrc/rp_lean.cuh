@@ -132,7 +132,7 @@ struct LeanBounded {
 };
 
 constexpr int kLPend = 8;        // queued wedge tests per lane and chunk
-constexpr int kTileTails = 64;   // tail records per tile (mean ~9 for the normal)
+constexpr int kTileTails = 64;   // tail records per tile (mean ~14 for the normal at 384-word chunks)
 
 // Chain state of pass 1 for one thread.
 struct LeanChain {
