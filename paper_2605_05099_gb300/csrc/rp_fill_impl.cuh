@@ -751,7 +751,7 @@ int dispatch_dist(const FillArgs& a, int grid, cudaStream_t s, int* occ) {
     case D_UNIFORM52: return launch_es<E, SampUniform52>(a, grid, s, occ);
     case D_NORMAL: return a.sp.epi ? launch_lean<E, LeanNormalE>(a, grid, s, occ) : launch_lean<E, LeanNormal>(a, grid, s, occ);
     case D_EXP: return a.sp.epi ? launch_lean<E, LeanExpE>(a, grid, s, occ) : launch_lean<E, LeanExp>(a, grid, s, occ);
-    case D_GAMMA: return launch_merge<E, SampGamma>(a, grid, s, occ);
+    case D_GAMMA: return a.sp.ga.boost ? launch_merge<E, SampGammaBoost>(a, grid, s, occ) : launch_merge<E, SampGamma>(a, grid, s, occ);
     case D_BETA: return launch_merge<E, SampBeta>(a, grid, s, occ);
     case D_T: return launch_merge<E, SampT>(a, grid, s, occ);
     default: return (int)cudaErrorInvalidValue;

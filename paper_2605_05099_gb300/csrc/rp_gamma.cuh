@@ -226,6 +226,12 @@ struct SampGamma {
   }
 };
 
+// Gamma with the boost (alpha < 1): each variate takes longer and its chains
+// coalesce more slowly at a seam, so longer chunks pay off, as for beta.
+struct SampGammaBoost : SampGamma {
+  static constexpr int kChunk = 4096;
+};
+
 struct SampBeta {
   // two gamma chains coalesce more slowly at a seam: longer chunks amortise the search
   static constexpr int kChunk = 4096;

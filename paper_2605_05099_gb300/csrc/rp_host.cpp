@@ -537,7 +537,7 @@ rp_status run_fill_state_locked(int engine, const u64 s_in[4], u64* pos, size_t 
   a.eng.engine = engine;
   a.dist = dist;
   a.sp = sp;
-  rp::TileGeom tg = rp::tile_geom(engine, dist);
+  rp::TileGeom tg = rp::tile_geom(engine, dist, dist == rp::D_GAMMA && sp.ga.boost);
   const u64 T = (u64)tg.tile_words;
   auto key = std::make_pair(engine, dist | (sp.epi ? 256 : 0));   // transformed fills run other kernels
   if (!g_occ.count(key)) g_occ[key] = rp::occupancy_blocks(engine, dist, sp.epi);
@@ -1070,7 +1070,7 @@ extern "C" rp_status rp_fill_normal_philox_static(uint64_t seed, uint64_t stream
   memset(&a, 0, sizeof(a));
   a.eng.engine = RP_PHILOX4X32_10;
   a.dist = rp::D_NORMAL;
-  rp::TileGeom tg = rp::tile_geom(RP_PHILOX4X32_10, rp::D_NORMAL);
+  rp::TileGeom tg = rp::tile_geom(RP_PHILOX4X32_10, rp::D_NORMAL, 0);
   const u64 T = (u64)tg.tile_words;
   memcpy(a.eng.s, s, sizeof(s));
   a.eng.tile_words = T;

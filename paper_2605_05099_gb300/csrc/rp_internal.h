@@ -167,7 +167,7 @@ int launch_mvn_grads(int d, unsigned long long n, const double* G, const double*
                      double* part, void* stream);
 // Tile geometry and resources of a (engine, dist) kernel.
 struct TileGeom { int nt, c, tile_words, smem_bytes; };
-TileGeom tile_geom(int engine, int dist);
+TileGeom tile_geom(int engine, int dist, int gamma_boost);   // gamma_boost: a gamma fill with alpha < 1
 int occupancy_blocks(int engine, int dist, int epi);   // resident CTAs per SM
 // One-time upload of ziggurat tables into device constant/global memory.
 int upload_tables();

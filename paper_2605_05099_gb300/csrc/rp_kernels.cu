@@ -139,8 +139,9 @@ int occupancy_blocks(int engine, int dist, int epi) {
   return occ;
 }
 
-TileGeom tile_geom(int engine, int dist) {
+TileGeom tile_geom(int engine, int dist, int gamma_boost) {
   (void)engine;
+  if (dist == D_GAMMA && gamma_boost) return TileGeom{NTM_, SampGammaBoost::kChunk, NTM_ * SampGammaBoost::kChunk, 0};
   if (dist == D_GAMMA) return TileGeom{NTM_, SampGamma::kChunk, NTM_ * SampGamma::kChunk, 0};
   if (dist == D_BETA) return TileGeom{NTM_, SampBeta::kChunk, NTM_ * SampBeta::kChunk, 0};
   if (dist == D_T) return TileGeom{NTM_, SampT::kChunk, NTM_ * SampT::kChunk, 0};
