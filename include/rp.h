@@ -159,7 +159,8 @@ typedef enum {
   RP_DIST_NORMAL = 3,
   RP_DIST_EXP = 4,
   RP_DIST_GAMMA = 5,     /* alpha = p0 */
-  RP_DIST_BETA = 6       /* a = p0, b = p1 */
+  RP_DIST_BETA = 6,      /* a = p0, b = p1 */
+  RP_DIST_UNIFORM52 = 7  /* 52-bit U[0,1), the paper's default (rp_fill_uniform52) */
 } rp_dist;
 
 /* Fill n variates of `dist` from a stream given by its state words (the

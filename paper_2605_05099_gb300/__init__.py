@@ -14,7 +14,7 @@ import os
 import torch
 
 XOSHIRO256PP, PCG64DXSM, PHILOX4X32_10, PHILOX4X64_10 = 1, 2, 3, 4
-DISTS = {"u64": 0, "uniform": 1, "bounded": 2, "normal": 3, "exp": 4, "gamma": 5, "beta": 6}
+DISTS = {"u64": 0, "uniform": 1, "bounded": 2, "normal": 3, "exp": 4, "gamma": 5, "beta": 6, "uniform52": 7}
 ENGINES = {"xoshiro256pp": XOSHIRO256PP, "pcg64dxsm": PCG64DXSM, "philox4x32_10": PHILOX4X32_10,
            "philox4x64_10": PHILOX4X64_10}
 NO_STREAM = (1 << 64) - 1

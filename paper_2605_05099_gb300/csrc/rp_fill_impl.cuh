@@ -626,6 +626,7 @@ __global__ void __launch_bounds__(NT) k_onepw_batch(BatchArgs b) {
     E e;
     e.init_tile(fa.eng, bi.tile, threadIdx.x, sh4);
     if (fa.dist == D_U64) onepw_tile<NT, C, E, SampU64>(fa, bi.tile, e, stage[wid]);
+    else if (fa.dist == D_UNIFORM52) onepw_tile<NT, C, E, SampUniform52>(fa, bi.tile, e, stage[wid]);
     else onepw_tile<NT, C, E, SampUniform>(fa, bi.tile, e, stage[wid]);
   }
 }

@@ -1142,6 +1142,7 @@ rp_status make_samp(int dist, double p0, double p1, u64 m, rp::SampArgs& sp, int
   *dist_out = dist;
   switch (dist) {
     case RP_DIST_U64: case RP_DIST_UNIFORM: case RP_DIST_NORMAL: case RP_DIST_EXP: return RP_OK;
+    case RP_DIST_UNIFORM52: *dist_out = rp::D_UNIFORM52; return RP_OK;
     case RP_DIST_BOUNDED:
       sp.m = m;
       if (m == 0) { *dist_out = rp::D_U64; return RP_OK; }
@@ -1270,7 +1271,7 @@ struct rp_batch_plan {
 namespace {
 
 int batch_class(int kdist) {
-  if (kdist == rp::D_U64 || kdist == rp::D_UNIFORM) return rp::BC_ONEPW;
+  if (kdist == rp::D_U64 || kdist == rp::D_UNIFORM || kdist == rp::D_UNIFORM52) return rp::BC_ONEPW;
   if (kdist == rp::D_GAMMA || kdist == rp::D_BETA) return rp::BC_MERGE;
   return rp::BC_LEAN;
 }

@@ -154,3 +154,12 @@ def test_state_checkpoint_round_trip(rp, orc, engine):
     with pytest.raises(rp.RPError):
         rp.rp_state_serialize(9, words, 0)
     assert rp.rp_engine_name(rp.ENGINES[engine]) == engine and rp.rp_engine_name(0) is None
+
+
+def test_dist_codes_match_the_header(rp):
+    """The binding's distribution codes are rp.h's rp_dist values."""
+    import re
+    hdr = open(os.path.join(ROOT, "include", "rp.h")).read()
+    body = re.search(r"typedef enum \{([^}]*)\} rp_dist;", hdr).group(1)
+    codes = {m.group(1).lower(): int(m.group(2)) for m in re.finditer(r"RP_DIST_(\w+) = (\d+)", body)}
+    assert codes == rp.DISTS

@@ -180,3 +180,20 @@ def test_batch_errors_and_empty():
     ref, opos = _oracle("philox4x32_10", {"stream": 4, "dist": "exp", "n": 10, "pos": 0})
     assert pos[1] == opos
     assert rp.lib().rp_batch_run(None, 0, 1, BASE, None) == 0
+
+
+@pytest.mark.parametrize("engine", ["xoshiro256pp", "philox4x64_10"])
+def test_batch_and_state_fills_of_the_52bit_uniform(engine):
+    """The paper's default uniform by its distribution code: batched
+    requests and state fills equal the oracle's substream fills bit for bit."""
+    reqs = [{"stream": s, "dist": "uniform52", "n": n, "pos": p, "p0": 0.0, "p1": 0.0, "m": 0}
+            for s, n, p in ((0, 1, 0), (3, 70_001, 5), (9, 12_345, 2 ** 33 + 1), (4095, 250_000, 0))]
+    outs, arr = _alloc(reqs)
+    pos = rp.rp_batch_run(arr, engine, BASE)
+    for i, (r, o) in enumerate(zip(reqs, outs)):
+        ref, opos = _oracle(engine, r)
+        assert pos[i] == opos and np.array_equal(_host(o).view(np.uint64), ref.view(np.uint64)), (engine, i)
+        words = rp.rp_substream_state(engine, BASE, r["stream"])
+        st = torch.empty_like(o)
+        assert rp.rp_fill_state(engine, words, r["pos"], "uniform52", st) == opos
+        assert np.array_equal(_host(st).view(np.uint64), ref.view(np.uint64)), (engine, i)
