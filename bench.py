@@ -152,7 +152,9 @@ def _dist_init():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
+        import torch
         import torch.distributed as dist
+        torch.cuda.set_device(local)   # before the process group, so that NCCL binds this rank's GPU
         dist.init_process_group("nccl")
     return world, rank, local
 
@@ -293,7 +295,9 @@ def run_gpu(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args.cpu_sample)
     extras = None
-    if rank == 0 and not args.no_extras and not args.only and args.log2n == 28:
+    # the other workloads are single-GPU: only a one-GPU run times them (a
+    # multi-GPU run would hold every GPU while rank 0 ran them)
+    if world == 1 and not args.no_extras and not args.only and args.log2n == 28:
         del out_f, out_u
         torch.cuda.empty_cache()
         extras = run_extras(rp, stream)
