@@ -6,14 +6,17 @@
 // constant jump of its engine state, so each thread generates long runs of
 // its stream with one jump per C words.
 //
-// One word per variate (raw words, uniforms): the output index of a word is
-// known, so every thread streams its chunk out through a per-warp staging
-// buffer that turns the chunk-contiguous runs into coalesced 128-byte lines.
+// One word per variate (raw words, uniforms, and bounded integers when
+// rejections are rare): the output index of a word is known, so every thread
+// streams its chunk out through a per-warp staging buffer that turns the
+// chunk-contiguous runs into coalesced 128-byte lines.  Bounded integers with
+// frequent rejections take one pass with parked runs (rp_rej.cuh).
 //
 // Rejection samplers: each thread walks the serial sampler's chain of
 // candidates over its chunk.  The parallel parse (chains across chunk seams)
 // uses sync points for samplers whose candidate length follows from its
-// first word (ziggurat normal/exponential, bounded; rp_lean.cuh):
+// first word (ziggurat normal/exponential, and bounded integers in batches;
+// rp_lean.cuh):
 //   * len(q) is the number of words a candidate starting at word q would
 //     consume (evaluated speculatively for any q);
 //   * the sync point of a chunk is the first s in [G, G+S) (relative to the
@@ -29,7 +32,8 @@
 // output index; pass 2 regenerates the chunk and writes the values through
 // the staging buffer.  Outputs whose value needs FP64 libm (ziggurat tails,
 // ~3e-4 of outputs) are queued and evaluated by full warps in a second
-// kernel.
+// kernel.  Derived distributions transform each value as it is written
+// (epi_apply below).
 #pragma once
 #include <cuda_runtime.h>
 
