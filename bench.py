@@ -390,7 +390,7 @@ def run_extras(rp, stream):
     for name, par in (("unif", (-2.0, 3.0)), ("normal_ms", (1.5, 2.0)), ("lognormal", (0.3, 0.7)),
                       ("exp_scale", (2.5,)), ("gamma_scale", (2.5, 0.5)), ("chi2", (5.0,)), ("gumbel", (1.0, 2.0)),
                       ("pareto", (2.0, 3.0)), ("weibull", (1.7, 2.0)), ("gpd", (0.5, 1.5, 0.3)), ("f", (5.0, 7.0)),
-                      ("skew_normal", (1.0, 2.0, 4.0))):
+                      ("skew_normal", (1.0, 2.0, 4.0)), ("t", (3.0,))):
         f = lambda: rp.rp_fill_derived("xoshiro256pp", 7, rp.NO_STREAM, 0, name, par, z, stream)
         f()
         dv[f"{name}{par}"] = round(n / (_ev_ms(stream, f) / 1e3))

@@ -163,3 +163,18 @@ def test_dist_codes_match_the_header(rp):
     body = re.search(r"typedef enum \{([^}]*)\} rp_dist;", hdr).group(1)
     codes = {m.group(1).lower(): int(m.group(2)) for m in re.finditer(r"RP_DIST_(\w+) = (\d+)", body)}
     assert codes == rp.DISTS
+
+
+def test_binding_refuses_bad_outputs_before_the_library(rp):
+    """The Python binding checks the output tensor (device, dtype, layout) and
+    the derived law's parameter count before any call into librp."""
+    import torch
+    cpu = torch.empty(8, dtype=torch.float64)
+    with pytest.raises(TypeError):
+        rp.rp_fill_normal("xoshiro256pp", 1, rp.NO_STREAM, 0, cpu)
+    with pytest.raises(ValueError):
+        rp.rp_fill_derived("xoshiro256pp", 1, rp.NO_STREAM, 0, "gumbel", (1.0,), cpu)
+    with pytest.raises(KeyError):
+        rp.rp_fill_derived("xoshiro256pp", 1, rp.NO_STREAM, 0, "no_such_law", (1.0,), cpu)
+    with pytest.raises(KeyError):
+        rp.rp_seed_state("no_such_engine", 1)
