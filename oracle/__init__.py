@@ -22,9 +22,9 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SO = os.path.join(_HERE, "liboracle.so")
 
-XOSHIRO256PP, PCG64DXSM, PHILOX4X32_10, PHILOX4X64_10 = 1, 2, 3, 4
+XOSHIRO256PP, PCG64DXSM, PHILOX4X32_10, PHILOX4X64_10, XOSHIRO256SS = 1, 2, 3, 4, 5
 ENGINES = {"xoshiro256pp": XOSHIRO256PP, "pcg64dxsm": PCG64DXSM, "philox4x32_10": PHILOX4X32_10,
-           "philox4x64_10": PHILOX4X64_10}
+           "philox4x64_10": PHILOX4X64_10, "xoshiro256ss": XOSHIRO256SS}
 
 
 def build(force=False):

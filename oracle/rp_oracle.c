@@ -90,10 +90,10 @@ static void seed_words64(uint64_t seed, int has_key, uint64_t key, uint64_t* w, 
  * ==================================================================== */
 static inline uint64_t rotl64(uint64_t x, int k) { return (x << k) | (x >> (64 - k)); }
 
-/* xoshiro256++ (Blackman & Vigna): output from the current state, then the
- * GF(2)-linear transition. */
-static uint64_t xoshiro_next(uint64_t s[4]) {
-  uint64_t out = rotl64(s[0] + s[3], 23) + s[0];
+/* The GF(2)-linear transition shared by xoshiro256++ and xoshiro256**
+ * (Blackman & Vigna 2018; Table "engines"): the two engines differ only in
+ * the scrambler applied to the state before the step. */
+static void xoshiro_step(uint64_t s[4]) {
   uint64_t t = s[1] << 17;
   s[2] ^= s[0];
   s[3] ^= s[1];
@@ -101,6 +101,21 @@ static uint64_t xoshiro_next(uint64_t s[4]) {
   s[0] ^= s[3];
   s[2] ^= t;
   s[3] = rotl64(s[3], 45);
+}
+
+/* xoshiro256++: the "++" scrambler, rotl(s0 + s3, 23) + s0, of the current
+ * state, then the transition. */
+static uint64_t xoshiro_next(uint64_t s[4]) {
+  uint64_t out = rotl64(s[0] + s[3], 23) + s[0];
+  xoshiro_step(s);
+  return out;
+}
+
+/* xoshiro256**: the "**" scrambler, rotl(5 s1, 7) 9, of the current state,
+ * then the same transition. */
+static uint64_t xoshiro_ss_next(uint64_t s[4]) {
+  uint64_t out = rotl64(s[1] * 5u, 7) * 9u;
+  xoshiro_step(s);
   return out;
 }
 
@@ -224,6 +239,7 @@ uint64_t or_next(or_gen* g) {
   uint64_t w;
   switch (g->engine) {
     case OR_XOSHIRO256PP: w = xoshiro_next(g->s); break;
+    case OR_XOSHIRO256SS: w = xoshiro_ss_next(g->s); break;
     case OR_PCG64DXSM: w = pcg_next(g->s); break;
     case OR_PHILOX4X64_10: w = philox64_word(g, g->pos); break;
     default: w = philox_word(g, g->pos); break;
@@ -242,7 +258,8 @@ int or_gen_seed(or_gen* g, int engine, uint64_t seed, int has_key, uint64_t key)
   uint64_t w[4] = {0, 0, 0, 0};
   memset(g, 0, sizeof(*g));
   g->engine = engine;
-  if (engine == OR_XOSHIRO256PP) {
+  if (engine == OR_XOSHIRO256PP || engine == OR_XOSHIRO256SS) {
+    /* both xoshiro engines: four seed-sequence words, as the state */
     seed_words64(seed, has_key, key, w, 4);
     memcpy(g->s, w, sizeof(w));
     if ((w[0] | w[1] | w[2] | w[3]) == 0) return -1;
@@ -300,7 +317,7 @@ void or_xoshiro_charpoly(uint64_t out[5]) {
     enum { NB = 512 };
     uint8_t seq[NB];
     uint64_t s[4] = {0x0123456789abcdefull, 0xfedcba9876543210ull, 0x0f1e2d3c4b5a6978ull, 0x8796a5b4c3d2e1f0ull};
-    for (int i = 0; i < NB; ++i) { seq[i] = (uint8_t)(s[0] & 1); xoshiro_next(s); }
+    for (int i = 0; i < NB; ++i) { seq[i] = (uint8_t)(s[0] & 1); xoshiro_step(s); }
     /* connection polynomial C(x) = 1 + c1 x + ... ; sequence satisfies
      * sum_{j=0..L} c_j a_{n-j} = 0 */
     uint8_t C[NB + 1] = {0}, B[NB + 1] = {0}, T[NB + 1];
@@ -368,7 +385,7 @@ void or_xoshiro_jump_poly(uint64_t s[4], const uint64_t* nl, int nlimbs) {
   for (int k = 0; k < 256; ++k) {
     if ((q[k >> 6] >> (k & 63)) & 1)
       for (int j = 0; j < 4; ++j) acc[j] ^= cur[j];
-    xoshiro_next(cur);
+    xoshiro_step(cur);
   }
   memcpy(s, acc, sizeof(acc));
 }
@@ -395,7 +412,7 @@ void or_xoshiro_jump_matrix(uint64_t s[4], const uint64_t* nl, int nlimbs) {
   for (int j = 0; j < 256; ++j) {
     uint64_t e[4] = {0, 0, 0, 0};
     e[j >> 6] = 1ull << (j & 63);
-    xoshiro_next(e);
+    xoshiro_step(e);
     memcpy(M->col[j], e, sizeof(e));
   }
   uint64_t v[4];
@@ -410,7 +427,7 @@ void or_xoshiro_jump_matrix(uint64_t s[4], const uint64_t* nl, int nlimbs) {
 }
 
 void or_jump(or_gen* g, uint64_t n_hi, uint64_t n_lo) {
-  if (g->engine == OR_XOSHIRO256PP) {
+  if (g->engine == OR_XOSHIRO256PP || g->engine == OR_XOSHIRO256SS) {
     uint64_t nl[2] = {n_lo, n_hi};
     or_xoshiro_jump_poly(g->s, nl, 2);
   } else if (g->engine == OR_PCG64DXSM) {
@@ -427,7 +444,7 @@ void or_seek(or_gen* g, uint64_t pos) {
 
 void or_substream(or_gen* g, int engine, uint64_t base_seed, uint64_t s) {
   or_gen_seed(g, engine, base_seed, 0, 0);
-  if (engine == OR_XOSHIRO256PP) {
+  if (engine == OR_XOSHIRO256PP || engine == OR_XOSHIRO256SS) {
     /* stream s = base jumped s times by 2^128 (Sec. 2.3, duplicate-and-jump) */
     uint64_t nl[3] = {0, 0, s};
     if (s) or_xoshiro_jump_poly(g->s, nl, 3);

@@ -20,11 +20,11 @@
 extern "C" {
 #endif
 
-enum { OR_XOSHIRO256PP = 1, OR_PCG64DXSM = 2, OR_PHILOX4X32_10 = 3, OR_PHILOX4X64_10 = 4 };
+enum { OR_XOSHIRO256PP = 1, OR_PCG64DXSM = 2, OR_PHILOX4X32_10 = 3, OR_PHILOX4X64_10 = 4, OR_XOSHIRO256SS = 5 };
 
 typedef struct {
   int engine;
-  /* xoshiro256++: s[0..3].
+  /* xoshiro256++ and xoshiro256**: s[0..3].
    * PCG64-DXSM:   s[0]=state hi, s[1]=state lo, s[2]=inc hi, s[3]=inc lo.
    * Philox4x32-10: s[0]=counter lo 64, s[1]=counter hi 64,
    *                s[2]=key (k0 = low 32 bits, k1 = high 32 bits).

@@ -209,3 +209,50 @@ def test_uniform52_closed_form(orc):
     u = orc.fill(orc.gen("philox4x64_10", 5), "uniform52", 1 << 16)
     assert np.array_equal((u * 2.0 ** 52).astype(np.uint64), w >> np.uint64(12))
     assert u.min() >= 0.0 and u.max() < 1.0
+
+
+# ------------------------------------------------------------------ xoshiro256**
+def _unscramble_ss(w):
+    """Inverse of the xoshiro256** scrambler x -> rotl(5 x, 7) 9 (mod 2^64):
+    multiply by the inverse of 9, rotate right by 7, multiply by the inverse
+    of 5.  The inverses come from Python's modular arithmetic, so a scrambler
+    that read another state word, or applied its steps in another order,
+    would not come back to the state."""
+    M = 2 ** 64
+    y = (int(w) * pow(9, -1, M)) % M
+    y = ((y >> 7) | (y << 57)) % M
+    return (y * pow(5, -1, M)) % M
+
+
+def test_xoshiro256ss_outputs_recover_the_shared_state(orc):
+    """Table "engines": xoshiro256** and xoshiro256++ share the seeding and
+    the linear transition and differ only in the scrambler.  Stepping the
+    (independently pinned) xoshiro256++ generator gives the state word s1
+    before each step; every xoshiro256** output, unscrambled, must equal it."""
+    for seed, key in [(2024, None), (7, 3)]:
+        pp = orc.gen("xoshiro256pp", seed, key)
+        ss = orc.gen("xoshiro256ss", seed, key)
+        assert orc.state_words(pp) == orc.state_words(ss)
+        for _ in range(2000):
+            s1 = orc.state_words(pp)[1]
+            orc.next_words(pp, 1)
+            assert _unscramble_ss(orc.next_words(ss, 1)[0]) == s1
+
+
+def test_xoshiro256ss_jumps_seek_and_substreams(orc):
+    """The jump polynomial is the transition's, so it serves both engines:
+    seeking equals stepping, and substream s starts from the xoshiro256++
+    substream's state."""
+    g = orc.gen("xoshiro256ss", 31337)
+    w = orc.next_words(g, 3000)
+    for p in (0, 1, 2, 777, 2999):
+        h = orc.gen("xoshiro256ss", 31337, pos=p)
+        assert int(orc.next_words(h, 1)[0]) == int(w[p]), p
+    for s in (0, 1, 4095):
+        assert orc.state_words(orc.substream("xoshiro256ss", 99, s)) == orc.state_words(orc.substream("xoshiro256pp", 99, s))
+
+
+def test_xoshiro256ss_bit_balance(orc):
+    w = orc.next_words(orc.gen("xoshiro256ss", 2024), 1 << 18)
+    bits = np.unpackbits(w.view(np.uint8)).reshape(-1, 64).mean(axis=0)
+    assert np.all(np.abs(bits - 0.5) < 6 * 0.5 / np.sqrt(len(w)))
