@@ -397,20 +397,22 @@ def run_extras(rp, stream):
     ex["derived_fill"] = {"unit": "variates/s", "n": n, **dv}
     del z, g, dz, dz2
     torch.cuda.empty_cache()
-    # the paper's own Philox (4x64-10) and its default 52-bit uniform, n = 2^28
+    # the paper's own Philox (4x64-10) and xoshiro256**, with the paper's
+    # default 52-bit uniform, n = 2^28
     n28 = 1 << 28
     of = torch.empty(n28, dtype=torch.float64, device="cuda")
-    ph = {}
-    for key, f in (("uniform52", lambda: rp.rp_fill_uniform52("philox4x64_10", SEED, rp.NO_STREAM, 0, of, stream)),
-                   ("normal", lambda: rp.rp_fill_normal("philox4x64_10", SEED, rp.NO_STREAM, 0, of, stream)),
-                   ("exp", lambda: rp.rp_fill_exp("philox4x64_10", SEED, rp.NO_STREAM, 0, of, stream)),
-                   ("bounded:6", lambda: rp.rp_fill_bounded("philox4x64_10", SEED, rp.NO_STREAM, 0, 6, of.view(torch.uint64), stream)),
-                   ("bounded:9223372036854775809",
-                    lambda: rp.rp_fill_bounded("philox4x64_10", SEED, rp.NO_STREAM, 0, 2 ** 63 + 1, of.view(torch.uint64), stream))):
-        f()
-        ms = _ev_ms(stream, f)
-        ph[key] = {"ms": round(ms, 4), "variates_per_s": round(n28 / (ms / 1e3))}
-    ex["philox4x64_10_fills"] = {"n": n28, **ph}
+    for eng in ("philox4x64_10", "xoshiro256ss"):
+        ph = {}
+        for key, f in (("uniform52", lambda: rp.rp_fill_uniform52(eng, SEED, rp.NO_STREAM, 0, of, stream)),
+                       ("normal", lambda: rp.rp_fill_normal(eng, SEED, rp.NO_STREAM, 0, of, stream)),
+                       ("exp", lambda: rp.rp_fill_exp(eng, SEED, rp.NO_STREAM, 0, of, stream)),
+                       ("bounded:6", lambda: rp.rp_fill_bounded(eng, SEED, rp.NO_STREAM, 0, 6, of.view(torch.uint64), stream)),
+                       ("bounded:9223372036854775809",
+                        lambda: rp.rp_fill_bounded(eng, SEED, rp.NO_STREAM, 0, 2 ** 63 + 1, of.view(torch.uint64), stream))):
+            f()
+            ms = _ev_ms(stream, f)
+            ph[key] = {"ms": round(ms, 4), "variates_per_s": round(n28 / (ms / 1e3))}
+        ex[f"{eng}_fills"] = {"n": n28, **ph}
     del of
     torch.cuda.empty_cache()
     # batched substreams (config 4)

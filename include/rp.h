@@ -2,8 +2,8 @@
  *
  * Bulk filling of a device array with n variates from one seeded engine
  * stream, after Randompack (arXiv 2605.05099): engines of Sec. 2.2
- * (xoshiro256++, PCG64-DXSM; Philox4x32-10 in place of the paper's
- * Philox-4x64), seeding and stream control of Sec. 2.3, the distribution
+ * (xoshiro256++, xoshiro256**, PCG64-DXSM, Philox4x32-10 and the paper's
+ * Philox4x64-10), seeding and stream control of Sec. 2.3, the distribution
  * algorithms of Sec. 3 and the validation ideas of Sec. 5.
  *
  * Conventions shared by every entry point
@@ -43,7 +43,9 @@ typedef enum {
   RP_XOSHIRO256PP = 1,   /* Blackman & Vigna 2019, 4 x 64-bit state */
   RP_PCG64DXSM = 2,      /* O'Neill 2019, 128-bit LCG + DXSM output */
   RP_PHILOX4X32_10 = 3,  /* Salmon et al. 2011, 128-bit counter, 64-bit key */
-  RP_PHILOX4X64_10 = 4   /* the paper's Philox: 4 x 64-bit words per block, NumPy's Philox seeding */
+  RP_PHILOX4X64_10 = 4,  /* the paper's Philox: 4 x 64-bit words per block, NumPy's Philox seeding */
+  RP_XOSHIRO256SS = 5    /* Blackman & Vigna 2018: xoshiro256++'s state, seeding, jumps and
+                            substreams, with the "**" scrambler rotl(5 s1, 7) 9 */
 } rp_engine;
 
 typedef int rp_status;
@@ -174,8 +176,8 @@ rp_status rp_fill_state(rp_engine engine, const uint64_t* words, uint64_t* pos, 
 /* State words of substream s of base_seed, the paper's recipe for parallel
  * simulations (Sec. 2.3: copy a base generator, then jump it or set its
  * stream): the
- * base state is seeded from base_seed with no spawn key; xoshiro256++ jumps
- * it by s * 2^128 words, Philox4x32-10 sets its key to s, PCG64-DXSM sets
+ * base state is seeded from base_seed with no spawn key; the xoshiro engines
+ * jump it by s * 2^128 words, Philox sets its (first) key word to s, PCG64-DXSM sets
  * its increment to 2 s + 1.  words must hold 4 entries; *nw receives the
  * count used. */
 rp_status rp_substream_state(rp_engine engine, uint64_t base_seed, uint64_t s, uint64_t* words, int* nw);
@@ -322,7 +324,7 @@ uint64_t rp_kernel_launches(void);
  *   rp_state_serialize    buf: RP_STATE_BYTES writable host bytes
  *   rp_state_deserialize  refuses (RP_ERR_PARAM) a short buffer, a wrong
  *                         magic or version, an unknown engine, a corrupted
- *                         checksum or an all-zero xoshiro256++ state;
+ *                         checksum or an all-zero xoshiro state;
  *                         words receives 4 words. */
 #define RP_STATE_BYTES 64
 rp_status rp_state_serialize(rp_engine engine, const uint64_t* words, uint64_t pos, uint8_t* buf, size_t buflen);

@@ -7,7 +7,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "librp.so")
-SOURCES = ["rp_fill_xo.cu", "rp_fill_pcg.cu", "rp_fill_ph.cu", "rp_fill_ph64.cu", "rp_kernels.cu", "rp_grad.cu", "rp_mvn.cu", "rp_static_scratch.cu", "rp_host.cpp"]
+SOURCES = ["rp_fill_xo.cu", "rp_fill_xss.cu", "rp_fill_pcg.cu", "rp_fill_ph.cu", "rp_fill_ph64.cu", "rp_kernels.cu", "rp_grad.cu", "rp_mvn.cu", "rp_static_scratch.cu", "rp_host.cpp"]
 DEPS = SOURCES + ["rp_device.cuh", "rp_gamma.cuh", "rp_fill_impl.cuh", "rp_lean.cuh", "rp_rej.cuh", "rp_internal.h", "zig_tables.inc", "log_table.inc"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-ffp-contract=off", "-fmad=false",

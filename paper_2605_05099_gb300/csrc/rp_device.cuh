@@ -278,12 +278,16 @@ __device__ __forceinline__ void gf2_apply(const ulonglong4_32a* __restrict__ tab
   s0 = a0; s1 = a1; s2 = a2; s3 = a3;
 }
 
-// xoshiro256++ (Blackman & Vigna): output from the current state, then the
-// linear transition.  Jumps by precomputed GF(2) matrices T^(2^j).
-struct XoshiroDev {
+// xoshiro256++ and xoshiro256** (Blackman & Vigna; Table "engines"): the
+// scrambler's output of the current state, then the linear transition that
+// both engines share, so they share the jump tables too.  kSS selects the
+// "**" scrambler, rotl(5 s1, 7) 9, over "++", rotl(s0 + s3, 23) + s0.
+// Jumps by precomputed GF(2) matrices T^(2^j).
+template <bool kSS>
+struct XoshiroT {
   u64 s0, s1, s2, s3;
   __device__ __forceinline__ u64 next() {
-    u64 r = rotl64(s0 + s3, 23) + s0;
+    u64 r = kSS ? rotl64(s1 * 5ull, 7) * 9ull : rotl64(s0 + s3, 23) + s0;
     u64 t = s1 << 17;
     s2 ^= s0; s3 ^= s1; s1 ^= s2; s0 ^= s3; s2 ^= t; s3 = rotl64(s3, 45);
     return r;
@@ -340,6 +344,8 @@ struct XoshiroDev {
     if (t) gf2_apply((const ulonglong4_32a*)a.gf2_thread + (size_t)t * 1024, s0, s1, s2, s3);
   }
 };
+using XoshiroDev = XoshiroT<false>;
+using XoshiroSSDev = XoshiroT<true>;
 
 // PCG64-DXSM (O'Neill): DXSM output of the current state, then the LCG step
 // with the 64-bit multiplier.  Jumps by affine powers (A, G): s <- A s + G inc.

@@ -318,14 +318,16 @@ int pcg_device_pow(u64** out) {
 // Counter-based engines address words directly: a fill starts at a word
 // offset instead of jumping its state.
 bool counter_engine(int engine) { return engine == RP_PHILOX4X32_10 || engine == RP_PHILOX4X64_10; }
+// xoshiro256++ and xoshiro256** share the state, the seeding and the jumps.
+bool xoshiro_engine(int engine) { return engine == RP_XOSHIRO256PP || engine == RP_XOSHIRO256SS; }
 
 constexpr u128 kPcgMult128 = ((u128)0x2360ED051FC65DA4ull << 64) | 0x4385DF649FCCF645ull;
 
 rp_status seed_state(int engine, u64 seed, u64 stream, u64 s[4]) {
   u64 w[4] = {0, 0, 0, 0};
-  if (engine == RP_XOSHIRO256PP) {
+  if (xoshiro_engine(engine)) {
     seed_words(seed, stream, w, 4);
-    if ((w[0] | w[1] | w[2] | w[3]) == 0) return fail(RP_ERR_SEED, "seeding gave an all-zero xoshiro256++ state");
+    if ((w[0] | w[1] | w[2] | w[3]) == 0) return fail(RP_ERR_SEED, "seeding gave an all-zero xoshiro state");
     memcpy(s, w, sizeof(w));
   } else if (engine == RP_PCG64DXSM) {
     seed_words(seed, stream, w, 4);
@@ -348,7 +350,7 @@ rp_status seed_state(int engine, u64 seed, u64 stream, u64 s[4]) {
 }
 
 void jump_state(int engine, u64 s[4], u128 delta) {
-  if (engine == RP_XOSHIRO256PP) {
+  if (xoshiro_engine(engine)) {
     xo_jump(s, delta);
   } else if (engine == RP_PCG64DXSM) {
     Aff a = aff_steps(delta);
@@ -569,7 +571,7 @@ rp_status run_fill_state_locked(int engine, const u64 s_in[4], u64* pos, size_t 
     a.eng.tile_words = T;
     a.eng.chunk_words = (u64)tg.c;
     if (grid > 65535) return fail(RP_ERR_INTERNAL, "grid too large for the CTA jump tables");
-    if (engine == RP_XOSHIRO256PP) {
+    if (xoshiro_engine(engine)) {
       e = xo_device_pow((void**)&a.eng.gf2_pow);
       if (!e) e = xo_device_stride(a.eng.stride, (void**)&a.eng.gf2_stride);
       if (!e) e = xo_device_thread((u64)tg.c, tg.nt, (void**)&a.eng.gf2_thread);
@@ -651,7 +653,7 @@ rp_status check_fill_args(int engine, u64* pos, size_t n, void* d_out) {
   if (n == 0) return RP_OK;
   if (!d_out) return fail(RP_ERR_NULL, "output pointer is NULL");
   if ((uintptr_t)d_out & 7) return fail(RP_ERR_PARAM, "output pointer must be 8-byte aligned");
-  if (engine < 1 || engine > 4) return fail(RP_ERR_ENGINE, "unknown engine id " + std::to_string(engine));
+  if (engine < 1 || engine > 5) return fail(RP_ERR_ENGINE, "unknown engine id " + std::to_string(engine));
   return RP_OK;
 }
 
@@ -914,7 +916,7 @@ rp_status rp_seed_state(rp_engine engine, uint64_t seed, uint64_t stream, uint64
 
 rp_status rp_jump_state(rp_engine engine, uint64_t* words, uint64_t delta_hi, uint64_t delta_lo) {
   if (!words) return fail(RP_ERR_NULL, "words is NULL");
-  if (engine < 1 || engine > 4) return fail(RP_ERR_ENGINE, "unknown engine id " + std::to_string((int)engine));
+  if (engine < 1 || engine > 5) return fail(RP_ERR_ENGINE, "unknown engine id " + std::to_string((int)engine));
   std::lock_guard<std::mutex> lk(g_mu);
   u128 d = ((u128)delta_hi << 64) | delta_lo;
   if (engine == RP_PHILOX4X32_10 && (d & 1)) return fail(RP_ERR_PARAM, "Philox4x32 state jumps must be even (two words per block)");
@@ -946,7 +948,7 @@ uint64_t get_le(const uint8_t* p, int bytes) {
 rp_status rp_state_serialize(rp_engine engine, const uint64_t* words, uint64_t pos, uint8_t* buf, size_t buflen) {
   if (!words || !buf) return fail(RP_ERR_NULL, "words/buf is NULL");
   if (buflen < RP_STATE_BYTES) return fail(RP_ERR_PARAM, "state buffer shorter than RP_STATE_BYTES");
-  if (engine < 1 || engine > 4) return fail(RP_ERR_ENGINE, "unknown engine id " + std::to_string((int)engine));
+  if (engine < 1 || engine > 5) return fail(RP_ERR_ENGINE, "unknown engine id " + std::to_string((int)engine));
   memset(buf, 0, RP_STATE_BYTES);
   memcpy(buf, "RPST", 4);
   put_le(buf + 4, 1, 2);
@@ -964,10 +966,10 @@ rp_status rp_state_deserialize(const uint8_t* buf, size_t buflen, rp_engine* eng
   if (get_le(buf + 56, 8) != fnv1a(buf, 56)) return fail(RP_ERR_PARAM, "state buffer checksum mismatch");
   if (get_le(buf + 48, 8) != 0) return fail(RP_ERR_PARAM, "state buffer reserved bytes are not zero");
   const uint64_t e = get_le(buf + 6, 2);
-  if (e < 1 || e > 4) return fail(RP_ERR_PARAM, "state buffer names an unknown engine");
+  if (e < 1 || e > 5) return fail(RP_ERR_PARAM, "state buffer names an unknown engine");
   uint64_t w[4];
   for (int i = 0; i < 4; ++i) w[i] = get_le(buf + 8 + 8 * i, 8);
-  if (e == RP_XOSHIRO256PP && (w[0] | w[1] | w[2] | w[3]) == 0) return fail(RP_ERR_PARAM, "all-zero xoshiro256++ state");
+  if (xoshiro_engine((int)e) && (w[0] | w[1] | w[2] | w[3]) == 0) return fail(RP_ERR_PARAM, "all-zero xoshiro state");
   *engine = (rp_engine)e;
   memcpy(words, w, sizeof(w));
   *pos = get_le(buf + 40, 8);
@@ -980,6 +982,7 @@ const char* rp_engine_name(int engine) {
     case RP_PCG64DXSM: return "pcg64dxsm";
     case RP_PHILOX4X32_10: return "philox4x32_10";
     case RP_PHILOX4X64_10: return "philox4x64_10";
+    case RP_XOSHIRO256SS: return "xoshiro256ss";
     default: return nullptr;
   }
 }
@@ -1191,7 +1194,7 @@ rp_status beta_equal_state_locked(int engine, const u64 s[4], u64* pos, size_t n
 rp_status substream_words(int engine, u64 base_seed, u64 sidx, u64 w[4]) {
   rp_status st = seed_state(engine, base_seed, RP_NO_STREAM, w);
   if (st) return st;
-  if (engine == RP_XOSHIRO256PP) {
+  if (xoshiro_engine(engine)) {
     const u64 limbs[3] = {0, 0, sidx};   // s * 2^128
     xo_jump_limbs(w, limbs, 3);
   } else if (engine == RP_PHILOX4X32_10 || engine == RP_PHILOX4X64_10) {
@@ -1224,7 +1227,7 @@ extern "C" rp_status rp_fill_state(rp_engine engine, const uint64_t* words, uint
 
 extern "C" rp_status rp_substream_state(rp_engine engine, uint64_t base_seed, uint64_t s, uint64_t* words, int* nw) {
   if (!words || !nw) return fail(RP_ERR_NULL, "words/nw is NULL");
-  if (engine < 1 || engine > 4) return fail(RP_ERR_ENGINE, "unknown engine id " + std::to_string((int)engine));
+  if (engine < 1 || engine > 5) return fail(RP_ERR_ENGINE, "unknown engine id " + std::to_string((int)engine));
   std::lock_guard<std::mutex> lk(g_mu);
   u64 w[4] = {0, 0, 0, 0};
   rp_status st = substream_words(engine, base_seed, s, w);
@@ -1304,7 +1307,7 @@ rp_status batch_build(rp_batch_plan& P, int schedule, BatchBuild& B) {
   int e = 0;
   void *gpow = nullptr, *gthr[3] = {nullptr, nullptr, nullptr}, *gcta[3] = {nullptr, nullptr, nullptr};
   u64* ppow = nullptr;
-  if (P.engine == RP_XOSHIRO256PP) {
+  if (xoshiro_engine(P.engine)) {
     e = xo_device_pow(&gpow);
     for (int c = 0; c < 3 && !e; ++c) {
       rp::TileGeom tg = rp::batch_geom(c, cvar);
@@ -1500,7 +1503,7 @@ extern "C" rp_status rp_batch_plan_create(const rp_request* reqs, size_t nreq, r
   if (!plan) return fail(RP_ERR_NULL, "plan is NULL");
   *plan = nullptr;
   if (nreq && !reqs) return fail(RP_ERR_NULL, "reqs is NULL");
-  if (engine < 1 || engine > 4) return fail(RP_ERR_ENGINE, "unknown engine id " + std::to_string((int)engine));
+  if (engine < 1 || engine > 5) return fail(RP_ERR_ENGINE, "unknown engine id " + std::to_string((int)engine));
   std::lock_guard<std::mutex> lk(g_mu);
   int e = ensure_zig();
   if (e) return cuda_fail(e, "ziggurat table upload");

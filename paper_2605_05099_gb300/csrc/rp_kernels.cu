@@ -7,14 +7,17 @@ int dispatch_xo(const FillArgs& a, int grid, void* s, int* occ);
 int dispatch_pcg(const FillArgs& a, int grid, void* s, int* occ);
 int dispatch_ph(const FillArgs& a, int grid, void* s, int* occ);
 int dispatch_ph64(const FillArgs& a, int grid, void* s, int* occ);
+int dispatch_xss(const FillArgs& a, int grid, void* s, int* occ);
 int upload_zig_xo(const void* host2);
 int batch_xo(int cls, int cvar, const BatchArgs& b, int grid, void* s, int* occ);
 int batch_pcg(int cls, int cvar, const BatchArgs& b, int grid, void* s, int* occ);
 int batch_ph(int cls, int cvar, const BatchArgs& b, int grid, void* s, int* occ);
 int batch_ph64(int cls, int cvar, const BatchArgs& b, int grid, void* s, int* occ);
+int batch_xss(int cls, int cvar, const BatchArgs& b, int grid, void* s, int* occ);
 int upload_zig_pcg(const void* host2);
 int upload_zig_ph(const void* host2);
 int upload_zig_ph64(const void* host2);
+int upload_zig_xss(const void* host2);
 
 namespace {
 int dispatch(const FillArgs& a, int grid, void* s, int* occ) {
@@ -23,6 +26,7 @@ int dispatch(const FillArgs& a, int grid, void* s, int* occ) {
     case 2: return dispatch_pcg(a, grid, s, occ);
     case 3: return dispatch_ph(a, grid, s, occ);
     case 4: return dispatch_ph64(a, grid, s, occ);
+    case 5: return dispatch_xss(a, grid, s, occ);
     default: return (int)cudaErrorInvalidValue;
   }
 }
@@ -36,6 +40,7 @@ int launch_batch(int engine, int cls, int cvar, const BatchArgs& b, int grid, vo
     case 2: return batch_pcg(cls, cvar, b, grid, stream, occ);
     case 3: return batch_ph(cls, cvar, b, grid, stream, occ);
     case 4: return batch_ph64(cls, cvar, b, grid, stream, occ);
+    case 5: return batch_xss(cls, cvar, b, grid, stream, occ);
     default: return (int)cudaErrorInvalidValue;
   }
 }
@@ -155,6 +160,7 @@ int upload_zig(const void* host2) {
   if (!e) e = upload_zig_pcg(host2);
   if (!e) e = upload_zig_ph(host2);
   if (!e) e = upload_zig_ph64(host2);
+  if (!e) e = upload_zig_xss(host2);
   return e;
 }
 

@@ -31,7 +31,7 @@ def test_exports_every_declared_symbol(rp):
         assert hasattr(L, s), s
 
 
-@pytest.mark.parametrize("engine", ["xoshiro256pp", "pcg64dxsm", "philox4x32_10", "philox4x64_10"])
+@pytest.mark.parametrize("engine", ["xoshiro256pp", "pcg64dxsm", "philox4x32_10", "philox4x64_10", "xoshiro256ss"])
 def test_seed_state_matches_oracle(rp, orc, engine):
     rng = np.random.default_rng(5)
     for seed in [0, 1, 7, 99, 2024, 12345, 2 ** 40 + 3, 2 ** 64 - 1] + [int(x) for x in rng.integers(0, 2 ** 62, 20)]:
@@ -53,6 +53,9 @@ def test_jump_state_matches_oracle(rp, orc):
     j = rp.rp_jump_state("philox4x32_10", ph, 2 ** 65 + 10)
     c0, c1 = ph[0] | ph[1] << 64, j[0] | j[1] << 64
     assert c1 - c0 == 2 ** 64 + 5 and j[2] == ph[2]
+    # xoshiro256** jumps with xoshiro256++'s tables (one transition)
+    x = rp.rp_seed_state("xoshiro256ss", 99)
+    assert x == s0 and rp.rp_jump_state("xoshiro256ss", x, 2 ** 100 + 3) == orc.xoshiro_jump(s0, 2 ** 100 + 3, "poly")
     q = rp.rp_seed_state("philox4x64_10", 3)
     j = rp.rp_jump_state("philox4x64_10", q, 2 ** 66 + 12)   # four words per block
     assert (j[0] | j[1] << 64) - (q[0] | q[1] << 64) == 2 ** 64 + 3 and j[2:] == q[2:]
@@ -91,7 +94,7 @@ def test_argument_errors(rp):
     assert rp.rp_version().startswith("rp ")
 
 
-@pytest.mark.parametrize("engine", ["xoshiro256pp", "pcg64dxsm", "philox4x32_10", "philox4x64_10"])
+@pytest.mark.parametrize("engine", ["xoshiro256pp", "pcg64dxsm", "philox4x32_10", "philox4x64_10", "xoshiro256ss"])
 def test_substream_state_matches_oracle(rp, orc, engine):
     """Substream s of a base seed (Sec. 2.3 recipe): library host code vs the
     oracle's independent construction (xoshiro: jump polynomial by s 2^128)."""
@@ -134,7 +137,7 @@ def test_derived_argument_errors_without_device(rp):
         assert codes[name.upper()] == kind and oracle.DERIVED[name][0] == kind, name
 
 
-@pytest.mark.parametrize("engine", ["xoshiro256pp", "pcg64dxsm", "philox4x32_10", "philox4x64_10"])
+@pytest.mark.parametrize("engine", ["xoshiro256pp", "pcg64dxsm", "philox4x32_10", "philox4x64_10", "xoshiro256ss"])
 def test_state_checkpoint_round_trip(rp, orc, engine):
     """A serialised state (Sec. 4.4 checkpointing) restores exactly, and any
     single corrupted byte, a short buffer or an unknown engine is refused."""
@@ -163,6 +166,17 @@ def test_dist_codes_match_the_header(rp):
     body = re.search(r"typedef enum \{([^}]*)\} rp_dist;", hdr).group(1)
     codes = {m.group(1).lower(): int(m.group(2)) for m in re.finditer(r"RP_DIST_(\w+) = (\d+)", body)}
     assert codes == rp.DISTS
+
+
+def test_engine_codes_match_the_header(rp, orc):
+    """rp.h's rp_engine values are the binding's and the oracle's engine ids."""
+    import re
+    hdr = open(os.path.join(ROOT, "include", "rp.h")).read()
+    body = re.search(r"typedef enum \{([^}]*)\} rp_engine;", hdr).group(1)
+    codes = {m.group(1).lower(): int(m.group(2)) for m in re.finditer(r"RP_(\w+) = (\d+)", body)}
+    assert codes == rp.ENGINES == orc.ENGINES
+    for name, e in codes.items():
+        assert rp.rp_engine_name(e) == name
 
 
 def test_binding_refuses_bad_outputs_before_the_library(rp):

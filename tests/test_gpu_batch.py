@@ -98,7 +98,7 @@ def test_mixed_batch_matches_oracle(engine):
         _compare(_host(o), ref, r, (engine, i, r["dist"], r["n"]))
 
 
-@pytest.mark.parametrize("engine", ["xoshiro256pp", "philox4x32_10", "philox4x64_10"])
+@pytest.mark.parametrize("engine", ["xoshiro256pp", "philox4x32_10", "philox4x64_10", "xoshiro256ss"])
 def test_autotuned_plan_replays_and_matches_state_fills(engine):
     reqs = inputs.batch_workload(n_req=48, lo=1e2, hi=2e5, seed=5)
     outs, arr = _alloc(reqs)

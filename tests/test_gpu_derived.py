@@ -120,7 +120,7 @@ def test_derived_parity(name, params, tol):
     check(name, params, tol)
 
 
-@pytest.mark.parametrize("engine", ["pcg64dxsm", "philox4x32_10", "philox4x64_10"])
+@pytest.mark.parametrize("engine", ["pcg64dxsm", "philox4x32_10", "philox4x64_10", "xoshiro256ss"])
 @pytest.mark.parametrize("name,params,tol", [c for c in CASES if c[0] in ("unif", "lognormal", "pareto", "chi2", "f", "t")][:8],
                          ids=lambda x: str(x))
 def test_derived_parity_engines(engine, name, params, tol):

@@ -15,7 +15,7 @@ from gpu_util import assert_parity, first_mismatch, gpu_fill, oracle_fill, same_
 
 pytestmark = pytest.mark.gpu
 
-ENGINES = ["xoshiro256pp", "pcg64dxsm", "philox4x32_10", "philox4x64_10"]
+ENGINES = ["xoshiro256pp", "pcg64dxsm", "philox4x32_10", "philox4x64_10", "xoshiro256ss"]
 DISTS = [("u64", ()), ("uniform", ()), ("uniform52", ()), ("normal", ()), ("exp", ()), ("bounded", (6,)),
          ("bounded", (1_000_000_007,)), ("bounded", (2 ** 63 + 1,))]
 SIZES = [1, 2, 63, 8191, 8192, 8193, 3 * 8192 + 17, 100_003]
@@ -118,7 +118,8 @@ def test_philox_bijection_matches_curand():
 # seeds whose first 100003 bounded words (m = 2^43 + 1, one rejection in
 # about 2.1e6 words) contain a rejection, found with the oracle, and seeds
 # without one: both sides of the one-pass shortcut for rare rejections
-REJECT_SEEDS = {"xoshiro256pp": [9, 15], "pcg64dxsm": [30, 99], "philox4x32_10": [16, 33], "philox4x64_10": [13, 54]}
+REJECT_SEEDS = {"xoshiro256pp": [9, 15], "pcg64dxsm": [30, 99], "philox4x32_10": [16, 33], "philox4x64_10": [13, 54],
+                "xoshiro256ss": [4, 12]}
 
 
 @pytest.mark.parametrize("engine", ENGINES)

@@ -11,7 +11,7 @@ from gpu_util import gpu_fill, oracle_fill
 
 pytestmark = pytest.mark.gpu
 
-ENGINES = ["xoshiro256pp", "pcg64dxsm", "philox4x32_10", "philox4x64_10"]
+ENGINES = ["xoshiro256pp", "pcg64dxsm", "philox4x32_10", "philox4x64_10", "xoshiro256ss"]
 SIZES = [1, 7, 1000, 40_000, (1 << 17) + 3]
 
 
