@@ -46,6 +46,19 @@ def oracle_fill(dist, engine, seed, stream, pos, n, params=(), with_start=False)
     return out, int(g.pos)
 
 
+# Bars for outputs built from gamma variates that went through the boost
+# for shapes below 1 (a libm exp; each such gamma is within 2 ulp, the bar
+# for transcendental outputs).  With X^ = X (1 + a), |a| <= 2 ulp(X)/X <=
+# 2^-51, likewise b for Y, and unit roundoff 2^-53 per IEEE operation, the
+# first-order relative error of each formula, over ulp(z) > z 2^-53, gives:
+#   beta   X/(X+Y):              (1-z)(|a|+|b|) + 2 roundings -> < 8 + 2 = 10 ulp
+#   F      (X/n1)/(Y/n2):        |a| + |b| + 3 roundings      -> < 8 + 3 = 11 ulp
+#   Gamma(alpha, theta)  X theta: |a| + 1 rounding            -> < 4 + 1 = 5 ulp
+#   t      Z / sqrt(2 G / nu):   (|a| + 1 rounding)/2 under the root, then the
+#                                root and the quotient: 2 roundings -> < 2.5 + 2 < 5 ulp
+BOOST_ULP = {"beta": 10, "f": 11, "gamma_scale": 5, "t": 5}
+
+
 def ulp_diff(a, b):
     """distance in units in the last place between doubles of the same sign"""
     ia = np.asarray(a, np.float64).view(np.int64).astype(object)

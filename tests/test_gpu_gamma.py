@@ -7,7 +7,7 @@ import numpy as np
 import pytest
 import torch
 
-from gpu_util import gpu_fill, oracle_fill
+from gpu_util import BOOST_ULP, gpu_fill, oracle_fill
 
 pytestmark = pytest.mark.gpu
 
@@ -50,7 +50,7 @@ def test_gamma_parity(engine, alpha):
 @pytest.mark.parametrize("engine", ENGINES)
 @pytest.mark.parametrize("ab", [(0.5, 0.5), (2.0, 5.0)])
 def test_beta_parity(engine, ab):
-    ulp = 0 if min(ab) >= 1 else 4
+    ulp = 0 if min(ab) >= 1 else BOOST_ULP["beta"]
     for n in SIZES:
         check("beta", engine, 7, n, ab, ulp)
 
