@@ -674,7 +674,7 @@ rp_status pairs_fill(int engine, u64 seed, u64 stream, u64* pos, size_t n, int b
                      const double* q, double* d_out, void* cuda_stream) {
   rp_status st = check_fill_args(engine, pos, n, d_out);
   if (st || n == 0) return st;
-  const size_t blk = (size_t)1 << 24;
+  const size_t blk = (size_t)1 << 26;   // pairs per block: 2^27 base variates keep the GPU full (1 GiB scratch)
   double* tmp = nullptr;
   size_t cap = std::min(n, blk);
   int e = (int)cudaMalloc((void**)&tmp, cap * 2 * sizeof(double));
@@ -1169,7 +1169,7 @@ rp_status make_samp(int dist, double p0, double p1, u64 m, rp::SampArgs& sp, int
 // Beta(a, a) from a state: consecutive Gamma(a) pairs (as rp_fill_beta).
 rp_status beta_equal_state_locked(int engine, const u64 s[4], u64* pos, size_t n, const rp::SampArgs& sp,
                                   double* d_out, void* cstream) {
-  const size_t blk = (size_t)1 << 24;
+  const size_t blk = (size_t)1 << 26;   // pairs per block: 2^27 base variates keep the GPU full (1 GiB scratch)
   double* tmp = nullptr;
   size_t cap = std::min(n, blk);
   int e = (int)cudaMalloc((void**)&tmp, cap * 2 * sizeof(double));
