@@ -12,6 +12,10 @@ Parity status per function (see the tests under tests/test_oracle_*.py):
 every function is pinned against something other than itself (NumPy
 black-box engines and SeedSequence, closed forms, brute force, jump
 identities, mpmath quadrature, SciPy finite differences, statistical tests).
+One exception: the constants of the xoshiro256** scrambler (5, 7, 9) come
+from the engine's published definition with no independent vectors here,
+so for them the parity is unpinned; which state word it scrambles, the
+order of its steps and the transition under it are pinned.
 """
 import ctypes
 import os

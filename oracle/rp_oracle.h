@@ -10,6 +10,10 @@
  * (Sec. 2.3) plus a word position `pos`; word p of the stream is the p-th
  * 64-bit engine output after seeding.  A fill consumes exactly the words its
  * variates used and leaves `pos` at the next unconsumed word.
+ *
+ * Parity unpinned: the constants of the xoshiro256** scrambler (5, 7, 9),
+ * taken from the engine's published definition; the rest of that engine is
+ * pinned through xoshiro256++ (see tests/test_oracle_engines.py).
  */
 #ifndef RP_ORACLE_H
 #define RP_ORACLE_H
