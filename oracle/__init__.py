@@ -88,6 +88,10 @@ def lib():
             "or_fill_bounded": (None, [P(Gen), sz, u64, vp, vp]),
             "or_fill_normal": (None, [P(Gen), sz, vp, vp]),
             "or_fill_exp": (None, [P(Gen), sz, vp, vp]),
+            "or_fill_uniformf": (None, [P(Gen), sz, vp]),
+            "or_fill_normalf": (None, [P(Gen), sz, vp, vp]),
+            "or_fill_expf": (None, [P(Gen), sz, vp, vp]),
+            "or_zig_table_f": (i32, [i32, i32, P(ctypes.c_uint32), P(ctypes.c_float), P(ctypes.c_float)]),
             "or_fill_gamma": (i32, [P(Gen), sz, dbl, vp, vp]),
             "or_fill_beta": (i32, [P(Gen), sz, dbl, dbl, vp, vp]),
             "or_fill_derived": (i32, [P(Gen), i32, sz, vp, vp, vp]),
@@ -241,6 +245,17 @@ def fill(g, dist, n, *params, with_start=False):
     elif dist == "exp":
         out = np.empty(n, np.float64)
         L.or_fill_exp(gp, n, _ptr(out), _ptr(start))
+    elif dist == "uniformf":
+        out = np.empty(n, np.float32)
+        L.or_fill_uniformf(gp, n, _ptr(out))
+        if with_start:
+            raise ValueError("uniformf has one 32-bit word per output: no start list")
+    elif dist == "normalf":
+        out = np.empty(n, np.float32)
+        L.or_fill_normalf(gp, n, _ptr(out), _ptr(start))
+    elif dist == "expf":
+        out = np.empty(n, np.float32)
+        L.or_fill_expf(gp, n, _ptr(out), _ptr(start))
     elif dist == "gamma":
         out = np.empty(n, np.float64)
         if L.or_fill_gamma(gp, n, float(params[0]), _ptr(out), _ptr(start)) != 0:
@@ -284,6 +299,19 @@ def zig_counts():
     c = np.zeros(4, np.uint64)
     lib().or_zig_counts(_ptr(c))
     return dict(fast=int(c[0]), wedge=int(c[1]), reject=int(c[2]), tail=int(c[3]))
+
+
+def zig_table_f(which):
+    """Float tables of the f variants, derived from the double ones:
+    which 0 normal, 1 exponential -> (k uint32[256], w, f float32[256])"""
+    k = np.empty(256, np.uint32)
+    w = np.empty(256, np.float32)
+    f = np.empty(256, np.float32)
+    kk, ww, ff = ctypes.c_uint32(), ctypes.c_float(), ctypes.c_float()
+    for i in range(256):
+        lib().or_zig_table_f(which, i, ctypes.byref(kk), ctypes.byref(ww), ctypes.byref(ff))
+        k[i], w[i], f[i] = kk.value, ww.value, ff.value
+    return k, w, f
 
 
 def zig_table(which):

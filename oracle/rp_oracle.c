@@ -734,6 +734,134 @@ void or_fill_exp(or_gen* g, size_t n, double* out, uint64_t* start) {
   }
 }
 
+/* ---- float variants (Table "continuous": the functions with suffix f;
+ * Sec. 3.1: the engines' bit stream read as 32-bit words; Sec. 4.4: floats
+ * save space and time).  Readings:
+ * - 32-bit words: each 64-bit stream word gives its low half, then its high
+ *   half.  A float fill starts at the low half of word pos.  When it ends
+ *   on a low half, the high half is left unused, so the position after a
+ *   float fill is the next whole word.
+ * - uniformf: the paper's default method with a float: the top 23 bits of
+ *   the 32-bit word in the fraction of a float in [1, 2), minus 1, which is
+ *   exactly floor(h / 2^9) 2^-23.
+ * - u24(h) = floor(h / 2^8) 2^-24 (method 1), the samplers' inner uniform.
+ * - normalf: bits 0-7 strip i, bit 8 sign, bits 9-31 r (23 bits).
+ *   x = RN_f(r w_i), with w_i = RN_f(2^29 W_i) from the double table's
+ *   W_i = x_i 2^-52.  Fast accept when r < k_i / 2^29 (integer division:
+ *   floor(2^23 x_{i-1} / x_i)).  The wedge takes y = RN_f((f_{i-1} - f_i) U + f_i)
+ *   in float operations, with f_i = RN_f(F_i) and U = u24 of the next word,
+ *   and accepts when y < exp(-x^2 / 2), decided in double (x^2 is exact
+ *   there) against the correctly rounded exp.  The tail is the double
+ *   sampler's with U1, U2 = u24 of the next two words, in double, and the
+ *   value RN_f(R + a).
+ * - expf: bits 0-7 strip, bits 8-31 r (24 bits); w_i = RN_f(2^29 W_i) with
+ *   W_i = x_i 2^-53; fast r < k_i / 2^29; wedge against exp(-x) as above;
+ *   tail RN_f(R - log(1 - U)). */
+typedef struct { or_gen* g; uint64_t w; int hi; } half_reader;
+
+static uint32_t next32(half_reader* h) {
+  if (h->hi) { h->hi = 0; return (uint32_t)(h->w >> 32); }
+  h->w = or_next(h->g);
+  h->hi = 1;
+  return (uint32_t)h->w;
+}
+/* 32-bit word index (2 * word + half) of the next 32-bit word */
+static uint64_t half_pos(const half_reader* h) { return h->hi ? 2 * h->g->pos - 1 : 2 * h->g->pos; }
+
+static inline double u24(uint32_t h) { return (double)(h >> 8) * 0x1.0p-24; }
+
+void or_fill_uniformf(or_gen* g, size_t n, float* out) {
+  half_reader h = {g, 0, 0};
+  for (size_t i = 0; i < n; ++i) {
+    uint32_t bits = (next32(&h) >> 9) | 0x3f800000u;
+    float x;
+    memcpy(&x, &bits, 4);
+    out[i] = x - 1.0f;
+  }
+}
+
+/* float tables from the double ones: which 0 normal, 1 exponential */
+int or_zig_table_f(int which, int i, uint32_t* k, float* w, float* f) {
+  if (i < 0 || i > 255) return -1;
+  const uint64_t* K = which ? OR_ZE_K : OR_ZN_K;
+  const double* W = which ? OR_ZE_W : OR_ZN_W;
+  const double* F = which ? OR_ZE_F : OR_ZN_F;
+  *k = (uint32_t)(K[i] >> 29);
+  *w = (float)(W[i] * 0x1.0p29);
+  *f = (float)F[i];
+  return 0;
+}
+
+void or_fill_normalf(or_gen* g, size_t n, float* out, uint64_t* start) {
+  half_reader h = {g, 0, 0};
+  memset(g_zc, 0, sizeof(g_zc));
+  for (size_t j = 0; j < n; ++j) {
+    for (;;) {
+      uint64_t p0 = half_pos(&h);
+      uint32_t u = next32(&h);
+      int i = (int)(u & 0xff);
+      int neg = (int)((u >> 8) & 1);
+      uint32_t r = u >> 9;
+      uint32_t ki; float wi, fi;
+      or_zig_table_f(0, i, &ki, &wi, &fi);
+      float x = (float)r * wi;
+      if (neg) x = -x;
+      if (r < ki) { g_zc[0]++; if (start) start[j] = p0; out[j] = x; break; }
+      if (i == 0) {
+        g_zc[3]++;
+        double a, b;
+        do {
+          double U1 = u24(next32(&h)), U2 = u24(next32(&h));
+          a = -or_cr_log(1.0 - U1) / OR_ZN_R;
+          b = -or_cr_log(1.0 - U2);
+        } while (!(b + b > a * a));
+        float v = (float)(OR_ZN_R + a);
+        if (start) start[j] = p0;
+        out[j] = neg ? -v : v;
+        break;
+      }
+      g_zc[1]++;
+      uint32_t k1; float w1, f1;
+      or_zig_table_f(0, i - 1, &k1, &w1, &f1);
+      float U = (float)u24(next32(&h));
+      float y = (f1 - fi) * U + fi;
+      double xd = (double)x;
+      if ((double)y < or_cr_exp(-0.5 * (xd * xd))) { if (start) start[j] = p0; out[j] = x; break; }
+      g_zc[2]++;
+    }
+  }
+}
+
+void or_fill_expf(or_gen* g, size_t n, float* out, uint64_t* start) {
+  half_reader h = {g, 0, 0};
+  memset(g_zc, 0, sizeof(g_zc));
+  for (size_t j = 0; j < n; ++j) {
+    for (;;) {
+      uint64_t p0 = half_pos(&h);
+      uint32_t u = next32(&h);
+      int i = (int)(u & 0xff);
+      uint32_t r = u >> 8;
+      uint32_t ki; float wi, fi;
+      or_zig_table_f(1, i, &ki, &wi, &fi);
+      float x = (float)r * wi;
+      if (r < ki) { g_zc[0]++; if (start) start[j] = p0; out[j] = x; break; }
+      if (i == 0) {
+        g_zc[3]++;
+        if (start) start[j] = p0;
+        out[j] = (float)(OR_ZE_R - or_cr_log(1.0 - u24(next32(&h))));
+        break;
+      }
+      g_zc[1]++;
+      uint32_t k1; float w1, f1;
+      or_zig_table_f(1, i - 1, &k1, &w1, &f1);
+      float U = (float)u24(next32(&h));
+      float y = (f1 - fi) * U + fi;
+      if ((double)y < or_cr_exp(-(double)x)) { if (start) start[j] = p0; out[j] = x; break; }
+      g_zc[2]++;
+    }
+  }
+}
+
 /* ---- gamma (Marsaglia & Tsang 2000; Sec. 3.1 "Gamma and related") ----
  * alpha >= 1: d = alpha - 1/3, c = 1/sqrt(9d); repeat: x ~ N(0,1) (ziggurat
  * above), v = 1 + c x; if v <= 0 draw again (no uniform consumed);

@@ -89,6 +89,14 @@ void or_fill_exp(or_gen* g, size_t n, double* out, uint64_t* start);
 int  or_fill_gamma(or_gen* g, size_t n, double alpha, double* out, uint64_t* start);
 int  or_fill_beta(or_gen* g, size_t n, double a, double b, double* out, uint64_t* start);
 
+/* float variants (suffix f): the stream read as 32-bit words, low half of
+ * each word first; `start` receives 32-bit word indices (2 word + half).
+ * The position after a fill is the next whole word. */
+void or_fill_uniformf(or_gen* g, size_t n, float* out);
+void or_fill_normalf(or_gen* g, size_t n, float* out, uint64_t* start);
+void or_fill_expf(or_gen* g, size_t n, float* out, uint64_t* start);
+int  or_zig_table_f(int which, int i, uint32_t* k, float* w, float* f);
+
 /* derived distributions (Table "continuous"): kinds and parameters p[]
  *   UNIF (a, b), NORMAL_MS (mu, sigma), LOGNORMAL (mu, sigma), EXP_SCALE (beta),
  *   GAMMA_SCALE (alpha, theta), CHI2 (nu), GUMBEL (mu, beta), PARETO (x_m, alpha),
