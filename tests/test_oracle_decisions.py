@@ -121,3 +121,82 @@ def test_walk_with_exact_decisions_matches_the_oracle(orc, dist, engine, seed):
     got, got_start = orc.fill(orc.gen(engine, seed), dist, N, with_start=True)
     assert np.array_equal(got_start, ref_start), dist
     assert np.array_equal(got.view(np.uint32 if halves else np.uint64), ref.view(np.uint32 if halves else np.uint64)), dist
+
+
+def _normal_one(words, tab):
+    """One standard normal of the double walk above, with exact decisions."""
+    k, w, f, R = tab
+    while True:
+        u = words.next()
+        i = u & 0xFF
+        r = (u >> 9) & (2 ** 52 - 1)
+        x = float(r) * w[i]
+        if (u >> 8) & 1:
+            x = -x
+        if r < k[i]:
+            return x
+        if i == 0:
+            while True:
+                a = -_log(1.0 - (words.next() >> 11) * 2.0 ** -53) / R
+                b = -_log(1.0 - (words.next() >> 11) * 2.0 ** -53)
+                if b + b > a * a:
+                    break
+            return -(R + a) if (u >> 8) & 1 else R + a
+        U = (words.next() >> 11) * 2.0 ** -53
+        y = (f[i - 1] - f[i]) * U + f[i]
+        if mp.mpf(y) < mp.exp(-mp.mpf(x * x) / 2):
+            return x
+
+
+def _gamma_one(words, tab, alpha):
+    """Marsaglia-Tsang (Sec. 3.1, Gamma), the log test decided on 40-digit
+    logs; the boost for alpha < 1 draws its uniform after the accepted
+    Gamma(alpha + 1)."""
+    s = alpha if alpha >= 1.0 else alpha + 1.0
+    d = s - 1.0 / 3.0
+    c = 1.0 / float(mp.sqrt(mp.mpf(9.0 * d)))
+    while True:
+        x = _normal_one(words, tab)
+        v = 1.0 + c * x
+        if v <= 0.0:
+            continue
+        v = v * v * v
+        U = (words.next() >> 11) * 2.0 ** -53
+        x2 = x * x
+        if U < 1.0 - 0.0331 * (x2 * x2) or _log(U) < 0.5 * x2 + d * ((1.0 - v) + _log(v)):
+            g = d * v
+            break
+    if alpha >= 1.0:
+        return g
+    U = (words.next() >> 11) * 2.0 ** -53
+    return g * float(mp.exp(mp.mpf(_log(U) / alpha))) if U > 0 else 0.0
+
+
+@pytest.mark.parametrize("alpha", [0.3, 2.5])
+def test_gamma_walk_with_exact_logs_matches_the_oracle(orc, alpha):
+    n = 4000
+    words = _Words(orc, "xoshiro256pp", 7, False)
+    tab = orc.zig_table(0)
+    tab = ([int(v) for v in tab[0]], tab[1], tab[2], tab[3])
+    ref = np.array([_gamma_one(words, tab, alpha) for _ in range(n)])
+    g = orc.gen("xoshiro256pp", 7)
+    got = orc.fill(g, "gamma", n, alpha)
+    assert int(g.pos) == words.p
+    assert np.array_equal(got.view(np.uint64), ref.view(np.uint64))
+
+
+def test_beta_walk_matches_the_oracle(orc):
+    """Beta (Table "continuous"): X ~ Gamma(a) drawn before Y ~ Gamma(b)."""
+    n = 2000
+    words = _Words(orc, "philox4x32_10", 3, False)
+    tab = orc.zig_table(0)
+    tab = ([int(v) for v in tab[0]], tab[1], tab[2], tab[3])
+    ref = []
+    for _ in range(n):
+        x = _gamma_one(words, tab, 2.0)
+        y = _gamma_one(words, tab, 5.0)
+        ref.append(x / (x + y))
+    g = orc.gen("philox4x32_10", 3)
+    got = orc.fill(g, "beta", n, 2.0, 5.0)
+    assert int(g.pos) == words.p
+    assert np.array_equal(got.view(np.uint64), np.array(ref).view(np.uint64))
