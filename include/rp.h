@@ -21,7 +21,11 @@
  * - Memory: `d_*` pointers are device memory owned by the caller; `h_*`
  *   pointers are host memory owned by the caller.  Output pointers must be
  *   8-byte aligned.  The library owns only immutable tables and an internal
- *   scratch pool (tile status words) that grows on demand.
+ *   scratch pool that grows on demand and is kept: tile status words, the
+ *   tail queue and, for bounded fills with frequent rejections, one parking
+ *   area per resident CTA.  Fills drawn as pairs of base variates (beta
+ *   and F with equal shapes, the skew normal) also allocate a temporary of
+ *   16 min(n, 2^26) bytes for the call and free it before returning.
  * - Streams: `cuda_stream` is a cudaStream_t (NULL = legacy default stream).
  *   Fill calls enqueue their kernels on it and return after they have
  *   completed (the call synchronises that stream once at the end to read
