@@ -103,6 +103,7 @@ def lib():
             "or_digamma": (dbl, [dbl]),
             "or_gamma_dzda": (dbl, [dbl, dbl]),
             "or_beta_dzdab": (None, [dbl, dbl, dbl, P(dbl), P(dbl)]),
+            "or_beta_dzdab_composed": (None, [dbl, dbl, dbl, dbl, P(dbl), P(dbl)]),
             "or_mvn_apply": (None, [i32, sz, vp, vp, vp, vp]),
             "or_mvn_grads": (None, [i32, sz, vp, vp, vp, vp]),
             "or_substream": (None, [P(Gen), i32, u64, u64]),
@@ -350,6 +351,22 @@ def beta_dzdab(z, a, b):
     da, db = ctypes.c_double(), ctypes.c_double()
     lib().or_beta_dzdab(float(z), float(a), float(b), ctypes.byref(da), ctypes.byref(db))
     return da.value, db.value
+
+
+def beta_dzdab_composed(x, y, a, b):
+    da, db = ctypes.c_double(), ctypes.c_double()
+    lib().or_beta_dzdab_composed(float(x), float(y), float(a), float(b), ctypes.byref(da), ctypes.byref(db))
+    return da.value, db.value
+
+
+def beta_pairs(g, n, a, b):
+    """The gamma pairs (X, Y) that the beta fill draws: X ~ Gamma(a) before
+    Y ~ Gamma(b), n times, from generator g."""
+    xy = np.empty((n, 2))
+    for j in range(n):
+        xy[j, 0] = fill(g, "gamma", 1, a)[0]
+        xy[j, 1] = fill(g, "gamma", 1, b)[0]
+    return xy
 
 
 def mvn_apply(mu, L, Z):

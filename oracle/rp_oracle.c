@@ -1182,6 +1182,18 @@ static double b_upper(double u, double um, void* c) {
   return g * fac;
 }
 
+/* Beta gradient through the gamma composition (the alternative to the
+ * implicit beta-CDF derivative): z = X / (X + Y) with X = Gamma(a) and
+ * Y = Gamma(b) each reparameterised by its own CDF, so
+ *   dz/da = Y / (X + Y)^2 dX/da,   dz/db = -X / (X + Y)^2 dY/db,
+ * dX/da and dY/db being the gamma implicit derivatives above. */
+void or_beta_dzdab_composed(double x, double y, double a, double b, double* dzda, double* dzdb) {
+  double s = x + y;
+  double s2 = s * s;
+  *dzda = y / s2 * or_gamma_dzda(x, a);
+  *dzdb = -x / s2 * or_gamma_dzda(y, b);
+}
+
 void or_beta_dzdab(double z, double a, double b, double* dzda, double* dzdb) {
   double pab = or_digamma(a + b);
   bctx k = {z, a, b, or_digamma(a) - pab, or_digamma(b) - pab, 0};

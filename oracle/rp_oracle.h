@@ -118,6 +118,8 @@ void or_zig_counts(uint64_t c[4]);
 double or_digamma(double x);
 double or_gamma_dzda(double z, double alpha);
 void   or_beta_dzdab(double z, double a, double b, double* dzda, double* dzdb);
+/* the same gradient through the gamma pair (x, y) that made z = x / (x + y) */
+void   or_beta_dzdab_composed(double x, double y, double a, double b, double* dzda, double* dzdb);
 
 /* ---- multivariate normal X = mu + L z (Sec. 3.1, mvn).  Row-major n x d
  *      X and Z, L lower-triangular d x d row-major.  Compensated dot

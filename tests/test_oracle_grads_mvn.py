@@ -120,3 +120,29 @@ def test_substream_recipe(orc):
     p = orc.substream("philox4x32_10", 99, 17)
     q = orc.gen("philox4x32_10", 99)
     assert p.s[0] == q.s[0] and p.s[1] == q.s[1] and p.s[2] == 17
+
+
+@pytest.mark.parametrize("ab", [(2.0, 5.0), (0.5, 0.5), (0.7, 3.0)])
+def test_beta_gradient_through_the_gamma_pair_is_unbiased(orc, ab):
+    """The composition estimator dz/da = Y/(X+Y)^2 dX/da, dz/db = -X/(X+Y)^2 dY/db
+    on the beta fill's own gamma pairs: its mean is d/da E[z] = b/(a+b)^2 and
+    d/db E[z] = -a/(a+b)^2, and E[2 z dz/da] is d/da E[z^2] with
+    E[z^2] = a(a+1)/((a+b)(a+b+1)); the implicit beta-CDF estimator on the
+    same z has the same means (both within 5 standard errors)."""
+    a, b = ab
+    n = 20_000
+    xy = orc.beta_pairs(orc.gen("xoshiro256pp", 5), n, a, b)
+    z = xy[:, 0] / (xy[:, 0] + xy[:, 1])
+    zb = orc.fill(orc.gen("xoshiro256pp", 5), "beta", n, a, b)
+    assert np.array_equal(z.view(np.uint64), zb.view(np.uint64))   # the pairs are the fill's draws
+    d = np.array([orc.beta_dzdab_composed(x, y, a, b) for x, y in xy])
+    se = d.std(axis=0) / np.sqrt(n)
+    assert abs(d[:, 0].mean() - b / (a + b) ** 2) < 5 * se[0]
+    assert abs(d[:, 1].mean() + a / (a + b) ** 2) < 5 * se[1]
+    m2 = lambda aa: aa * (aa + 1) / ((aa + b) * (aa + b + 1))
+    dm2 = float(mp.diff(m2, mp.mpf(a)))
+    v = 2 * z * d[:, 0]
+    assert abs(v.mean() - dm2) < 5 * v.std() / np.sqrt(n)
+    imp = np.array([orc.beta_dzdab(zz, a, b) for zz in z])
+    diff = d - imp
+    assert np.all(np.abs(diff.mean(axis=0)) < 5 * diff.std(axis=0) / np.sqrt(n))
