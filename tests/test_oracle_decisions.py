@@ -11,7 +11,6 @@ import mpmath as mp
 import numpy as np
 import pytest
 
-mp.mp.dps = 40
 N = 20_000
 
 
@@ -35,7 +34,21 @@ class _Words:
 
 
 def _log(x):
-    return float(mp.log(mp.mpf(x)))   # rounded to nearest from 40 digits
+    with mp.workdps(40):
+        return float(mp.log(mp.mpf(x)))   # rounded to nearest from 40 digits
+
+
+def _below_exp(y, t):
+    """y < exp(t) for doubles y and t (t exact as given), on 40 digits."""
+    with mp.workdps(40):
+        return mp.mpf(y) < mp.exp(mp.mpf(t))
+
+
+def _below_exp_half_square(y, x):
+    """y < exp(-x^2 / 2) with x^2 exact, on 40 digits."""
+    with mp.workdps(40):
+        xm = mp.mpf(float(x))
+        return mp.mpf(float(y)) < mp.exp(-xm * xm / 2)
 
 
 def _walk_double(orc, words, normal):
@@ -68,7 +81,7 @@ def _walk_double(orc, words, normal):
         U = (words.next() >> 11) * 2.0 ** -53
         y = (f[i - 1] - f[i]) * U + f[i]
         t = -0.5 * (x * x) if normal else -x
-        if mp.mpf(y) < mp.exp(mp.mpf(t)):
+        if _below_exp(y, t):
             out.append(x), start.append(p0)
     return np.array(out), np.array(start, np.uint64)
 
@@ -104,9 +117,7 @@ def _walk_float(orc, words, normal):
             continue
         U = f32((words.next() >> 8) * 2.0 ** -24)
         y = (f[i - 1] - f[i]) * U + f[i]
-        xm = mp.mpf(float(x))
-        t = -xm * xm / 2 if normal else -xm
-        if mp.mpf(float(y)) < mp.exp(t):
+        if _below_exp_half_square(y, x) if normal else _below_exp(float(y), -float(x)):
             out.append(x), start.append(p0)
     return np.array(out, np.float32), np.array(start, np.uint64)
 
@@ -144,7 +155,7 @@ def _normal_one(words, tab):
             return -(R + a) if (u >> 8) & 1 else R + a
         U = (words.next() >> 11) * 2.0 ** -53
         y = (f[i - 1] - f[i]) * U + f[i]
-        if mp.mpf(y) < mp.exp(-mp.mpf(x * x) / 2):
+        if _below_exp(y, -0.5 * (x * x)):
             return x
 
 
@@ -154,7 +165,8 @@ def _gamma_one(words, tab, alpha):
     Gamma(alpha + 1)."""
     s = alpha if alpha >= 1.0 else alpha + 1.0
     d = s - 1.0 / 3.0
-    c = 1.0 / float(mp.sqrt(mp.mpf(9.0 * d)))
+    with mp.workdps(40):
+        c = 1.0 / float(mp.sqrt(mp.mpf(9.0 * d)))
     while True:
         x = _normal_one(words, tab)
         v = 1.0 + c * x
@@ -169,7 +181,10 @@ def _gamma_one(words, tab, alpha):
     if alpha >= 1.0:
         return g
     U = (words.next() >> 11) * 2.0 ** -53
-    return g * float(mp.exp(mp.mpf(_log(U) / alpha))) if U > 0 else 0.0
+    if U == 0:
+        return 0.0
+    with mp.workdps(40):
+        return g * float(mp.exp(mp.mpf(_log(U) / alpha)))
 
 
 @pytest.mark.parametrize("alpha", [0.3, 2.5])

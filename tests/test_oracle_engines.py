@@ -5,6 +5,8 @@ statistics.  Philox4x32-10 is pinned bit-for-bit against cuRAND in the GPU
 suite (tests/test_gpu_engines.py); on the CPU only its structural properties
 are checked here."""
 import ctypes
+import json
+import os
 
 import numpy as np
 import pytest
@@ -13,6 +15,19 @@ from numpy.random import PCG64DXSM, SeedSequence
 
 def _rng():
     return np.random.default_rng(20240601)
+
+
+def _gold_engines():
+    with open(os.path.join(os.path.dirname(__file__), "golden", "paper_engines.json")) as f:
+        return json.load(f)
+
+
+def _table_period(engine):
+    """Period printed in Table "engines", as an integer."""
+    form = _gold_engines()[engine]["period_log2_form"]
+    base, _, rest = form.partition("^")
+    exp, _, minus = rest.partition("-")
+    return int(base) ** int(exp) - (int(minus) if minus else 0)
 
 
 # ------------------------------------------------------------------ seeding
@@ -91,11 +106,22 @@ def test_xoshiro_charpoly_primitive_shape(orc):
             e >>= 1
         return r
 
-    assert powmod(2 ** 256 - 1) == 1
-    # the period is not a proper divisor (prime factors of 2^256-1 up to the
-    # Fermat primes): x^((2^256-1)/q) != 1
-    for q in (3, 5, 17, 257, 641, 65537, 274177, 6700417):
-        assert powmod((2 ** 256 - 1) // q) != 1
+    period = _table_period("xoshiro256pp")
+    assert period == 2 ** 256 - 1 and _table_period("xoshiro256ss") == period
+    assert powmod(period) == 1
+    # x has order exactly 2^256 - 1 (p is primitive): x^(P/q) != 1 for every
+    # prime q of P = 2^256 - 1 = F0 F1 ... F7 (Fermat numbers); the list is
+    # checked to be the complete factorisation into primes
+    primes = (3, 5, 17, 257, 65537, 641, 6700417, 274177, 67280421310721,
+              59649589127497217, 5704689200685129054721)
+    sympy = pytest.importorskip("sympy")
+    prod = 1
+    for q in primes:
+        assert sympy.isprime(q)
+        prod *= q
+    assert prod == period
+    for q in primes:
+        assert powmod(period // q) != 1
 
 
 def test_xoshiro_jump_equals_steps(orc):
@@ -256,3 +282,21 @@ def test_xoshiro256ss_bit_balance(orc):
     w = orc.next_words(orc.gen("xoshiro256ss", 2024), 1 << 18)
     bits = np.unpackbits(w.view(np.uint8)).reshape(-1, 64).mean(axis=0)
     assert np.all(np.abs(bits - 0.5) < 6 * 0.5 / np.sqrt(len(w)))
+
+
+def test_engine_table_state_words_and_pcg_period(orc):
+    """Table "engines" (golden): xoshiro and PCG64-DXSM keep 4 state words
+    (the oracle's and the library's layout); PCG64-DXSM has period 2^128 (a
+    jump by half the period moves the state, two of them bring it back).
+    Philox-4x64 is printed with 6 words (a 256-bit counter and a 128-bit
+    key); this library keeps the counter's upper 128 bits at zero, so its
+    state is 4 words and a stream has 2^130 words."""
+    gold = _gold_engines()
+    for eng in ("xoshiro256pp", "xoshiro256ss", "pcg64dxsm"):
+        assert gold[eng]["state_words"] == len(orc.state_words(orc.gen(eng, 1)))
+    assert gold["philox4x64_10"]["state_words"] == 6
+    period = _table_period("pcg64dxsm")
+    s0 = orc.state_words(orc.gen("pcg64dxsm", 99))
+    half = orc.pcg_advance(s0, period // 2)
+    assert half[:2] != s0[:2] and half[2:] == s0[2:]
+    assert orc.pcg_advance(half, period // 2) == s0
