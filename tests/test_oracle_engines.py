@@ -33,10 +33,10 @@ def _table_period(engine):
 # ------------------------------------------------------------------ seeding
 def test_seedseq_matches_numpy(orc):
     """Sec. 2.3: seed + spawn key -> 128-bit pool -> state words; reading =
-    NumPy SeedSequence semantics.  2000 random (seed, key) pairs plus edges."""
+    NumPy SeedSequence semantics.  10^4 random (seed, key) pairs plus edges."""
     rng = _rng()
-    seeds = [0, 1, 2 ** 32 - 1, 2 ** 32, 2 ** 64 - 1] + [int(x) for x in rng.integers(0, 2 ** 63, 1000)]
-    keys = [None, 0, 1, 2 ** 32, 2 ** 64 - 1] + [int(x) for x in rng.integers(0, 2 ** 40, 1000)]
+    seeds = [0, 1, 2 ** 32 - 1, 2 ** 32, 2 ** 64 - 1] + [int(x) for x in rng.integers(0, 2 ** 63, 10_000)]
+    keys = [None, 0, 1, 2 ** 32, 2 ** 64 - 1] + [int(x) for x in rng.integers(0, 2 ** 40, 10_000)]
     for i, seed in enumerate(seeds):
         key = keys[i % len(keys)]
         ss = SeedSequence(seed) if key is None else SeedSequence(seed, spawn_key=(key,))
@@ -56,14 +56,14 @@ def test_xoshiro_seed_is_seedseq_words(orc):
 @pytest.mark.parametrize("seed,key", [(0, None), (2024, None), (12345, 3), (2 ** 63 + 11, None)])
 def test_pcg64dxsm_matches_numpy(orc, seed, key):
     """Sec. 2.2 / Sec. 5.1: pcg64 is validated against NumPy.  Seeded state,
-    increment and the first 100k words must be identical."""
+    increment and the first 10^6 words must be identical."""
     ss = SeedSequence(seed) if key is None else SeedSequence(seed, spawn_key=(key,))
     bg = PCG64DXSM(ss)
     g = orc.gen("pcg64dxsm", seed, key)
     s = orc.state_words(g)
     st = bg.state["state"]
     assert st["state"] == (s[0] << 64 | s[1]) and st["inc"] == (s[2] << 64 | s[3])
-    assert np.array_equal(bg.random_raw(100_000), orc.next_words(g, 100_000))
+    assert np.array_equal(bg.random_raw(1_000_000), orc.next_words(g, 1_000_000))
 
 
 def test_pcg64dxsm_advance_matches_numpy(orc):
