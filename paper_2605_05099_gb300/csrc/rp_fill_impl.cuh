@@ -447,7 +447,7 @@ __global__ void __launch_bounds__(NT) k_onepw(FillArgs a) {
 // no segment and the previous thread's walk continues to the next chunk's
 // merge point (same rule, same words, so both threads agree).
 constexpr int kE = 12;
-constexpr int kSkipMax = 8;  // chunks a walk may cross to find a merge point
+constexpr int kSkipMax = 64;  // chunks a walk may cross to find a merge point
 constexpr int kRecW = 8;     // record words per staged variate (7 used + tail flag)
 constexpr int kRecS = 4;     // staged records per lane
 

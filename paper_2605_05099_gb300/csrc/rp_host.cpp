@@ -635,8 +635,8 @@ rp_status run_fill_state_locked(int engine, const u64 s_in[4], u64* pos, size_t 
       const bool merge = dist == rp::D_BETA || dist == rp::D_GAMMA || dist == rp::D_T;
       snprintf(buf, sizeof buf, "device check failed (bits 0x%x, tile %llu)%s", c.err, (unsigned long long)c.err_info,
                (c.err & rp::E_NOSYNC) && merge
-                   ? ": no merge point within 9 chunks; the two gamma shapes of this beta or F fill consume words "
-                     "alike too often (shapes close to each other, or both large)"
+                   ? ": no merge point within the 64 chunks a walk may cross; the two gamma shapes of this beta "
+                     "or F fill consume words alike too often (shapes nearly equal, or both large and close)"
                    : "");
       return fail(c.err & rp::E_TIMEOUT ? RP_ERR_TIMEOUT : RP_ERR_INTERNAL, buf);
     }
