@@ -47,7 +47,12 @@ struct LeanNormalT {
   static constexpr bool kSync = true;
   static constexpr int kWhich = 0;
   static constexpr int kKShift = 20;
-  static constexpr int kG = 8, kS = 24;    // tails may overhang a seam by several words
+  // A tail of 1 + 2k words that starts just before a seam overhangs it by up
+  // to 2k words, so sync points start at 16: an overhang past 16 needs
+  // k >= 9 (probability 0.062^8 per tail), against k >= 5 (1.5e-5) for 8,
+  // which a 2^28-variate fill met about once in 170.  kG + kS stays 32: the
+  // walk into the next chunk fits the one overhang mask word.
+  static constexpr int kG = 16, kS = 16;
   static constexpr bool kTailPairs = true;
   typedef double out_t;
   __device__ static __forceinline__ bool fast_exact(u64 u, const ZigDev& z) { return ((u >> 9) & M52) < z.k[u & 0xff]; }

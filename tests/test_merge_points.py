@@ -1,4 +1,6 @@
-"""Host check of the merge-point seams of the gamma, beta and t kernels
+"""Host checks of the chunk seams of the fill kernels.
+
+Merge points of the gamma, beta and t kernels
 (Sec. 3.1 samplers; the seams are this library's, not the paper's).  A
 chunk's merge point is found by starting the sampler at each of the first
 12 word offsets of the chunk (a hypothesis that a variate starts there),
@@ -10,7 +12,13 @@ lengths (the words one variate consumes from any start word) and checked
 against the true chain of the sequential sampler, for the shapes the
 library runs on these kernels: every chunk of the kernel's length (2048 or
 4096 words) has a merge point, and every merge point lies on the true
-chain."""
+chain.
+
+Sync points of the ziggurat normal kernel: the first position s >= G of a
+chunk such that every candidate starting in [0, s) ends by s.  A true-chain
+tail that starts just before the seam and overhangs it past s would leave
+the previous chunk's walk mid-candidate there; the GPU fills of the same
+streams are in the GPU suite."""
 import numpy as np
 import pytest
 
@@ -64,3 +72,56 @@ def test_merge_points_exist_and_lie_on_the_true_chain(orc, dist, params, chunk):
         q = _merge_point(length, k * window, window)
         assert q >= KE - 1, (dist, params, k)
         assert k * window + q in bounds, (dist, params, k, q)
+
+
+# Normal ziggurat tails that consume 11 words (four rejected pairs), found by
+# scanning the oracle's xoshiro256++ seed-2024 stream: word index of the
+# tail's first word.  A fill starting 383 words before one puts it on the
+# last word of a 384-word chunk, across the seam.
+LONG_TAILS = (695813604, 808170845, 1021565374)
+
+
+def _candidate_len(orc, words, q, tab):
+    """Words one normal candidate starting at q consumes (Sec. 3.1): 1 when
+    fast, 2 for a wedge, 1 + 2k for a tail accepted at its k-th pair."""
+    import mpmath as mp
+    k, w, f, R = tab
+    u = int(words[q])
+    i, r = u & 0xFF, (u >> 9) & (2 ** 52 - 1)
+    if r < int(k[i]):
+        return 1
+    if i:
+        return 2
+    j = q + 1
+    while True:
+        with mp.workdps(40):
+            a = -float(mp.log(1 - mp.mpf((int(words[j]) >> 11) * 2.0 ** -53))) / R
+            b = -float(mp.log(1 - mp.mpf((int(words[j + 1]) >> 11) * 2.0 ** -53)))
+        j += 2
+        if b + b > a * a:
+            return j - q
+
+
+def _sync_point(orc, words, c, g, s_win, tab):
+    reach = 0
+    for q in range(g + s_win):
+        if q >= g and reach <= q:
+            return q
+        reach = max(reach, q + _candidate_len(orc, words, c + q, tab))
+    return -1
+
+
+@pytest.mark.parametrize("w", LONG_TAILS)
+def test_normal_sync_points_clear_an_overhanging_tail(orc, w):
+    """With sync points from 16 on, the chunk after the seam starts its
+    chain after the 11-word tail has ended; from 8 on (the earlier rule) it
+    would start inside it."""
+    chunk, pos = 384, w - 383
+    words = orc.next_words(orc.gen("xoshiro256pp", 2024, pos=pos), 1200)
+    tab = orc.zig_table(0)
+    assert _candidate_len(orc, words, chunk - 1, tab) == 11
+    _, start = orc.fill(orc.gen("xoshiro256pp", 2024, pos=pos), "normal", 600, with_start=True)
+    assert w in set(int(x) for x in start)   # on the true chain of a fill from pos
+    tail_end = chunk - 1 + 11 - chunk        # relative to the next chunk
+    assert _sync_point(orc, words, chunk, 16, 16, tab) >= tail_end
+    assert _sync_point(orc, words, chunk, 8, 24, tab) < tail_end
