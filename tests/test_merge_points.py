@@ -25,6 +25,13 @@ import pytest
 KE = 12   # entry offsets tried per chunk
 
 
+def _one(orc, g, dist, params):
+    if dist in orc.DERIVED:
+        orc.fill_derived(g, dist, 1, *params)
+    else:
+        orc.fill(g, dist, 1, *params)
+
+
 def _length_fn(orc, dist, params, seed):
     cache = {}
 
@@ -32,7 +39,7 @@ def _length_fn(orc, dist, params, seed):
         v = cache.get(q)
         if v is None:
             g = orc.gen("philox4x32_10", seed, pos=q)   # counter-based: any start word directly
-            orc.fill(g, dist, 1, *params)
+            _one(orc, g, dist, params)
             v = cache[q] = int(g.pos) - q
         return v
     return length
@@ -59,6 +66,7 @@ def _merge_point(length, c, limit):
 @pytest.mark.parametrize("dist,params,chunk", [
     ("gamma", (2.5,), 2048), ("gamma", (30.0,), 2048), ("gamma", (0.3,), 4096),
     ("beta", (2.0, 5.0), 4096), ("beta", (2.5, 3.5), 4096), ("beta", (3.0, 0.7), 4096),
+    ("t", (3.0,), 4096), ("t", (100.0,), 4096),
 ])
 def test_merge_points_exist_and_lie_on_the_true_chain(orc, dist, params, chunk):
     seed, nchunks, window = 7, 8, chunk
@@ -66,7 +74,7 @@ def test_merge_points_exist_and_lie_on_the_true_chain(orc, dist, params, chunk):
     g = orc.gen("philox4x32_10", seed)
     bounds = {0}
     while max(bounds) < window * (nchunks + 1):
-        orc.fill(g, dist, 1, *params)
+        _one(orc, g, dist, params)
         bounds.add(int(g.pos))
     for k in range(1, nchunks + 1):
         q = _merge_point(length, k * window, window)
