@@ -192,3 +192,34 @@ def test_binding_refuses_bad_outputs_before_the_library(rp):
         rp.rp_fill_derived("xoshiro256pp", 1, rp.NO_STREAM, 0, "no_such_law", (1.0,), cpu)
     with pytest.raises(KeyError):
         rp.rp_seed_state("no_such_engine", 1)
+
+
+def test_last_error_is_per_host_thread(rp):
+    """rp_last_error returns the calling thread's last failure (the header's
+    convention, after the per-generator error string of Sec. 2.1): two
+    threads that fail differently each read back their own message."""
+    import ctypes
+    import threading
+    L = rp.lib()
+    got = {}
+    barrier = threading.Barrier(2)
+
+    def fail_engine():
+        pos = ctypes.c_uint64(0)
+        assert L.rp_fill_normal(9, 1, rp.NO_STREAM, ctypes.byref(pos), 10, ctypes.c_void_p(0x1000), None) == -3
+        barrier.wait()
+        got["engine"] = rp.rp_last_error()
+
+    def fail_param():
+        pos = ctypes.c_uint64(0)
+        assert L.rp_fill_gamma(1, 1, rp.NO_STREAM, ctypes.byref(pos), 10, -1.0, ctypes.c_void_p(0x1000), None) == -2
+        barrier.wait()
+        got["param"] = rp.rp_last_error()
+
+    ts = [threading.Thread(target=fail_engine), threading.Thread(target=fail_param)]
+    for t in ts:
+        t.start()
+    for t in ts:
+        t.join()
+    assert got["engine"] == "unknown engine id 9"
+    assert got["param"] == "gamma shape must be positive and finite"
