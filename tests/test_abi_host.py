@@ -223,3 +223,34 @@ def test_last_error_is_per_host_thread(rp):
         t.join()
     assert got["engine"] == "unknown engine id 9"
     assert got["param"] == "gamma shape must be positive and finite"
+
+
+def _fnv1a64(data):
+    """FNV-1a, 64-bit (offset basis 0xcbf29ce484222325, prime 0x100000001b3)."""
+    h = 0xCBF29CE484222325
+    for b in data:
+        h = ((h ^ b) * 0x100000001B3) & (2 ** 64 - 1)
+    return h
+
+
+def _state_buf(magic=b"RPST", version=1, engine=1, words=(1, 2, 3, 4), pos=5, reserved=0):
+    import struct
+    head = magic + struct.pack("<HH4QQQ", version, engine, *words, pos, reserved)
+    return head + struct.pack("<Q", _fnv1a64(head))
+
+
+def test_checkpoint_layout_is_the_documented_one(rp):
+    """The 64-byte layout of rp.h, written here byte by byte with an
+    independent FNV-1a: a library-written buffer equals it, and buffers with
+    a valid checksum are still refused for a wrong magic or version, an
+    unknown engine, nonzero reserved bytes or an all-zero xoshiro state."""
+    words = rp.rp_seed_state("xoshiro256ss", 2024, 3)
+    assert rp.rp_state_serialize("xoshiro256ss", words, 77) == _state_buf(engine=5, words=words, pos=77)
+    assert rp.rp_state_deserialize(_state_buf()) == (1, [1, 2, 3, 4], 5)
+    for bad in (_state_buf(magic=b"RPSX"), _state_buf(version=2), _state_buf(engine=6), _state_buf(engine=0),
+                _state_buf(reserved=1), _state_buf(engine=1, words=(0, 0, 0, 0)),
+                _state_buf(engine=5, words=(0, 0, 0, 0))):
+        with pytest.raises(rp.RPError):
+            rp.rp_state_deserialize(bad)
+    # PCG and Philox states may be all zero
+    assert rp.rp_state_deserialize(_state_buf(engine=3, words=(0, 0, 0, 0)))[0] == 3
