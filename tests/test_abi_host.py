@@ -254,3 +254,34 @@ def test_checkpoint_layout_is_the_documented_one(rp):
             rp.rp_state_deserialize(bad)
     # PCG and Philox states may be all zero
     assert rp.rp_state_deserialize(_state_buf(engine=3, words=(0, 0, 0, 0)))[0] == 3
+
+
+def test_gradient_and_mvn_argument_errors_without_device(rp):
+    """Gradients and the MVN entry points check their arguments before any
+    device work: bad shapes and missing pointers are refused, and n = 0
+    returns zero sums without touching the device."""
+    import ctypes
+    L = rp.lib()
+    dummy = ctypes.c_void_p(0x1000)
+    h = ctypes.c_double(7.0)
+    h2 = ctypes.c_double(7.0)
+    assert L.rp_gamma_grad(dummy, ctypes.c_double(0.0), dummy, 4, None, ctypes.byref(h), None) == -2
+    assert L.rp_gamma_grad(dummy, ctypes.c_double(float("inf")), dummy, 4, None, ctypes.byref(h), None) == -2
+    assert L.rp_gamma_grad(None, ctypes.c_double(2.0), dummy, 4, None, ctypes.byref(h), None) == -1
+    assert L.rp_gamma_grad(dummy, ctypes.c_double(2.0), dummy, 4, None, None, None) == -1
+    assert L.rp_gamma_grad(dummy, ctypes.c_double(2.0), None, 4, None, None, None) == -1
+    assert L.rp_gamma_grad(None, ctypes.c_double(2.0), None, 0, None, ctypes.byref(h), None) == 0 and h.value == 0.0
+    assert L.rp_beta_grad(dummy, ctypes.c_double(-1.0), ctypes.c_double(2.0), dummy, 4, None, None,
+                          ctypes.byref(h), ctypes.byref(h2), None) == -2
+    assert L.rp_beta_grad(dummy, ctypes.c_double(1.0), ctypes.c_double(2.0), dummy, 4, None, None,
+                          ctypes.byref(h), None, None) == -1
+    h.value = h2.value = 7.0
+    assert L.rp_beta_grad(None, ctypes.c_double(1.0), ctypes.c_double(2.0), None, 0, None, None,
+                          ctypes.byref(h), ctypes.byref(h2), None) == 0 and h.value == 0.0 and h2.value == 0.0
+    pos = ctypes.c_uint64(11)
+    assert L.rp_mvn(1, 3, rp.NO_STREAM, ctypes.byref(pos), 0, 8, dummy, dummy, dummy, dummy, None) == -2
+    assert L.rp_mvn(1, 3, rp.NO_STREAM, None, 4, 8, dummy, dummy, dummy, dummy, None) == -1
+    assert L.rp_mvn(1, 3, rp.NO_STREAM, ctypes.byref(pos), 4, 8, None, dummy, dummy, dummy, None) == -1
+    assert L.rp_mvn(1, 3, rp.NO_STREAM, ctypes.byref(pos), 4, 0, None, None, None, None, None) == 0 and pos.value == 11
+    assert L.rp_mvn_grads(0, 8, dummy, dummy, dummy, dummy, None) == -2
+    assert L.rp_mvn_grads(4, 8, None, dummy, dummy, dummy, None) == -1
