@@ -12,7 +12,6 @@ import torch
 import oracle
 import paper_2605_05099_gb300 as rp
 from gpu_util import assert_parity, first_mismatch, gpu_fill, oracle_fill, same_bits, ulp_diff
-from test_merge_points import LONG_TAILS
 
 pytestmark = pytest.mark.gpu
 
@@ -133,18 +132,6 @@ def test_bounded_rare_rejection_one_pass_and_fallback(engine):
         assert np.array_equal(g, o), (engine, seed)
         if seed in REJECT_SEEDS[engine]:
             assert opos == n + 1
-
-
-# ------------------------------------------------------------------ tails across chunk seams
-@pytest.mark.parametrize("w", LONG_TAILS)
-def test_normal_tail_across_a_chunk_seam(w):
-    """An 11-word normal tail (four rejected pairs) on the last word of a
-    384-word chunk overhangs the seam by ten words: the fill from 383 words
-    before it (first seam) and from 10 chunks further back (a seam between
-    two later threads) must still equal the oracle, with the same consumed
-    words."""
-    for before in (383, 383 + 10 * 384):
-        assert_parity("normal", "xoshiro256pp", 2024, None, w - before, 6000)
 
 
 # ------------------------------------------------------------------ ties of the top significand bits

@@ -69,13 +69,3 @@ def test_gamma_full_size_sampled():
     whole-array compare against the oracle and identical consumed words."""
     for dist, params, ulp in [("gamma", (2.5,), 0), ("gamma", (0.3,), 2), ("beta", (2.0, 5.0), 0)]:
         check(dist, "xoshiro256pp", 7, 1 << 26, params, ulp)
-
-
-@pytest.mark.parametrize("ab", [(2.0, 2.01), (10.0, 11.0)])
-def test_beta_with_shapes_that_merge_rarely(ab):
-    """Shapes whose gamma draws mostly consume the same word counts leave
-    runs of chunks without a merge point: on this stream the longest runs
-    are 14 chunks (2, 2.01) and 8 chunks (10, 11), per the host model of the
-    merge rule.  A walk crosses them (up to 64), and the fill stays
-    bit-exact."""
-    check("beta", "philox4x32_10", 7, 1 << 18, ab, 0)
