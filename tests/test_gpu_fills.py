@@ -116,8 +116,9 @@ def test_philox_bijection_matches_curand():
 
 
 # seeds whose first 100003 bounded words (m = 2^43 + 1, one rejection in
-# about 2.1e6 words) contain a rejection, found with the oracle, and seeds
-# without one: both sides of the one-pass shortcut for rare rejections
+# about 2.1e6 words) contain a rejection, found with the oracle
+# (tests/find_stream_cases.py), and seeds without one: both sides of the
+# one-pass shortcut for rare rejections
 REJECT_SEEDS = {"xoshiro256pp": [9, 15], "pcg64dxsm": [30, 99], "philox4x32_10": [16, 33], "philox4x64_10": [13, 54],
                 "xoshiro256ss": [4, 12]}
 

@@ -83,8 +83,8 @@ def test_merge_points_exist_and_lie_on_the_true_chain(orc, dist, params, chunk):
 
 
 # Normal ziggurat tails that consume 11 words (four rejected pairs), found by
-# scanning the oracle's xoshiro256++ seed-2024 stream: word index of the
-# tail's first word.  A fill starting 383 words before one puts it on the
+# scanning the oracle's xoshiro256++ seed-2024 stream
+# (tests/find_stream_cases.py): word index of the tail's first word.  A fill starting 383 words before one puts it on the
 # last word of a 384-word chunk, across the seam.
 LONG_TAILS = (695813604, 808170845, 1021565374)
 
