@@ -172,12 +172,18 @@ struct SampUniform {
 };
 // 52-bit uniform, the paper's default (Sec. 3.1, method 2): the word's top
 // 52 bits as the fraction of a double in [1, 2), minus 1 (exact).
+// floor(u / 2^12) 2^-52 is exact and is assembled with integer operations,
+// as u53_bits does (no FP64 instruction).
 struct SampUniform52 {
   static constexpr bool kOnePerWord = true;
   static constexpr bool kCheckReject = false;
   typedef double out_t;
   __device__ static __forceinline__ double value1(u64 u, const SampArgs&) {
-    return __dsub_rn(__longlong_as_double((long long)((u >> 12) | 0x3ff0000000000000ull)), 1.0);
+    const u64 v = u >> 12;
+    if (v == 0) return 0.0;
+    const int lz = __clzll(v);                  // >= 12
+    const u64 mt = v << (lz - 11);              // in [2^52, 2^53)
+    return __longlong_as_double((long long)((((u64)(1033 - lz)) << 52) + mt));
   }
 };
 // Uniform base of a derived distribution (unif, Gumbel).
@@ -197,6 +203,26 @@ struct SampBoundedOne {
   static constexpr bool kCheckReject = true;
   typedef u64 out_t;
   __device__ static __forceinline__ u64 value1(u64 u, const SampArgs& a) { return __umul64hi(u, a.m); }
+  // hi(u m) and, in lo, the low 64 bits that decide the rejection
+  __device__ static __forceinline__ u64 value_lo(u64 u, const SampArgs& a, u64& lo) {
+    lo = u * a.m;
+    return __umul64hi(u, a.m);
+  }
+};
+// The same for m < 2^32: u m from two 32 x 32 -> 64 products (u = uh 2^32 +
+// ul: u m = uh m 2^32 + ul m), instead of a full 64 x 64 -> 128 product.
+struct SampBoundedOne32 {
+  static constexpr bool kOnePerWord = true;
+  static constexpr bool kCheckReject = true;
+  typedef u64 out_t;
+  __device__ static __forceinline__ u64 value_lo(u64 u, const SampArgs& a, u64& lo) {
+    const unsigned m = (unsigned)a.m;
+    const u64 pl = (u64)(unsigned)u * m, ph = (u64)(unsigned)(u >> 32) * m;
+    const u64 mid = (pl >> 32) + (unsigned)ph;   // < 2^33
+    lo = (mid << 32) | (unsigned)pl;
+    return (ph >> 32) + (mid >> 32);
+  }
+  __device__ static __forceinline__ u64 value1(u64 u, const SampArgs& a) { u64 lo; return value_lo(u, a, lo); }
 };
 
 // Values of ziggurat tail outputs (FP64 libm log, within 2 ulp of the
@@ -384,10 +410,10 @@ __device__ __forceinline__ bool batch_claim(const BatchArgs& b, FillArgs& fa, Ba
 // ------------------------------------------------------------------ kernels
 // One tile of a one-word-per-variate fill: chunk words stream straight to
 // the output through the warp's staging rows.
-template <int NT, int C, class E, class S>
-__device__ __forceinline__ void onepw_tile(const FillArgs& a, u64 k, const E& e, u64* stage_w) {
-  static_assert(kStage % 2 == 0 && C % 2 == 0, "rows are written in pairs of words");
-  constexpr int T = NT * C;
+template <int NT, class E, class S>
+__device__ __forceinline__ void onepw_tile(const FillArgs& a, u64 k, const E& e, u64* stage_w, const int C) {
+  static_assert(kStage % 2 == 0, "rows are written in pairs of words");
+  const u64 T = (u64)NT * C;
   const int t = threadIdx.x, lane = t & 31;
   u64* out = (u64*)a.out;
   const bool wide = ((unsigned long long)a.out & 15) == 0;
@@ -403,14 +429,18 @@ __device__ __forceinline__ void onepw_tile(const FillArgs& a, u64 k, const E& e,
       take_words<E, W>(g, u);
 #pragma unroll
       for (int i = 0; i < W; i += 2) {
-        *reinterpret_cast<ulonglong2*>(row + j + i) =
-            make_ulonglong2(as_bits(S::value1(u[i], a.sp)), as_bits(S::value1(u[i + 1], a.sp)));
         if constexpr (S::kCheckReject) {
+          u64 lo[2], v[2];
 #pragma unroll
           for (int k = 0; k < 2; ++k) {
+            v[k] = S::value_lo(u[i + k], a.sp, lo[k]);
             const u64 p = base + j0 + j + i + k;
-            if (u[i + k] * a.sp.m < a.sp.thresh && p < a.n) atomicMin(&a.ctrl->first_reject, p);
+            if (lo[k] < a.sp.thresh && p < a.n) atomicMin(&a.ctrl->first_reject, p);
           }
+          *reinterpret_cast<ulonglong2*>(row + j + i) = make_ulonglong2(v[0], v[1]);
+        } else {
+          *reinterpret_cast<ulonglong2*>(row + j + i) =
+              make_ulonglong2(as_bits(S::value1(u[i], a.sp)), as_bits(S::value1(u[i + 1], a.sp)));
         }
       }
     }
@@ -421,17 +451,17 @@ __device__ __forceinline__ void onepw_tile(const FillArgs& a, u64 k, const E& e,
   }
 }
 
-template <int NT, int C, class E, class S>
+// One tile per CTA: the host sizes the chunk (a multiple of kStage, in
+// a.eng.chunk_words) so that the grid covers the fill, and every thread
+// streams one contiguous range of the stream after a single jump.
+template <int NT, class E, class S>
 __global__ void __launch_bounds__(NT) k_onepw(FillArgs a) {
   __shared__ __align__(16) u64 stage[NT / 32][32 * kRowW];
   __shared__ u64 sh4[4];
   const int t = threadIdx.x, wid = t >> 5;
   E e;
   e.init_tile(a.eng, blockIdx.x, t, sh4);
-  for (u64 k = blockIdx.x; k < a.n_tiles; k += gridDim.x) {
-    onepw_tile<NT, C, E, S>(a, k, e, stage[wid]);
-    e.advance(a.eng);
-  }
+  onepw_tile<NT, E, S>(a, blockIdx.x, e, stage[wid], (int)a.eng.chunk_words);
 }
 
 // ------------------------------------------------------------------ merge seams
@@ -629,9 +659,9 @@ __global__ void __launch_bounds__(NT) k_onepw_batch(BatchArgs b) {
   while (batch_claim(b, fa, bi, &slot)) {
     E e;
     e.init_tile(fa.eng, bi.tile, threadIdx.x, sh4);
-    if (fa.dist == D_U64) onepw_tile<NT, C, E, SampU64>(fa, bi.tile, e, stage[wid]);
-    else if (fa.dist == D_UNIFORM52) onepw_tile<NT, C, E, SampUniform52>(fa, bi.tile, e, stage[wid]);
-    else onepw_tile<NT, C, E, SampUniform>(fa, bi.tile, e, stage[wid]);
+    if (fa.dist == D_U64) onepw_tile<NT, E, SampU64>(fa, bi.tile, e, stage[wid], C);
+    else if (fa.dist == D_UNIFORM52) onepw_tile<NT, E, SampUniform52>(fa, bi.tile, e, stage[wid], C);
+    else onepw_tile<NT, E, SampUniform>(fa, bi.tile, e, stage[wid], C);
   }
 }
 
@@ -697,10 +727,10 @@ int launch_merge(const FillArgs& a, int grid, cudaStream_t s, int* occ) {
 template <class E, class S>
 int launch_es(const FillArgs& a, int grid, cudaStream_t s, int* occ) {
   if (occ) {
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k_onepw<NT_, C_, E, S>, NT_, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k_onepw<NT_, E, S>, NT_, 0);
     return 0;
   }
-  k_onepw<NT_, C_, E, S><<<grid, NT_, 0, s>>>(a);
+  k_onepw<NT_, E, S><<<grid, NT_, 0, s>>>(a);
   return (int)cudaGetLastError();
 }
 
@@ -752,7 +782,8 @@ int dispatch_dist(const FillArgs& a, int grid, cudaStream_t s, int* occ) {
     case D_U64: return launch_es<E, SampU64>(a, grid, s, occ);
     case D_UNIFORM: return a.sp.epi ? launch_es<E, SampUniformE>(a, grid, s, occ) : launch_es<E, SampUniform>(a, grid, s, occ);
     case D_BOUNDED: return launch_rej<E>(a, grid, s, occ);
-    case D_BOUNDED_ONE: return launch_es<E, SampBoundedOne>(a, grid, s, occ);
+    case D_BOUNDED_ONE:
+      return (a.sp.m >> 32) ? launch_es<E, SampBoundedOne>(a, grid, s, occ) : launch_es<E, SampBoundedOne32>(a, grid, s, occ);
     case D_UNIFORM52: return launch_es<E, SampUniform52>(a, grid, s, occ);
     case D_NORMAL: return a.sp.epi ? launch_lean<E, LeanNormalE>(a, grid, s, occ) : launch_lean<E, LeanNormal>(a, grid, s, occ);
     case D_EXP: return a.sp.epi ? launch_lean<E, LeanExpE>(a, grid, s, occ) : launch_lean<E, LeanExp>(a, grid, s, occ);

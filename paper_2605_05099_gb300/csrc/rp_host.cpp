@@ -217,12 +217,24 @@ int upload_tables(const std::vector<Mat>& mats, void** out) {
   return 0;
 }
 
+// Device tables are cached per chunk length; the one-word fills pick their
+// chunk length from n, so the caches keep at most kTableCache entries
+// (cudaFree waits for the kernels that may still read an evicted table).
+constexpr size_t kTableCache = 16;
+template <class M>
+void evict_one(M& m) {
+  if (m.size() < kTableCache) return;
+  cudaFree(m.begin()->second);
+  m.erase(m.begin());
+}
+
 // nibble tables of T^(t C), t < nt (per-thread offsets inside a tile)
 std::map<std::pair<u64, int>, void*> g_xo_thread;
 int xo_device_thread(u64 C, int nt, void** out) {
   auto key = std::make_pair(C, nt);
   auto it = g_xo_thread.find(key);
   if (it == g_xo_thread.end()) {
+    evict_one(g_xo_thread);
     std::vector<Mat> mats(nt);
     xo_power(0, mats[0]);
     Mat step;
@@ -242,6 +254,7 @@ std::map<u64, void*> g_xo_cta;
 int xo_device_cta(u64 T, void** out) {
   auto it = g_xo_cta.find(T);
   if (it == g_xo_cta.end()) {
+    evict_one(g_xo_cta);
     std::vector<Mat> mats(16);
     xo_power(T, mats[0]);
     for (int j = 1; j < 16; ++j) mat_mul(mats[j - 1], mats[j - 1], mats[j]);
@@ -555,8 +568,21 @@ rp_status run_fill_state_locked(int engine, const u64 s_in[4], u64* pos, size_t 
     size_t left = n - done;
     double wpv = words_per_variate(dist, sp);
     double need = (double)left * wpv + 8.0 * std::sqrt((double)left * (wpv > 1.0 ? wpv : 1.0)) + 64.0;
-    u64 tiles = trivial ? (left + T - 1) / T : (u64)(need / (double)T) + 2;
-    u64 grid = std::min<u64>(tiles, (u64)sm_count() * occ);
+    u64 C = (u64)tg.c, T = (u64)tg.tile_words;
+    u64 tiles, grid;
+    if (trivial) {
+      // one tile per CTA: each thread streams one contiguous range of at
+      // least 64 words (a multiple of 16; of 64 for xoshiro, whose per-thread
+      // jump tables are built per chunk length)
+      const u64 nt = (u64)tg.nt, q = xoshiro_engine(engine) ? 64 : 16;
+      grid = std::max<u64>(1, std::min<u64>((u64)sm_count() * occ, (left + nt * 64 - 1) / (nt * 64)));
+      C = ((left + grid * nt - 1) / (grid * nt) + q - 1) / q * q;
+      T = nt * C;
+      tiles = grid;
+    } else {
+      tiles = (u64)(need / (double)T) + 2;
+      grid = std::min<u64>(tiles, (u64)sm_count() * occ);
+    }
     // engine at word `cur`
     u64 s0[4];
     memcpy(s0, s, sizeof(s0));
@@ -569,12 +595,12 @@ rp_status run_fill_state_locked(int engine, const u64 s_in[4], u64* pos, size_t 
     memcpy(a.eng.s, s0, sizeof(s0));
     a.eng.stride = grid * T;
     a.eng.tile_words = T;
-    a.eng.chunk_words = (u64)tg.c;
+    a.eng.chunk_words = C;
     if (grid > 65535) return fail(RP_ERR_INTERNAL, "grid too large for the CTA jump tables");
     if (xoshiro_engine(engine)) {
       e = xo_device_pow((void**)&a.eng.gf2_pow);
-      if (!e) e = xo_device_stride(a.eng.stride, (void**)&a.eng.gf2_stride);
-      if (!e) e = xo_device_thread((u64)tg.c, tg.nt, (void**)&a.eng.gf2_thread);
+      if (!e && !trivial) e = xo_device_stride(a.eng.stride, (void**)&a.eng.gf2_stride);
+      if (!e) e = xo_device_thread(C, tg.nt, (void**)&a.eng.gf2_thread);
       if (!e) e = xo_device_cta(T, (void**)&a.eng.gf2_cta);
       if (e) return cuda_fail(e, "jump tables");
     } else if (engine == RP_PCG64DXSM) {
