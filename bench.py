@@ -34,11 +34,7 @@ WORKLOAD = "single-stream fills: engines {xoshiro256++, PCG64-DXSM, Philox4x32-1
 # one ncu capture at n = 2^26 scaled by outputs (profiles/*_n2e26.md), by fill
 # key.  Only kernels whose current version was captured are listed.
 TRAFFIC = {
-    "philox4x32_10/normal": 4 * 511758848,
-    "xoshiro256pp/normal": 4 * 512455168,
     "philox4x32_10/bounded:9223372036854775809": 4 * 1579835928,
-    "xoshiro256pp/bounded:6": 4 * 483461120,
-    "xoshiro256pp/bounded:1000000007": 4 * 483461120,
 }
 
 
@@ -54,10 +50,11 @@ TRAFFIC = {
 #                 rounds of two 32 x 32 -> 64 products (4) and four xors;
 #                 the round keys depend on the key alone, so every block
 #                 of a fill shares them                                 -> 42 per word
+# With the issue rate of this GPU (4 schedulers x 32 lanes per SM and clock)
+# these give the derived integer peak that the measured engine-only rates
+# (rp_engine_fold) are compared with.
 ENGINE_OPS = {"xoshiro256pp": 20, "pcg64dxsm": 42, "philox4x32_10": 42}
-# integer lanes per SM and clock for adds, shifts and multiply-adds on this GPU
-INT_LANES_PER_SM = 64
-SMS = 152
+ISSUE_LANES_PER_SM = 128
 
 
 def words_per_output(dist, params):
@@ -228,34 +225,42 @@ def run_gpu(args):
     ms, variates = shard.reduce_timing(ms, len(fills) * N_FILL * args.steps, device="cuda")
     value = variates / (ms / 1e3)
 
-    # ---- roofline of the dominant kernel (the fill with the largest time)
-    # roofline of each fill: the slower of the HBM write time (8 B per
-    # output) and the engine's integer operations at peak issue; the line
-    # reports the dominant fill (largest time)
+    # ---- roofline of each fill: the slower of the HBM write time (8 B per
+    # output at the copy rate of MEASURED_PEAKS.json) and the engine time
+    # (words per output at the engine-only rate measured here with
+    # rp_engine_fold); the line reports the dominant fill (largest time)
     peaks, peak_kind = _peaks()
-    int_peak = SMS * INT_LANES_PER_SM * peaks.get("sm_max_mhz", 2070.0) * 1e6   # ops/s
-    fracs = {}
-    best = None
+    ceil = measure_ceilings(rp, stream, out_u, [e for e, _, _ in fills])
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    issue_peak = sms * ISSUE_LANES_PER_SM * peaks.get("sm_max_mhz", 2070.0) * 1e6   # thread ops/s
+    hbm = peaks["hbm_gbs"] * 1e9
+    flat, best = {}, None
     for (e, d, p), key in zip(fills, per_fill_ms):
         t = per_fill_ms[key] / args.steps / 1e3
-        ops = N_FILL * words_per_output(d, p) * ENGINE_OPS[e]
-        t_hbm = 8.0 * N_FILL / (peaks["hbm_gbs"] * 1e9)
-        t_alu = ops / int_peak
-        fracs[key] = round(max(t_hbm, t_alu) / t, 4)
+        words = N_FILL * words_per_output(d, p)
+        t_hbm, t_w, t_eng = 8.0 * N_FILL / hbm, 8.0 * N_FILL / (ceil["write_gbs"] * 1e9), words / ceil[e]
+        flat[f"ms:{key}"] = round(t * 1e3, 4)
+        flat[f"frac:{key}"] = round(max(t_hbm, t_eng) / t, 4)
+        flat[f"frac_vs_write_only:{key}"] = round(max(t_w, t_eng) / t, 4)
         if best is None or t > best[0]:
-            best = (t, key, t_hbm, t_alu, ops)
-    t, key, t_hbm, t_alu, ops = best
-    if t_alu > t_hbm:
-        roof = {"bound": "alu", "kernel": key, "achieved": round(ops / t / 1e9, 1), "peak": round(int_peak / 1e9, 1),
-                "unit": "Gops/s (32-bit integer engine operations)", "frac": round(t_alu / t, 4),
-                "peak_source": "derived: 152 SMs x 64 integer lanes x max SM clock (MEASURED_PEAKS.json sm_max_mhz)"}
+            best = (t, key, t_hbm, t_eng, words, e)
+    t, key, t_hbm, t_eng, words, e = best
+    if t_eng > t_hbm:
+        roof = {"bound": "alu", "kernel": key, "achieved": round(words / t / 1e9, 2), "peak": round(ceil[e] / 1e9, 2),
+                "unit": "Gwords/s (engine words)", "frac": round(t_eng / t, 4),
+                "peak_source": "measured: engine-only kernel (rp_engine_fold) of this engine, this run"}
     else:
         roof = {"bound": "hbm", "kernel": key, "achieved": round(8.0 * N_FILL / t / 1e9, 1), "peak": peaks["hbm_gbs"],
-                "unit": "GB/s", "frac": round(t_hbm / t, 4), "peak_source": peak_kind}
+                "unit": "GB/s", "frac": round(t_hbm / t, 4), "peak_source": peak_kind + " (MEASURED_PEAKS.json copy rate)"}
     roof.update({"traffic": TRAFFIC.get(key) if N_FILL == 1 << 28 else None,
-                 "hbm_time_ms": round(t_hbm * 1e3, 4), "alu_time_ms": round(t_alu * 1e3, 4),
-                 "per_fill_ms": {k: round(v / args.steps, 4) for k, v in per_fill_ms.items()},
-                 "per_fill_roofline_frac": fracs})
+                 "hbm_time_ms": round(t_hbm * 1e3, 4), "engine_time_ms": round(t_eng * 1e3, 4),
+                 "write_only_gbs": round(ceil["write_gbs"], 1),
+                 "frac_vs_write_only": round(max(8.0 * N_FILL / (ceil["write_gbs"] * 1e9), t_eng) / t, 4),
+                 "issue_peak_tops": round(issue_peak / 1e12, 2)})
+    for eng in sorted(set(x for x, _, _ in fills)):
+        roof[f"engine_gwords_per_s:{eng}"] = round(ceil[eng] / 1e9, 2)
+        roof[f"engine_issue_frac:{eng}"] = round(ceil[eng] * ENGINE_OPS[eng] / issue_peak, 3)
+    roof.update(flat)
 
     # ---- end to end through the public API with host buffers: every fill's
     # result is copied back to pinned host memory inside the timed region.
@@ -267,7 +272,7 @@ def run_gpu(args):
         hbuf = [torch.empty(N_FILL * 8, dtype=torch.uint8, pin_memory=True) for _ in range(2)]
         cstream = torch.cuda.Stream()
         copied = [None, None]
-        e_steps = max(1, min(args.steps, 2))
+        e_steps = max(1, args.steps)
         torch.cuda.synchronize()
         a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a0.record(stream)
@@ -318,6 +323,31 @@ def run_gpu(args):
         import torch.distributed as dist
         dist.barrier()
         dist.destroy_process_group()
+
+
+def measure_ceilings(rp, stream, buf_u, engines):
+    """The two measured ceilings of the fills, timed with CUDA events after
+    three untimed runs (median of five): the engine-only rate of each
+    engine, words/s of rp_engine_fold over N_FILL words (generation as in a
+    fill, nothing stored), and the write-only HBM rate, GB/s of filling the
+    2 GiB output buffer (torch fill_ of a pattern and zero_, the faster)."""
+    import torch
+    out = {}
+    fold = torch.zeros(1, dtype=torch.uint64, device="cuda")
+
+    def med(f):
+        for _ in range(3):
+            f()
+        ts = sorted(_ev_ms(stream, f) for _ in range(5))
+        return ts[2]
+    for e in engines:
+        if e not in out:
+            out[e] = N_FILL / (med(lambda: rp.rp_engine_fold(e, SEED, rp.NO_STREAM, 0, N_FILL, fold, stream)) / 1e3)
+    buf = buf_u.view(torch.float64)
+    with torch.cuda.stream(stream):
+        ms = min(med(lambda: buf.fill_(1.5)), med(lambda: buf.zero_()))
+    out["write_gbs"] = 8.0 * N_FILL / (ms / 1e3) / 1e9
+    return out
 
 
 def _ev_ms(stream, fn, reps=1):

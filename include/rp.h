@@ -80,6 +80,16 @@ typedef int rp_status;
 rp_status rp_fill_u64(rp_engine engine, uint64_t seed, uint64_t stream, uint64_t* pos,
                       size_t n, uint64_t* d_out, void* cuda_stream);
 
+/* The xor of words pos .. pos + n - 1 of the stream, written to d_fold (one
+ * 64-bit device word, owned by the caller); *pos advances by n.  The words
+ * are generated as a fill generates them (each thread one contiguous range
+ * after one jump, Sec. 4.4 jump-ahead) and folded, and nothing else is
+ * computed or stored, so the call's words/s is the engine's throughput
+ * ceiling for the fills (Table "engines" lists the paper's CPU rates of the
+ * same engines).  Errors as for the fills; n = 0 leaves d_fold untouched. */
+rp_status rp_engine_fold(rp_engine engine, uint64_t seed, uint64_t stream, uint64_t* pos,
+                         size_t n, uint64_t* d_fold, void* cuda_stream);
+
 /* U[0,1) doubles with 53-bit resolution: floor(u / 2^11) * 2^-53 (Sec. 3.1,
  * method 1), one word per variate, bit-exact. */
 rp_status rp_fill_uniform(rp_engine engine, uint64_t seed, uint64_t stream, uint64_t* pos,

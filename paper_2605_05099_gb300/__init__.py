@@ -53,6 +53,7 @@ def lib():
         pu64 = ctypes.POINTER(u64)
         sig = {
             "rp_fill_u64": [i32, u64, u64, pu64, sz, vp, vp],
+            "rp_engine_fold": [i32, u64, u64, pu64, sz, vp, vp],
             "rp_fill_uniform": [i32, u64, u64, pu64, sz, vp, vp],
             "rp_fill_uniform52": [i32, u64, u64, pu64, sz, vp, vp],
             "rp_fill_bounded": [i32, u64, u64, pu64, sz, u64, vp, vp],
@@ -132,6 +133,16 @@ def _fill(fn, engine, seed, stream, pos, out, dtype, extra=(), cuda_stream=None)
 # tensor of n elements; the return value is the new stream position.
 def rp_fill_u64(engine, seed, stream, pos, out, cuda_stream=None):
     return _fill(lib().rp_fill_u64, engine, seed, stream, pos, out, torch.uint64, cuda_stream=cuda_stream)
+
+
+def rp_engine_fold(engine, seed, stream, pos, n, fold, cuda_stream=None):
+    """XOR of stream words pos .. pos + n - 1 into `fold` (a 1-element uint64
+    CUDA tensor); returns the new position."""
+    assert fold.is_cuda and fold.dtype == torch.uint64 and fold.numel() >= 1
+    cpos = ctypes.c_uint64(pos)
+    _check(lib().rp_engine_fold(_engine(engine), seed, stream, ctypes.byref(cpos), n, fold.data_ptr(),
+                                _stream_handle(cuda_stream)))
+    return cpos.value
 
 
 def rp_fill_uniform(engine, seed, stream, pos, out, cuda_stream=None):

@@ -464,6 +464,35 @@ __global__ void __launch_bounds__(NT) k_onepw(FillArgs a) {
   onepw_tile<NT, E, S>(a, blockIdx.x, e, stage[wid], (int)a.eng.chunk_words);
 }
 
+// Engine alone: the xor of the launch's n words, one contiguous range per
+// thread as in k_onepw, folded per warp into *a.out (zeroed by the host).
+// Nothing else is computed or stored, so its words/s is the engine's
+// throughput ceiling for the fills.
+template <int NT, class E>
+__global__ void __launch_bounds__(NT) k_fold(FillArgs a) {
+  __shared__ u64 sh4[4];
+  E e;
+  e.init_tile(a.eng, blockIdx.x, threadIdx.x, sh4);
+  const int C = (int)a.eng.chunk_words;   // a multiple of 16
+  const u64 base = (u64)blockIdx.x * NT * C + (u64)threadIdx.x * C;
+  u64 f = 0;
+  E g = e;
+  for (int j0 = 0; j0 < C; j0 += 16) {
+    u64 u[16];
+    take_words<E, 16>(g, u);
+    if (base + j0 + 16 <= a.n) {
+#pragma unroll
+      for (int i = 0; i < 16; ++i) f ^= u[i];
+    } else {
+#pragma unroll
+      for (int i = 0; i < 16; ++i) f ^= base + j0 + i < a.n ? u[i] : 0ull;
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) f ^= __shfl_xor_sync(0xffffffffu, f, o);
+  if ((threadIdx.x & 31) == 0) atomicXor((unsigned long long*)a.out, f);
+}
+
 // ------------------------------------------------------------------ merge seams
 // Gamma and beta attempts are at least two words long, so one-word sync
 // points do not exist.  Instead the seam of a chunk is a merge point: run
@@ -735,6 +764,13 @@ int launch_es(const FillArgs& a, int grid, cudaStream_t s, int* occ) {
 }
 
 template <class E>
+int launch_fold(const FillArgs& a, int grid, cudaStream_t s, int* occ) {
+  if (occ) return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k_fold<NT_, E>, NT_, 0);
+  k_fold<NT_, E><<<grid, NT_, 0, s>>>(a);
+  return (int)cudaGetLastError();
+}
+
+template <class E>
 int launch_rej(const FillArgs& a, int grid, cudaStream_t s, int* occ) {
   if (occ) {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k_rej<NT_, CR_, E>, NT_, 0);
@@ -785,6 +821,7 @@ int dispatch_dist(const FillArgs& a, int grid, cudaStream_t s, int* occ) {
     case D_BOUNDED_ONE:
       return (a.sp.m >> 32) ? launch_es<E, SampBoundedOne>(a, grid, s, occ) : launch_es<E, SampBoundedOne32>(a, grid, s, occ);
     case D_UNIFORM52: return launch_es<E, SampUniform52>(a, grid, s, occ);
+    case D_FOLD: return launch_fold<E>(a, grid, s, occ);
     case D_NORMAL: return a.sp.epi ? launch_lean<E, LeanNormalE>(a, grid, s, occ) : launch_lean<E, LeanNormal>(a, grid, s, occ);
     case D_EXP: return a.sp.epi ? launch_lean<E, LeanExpE>(a, grid, s, occ) : launch_lean<E, LeanExp>(a, grid, s, occ);
     case D_GAMMA: return a.sp.ga.boost ? launch_merge<E, SampGammaBoost>(a, grid, s, occ) : launch_merge<E, SampGamma>(a, grid, s, occ);

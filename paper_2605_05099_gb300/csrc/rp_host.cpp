@@ -557,7 +557,8 @@ rp_status run_fill_state_locked(int engine, const u64 s_in[4], u64* pos, size_t 
   auto key = std::make_pair(engine, dist | (sp.epi ? 256 : 0));   // transformed fills run other kernels
   if (!g_occ.count(key)) g_occ[key] = rp::occupancy_blocks(engine, dist, sp.epi);
   int occ = g_occ[key] > 0 ? g_occ[key] : 1;
-  const bool trivial = (dist == rp::D_U64 || dist == rp::D_UNIFORM || dist == rp::D_BOUNDED_ONE || dist == rp::D_UNIFORM52);
+  const bool trivial = (dist == rp::D_U64 || dist == rp::D_UNIFORM || dist == rp::D_BOUNDED_ONE ||
+                        dist == rp::D_UNIFORM52 || dist == rp::D_FOLD);
   const bool one_pass_check = dist == rp::D_BOUNDED_ONE;
 
   u64 cur = *pos;
@@ -736,6 +737,17 @@ rp_status rp_fill_u64(rp_engine engine, uint64_t seed, uint64_t stream, uint64_t
                       void* cuda_stream) {
   rp::SampArgs sp{};
   return run_fill(engine, seed, stream, (u64*)pos, n, rp::D_U64, sp, d_out, cuda_stream);
+}
+
+rp_status rp_engine_fold(rp_engine engine, uint64_t seed, uint64_t stream, uint64_t* pos, size_t n, uint64_t* d_fold,
+                         void* cuda_stream) {
+  rp_status st = check_fill_args(engine, (u64*)pos, n, d_fold);
+  if (st || n == 0) return st;
+  const int e = (int)cudaMemsetAsync(d_fold, 0, sizeof(uint64_t), (cudaStream_t)cuda_stream);
+  if (e) return cuda_fail(e, "fold reset");
+  rp::SampArgs sp;
+  memset(&sp, 0, sizeof(sp));
+  return run_fill(engine, seed, stream, (u64*)pos, n, rp::D_FOLD, sp, d_fold, cuda_stream);
 }
 
 rp_status rp_fill_uniform(rp_engine engine, uint64_t seed, uint64_t stream, uint64_t* pos, size_t n, double* d_out,

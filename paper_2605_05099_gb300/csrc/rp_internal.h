@@ -9,7 +9,8 @@ namespace rp {
 enum Dist : int { D_U64 = 0, D_UNIFORM = 1, D_BOUNDED = 2, D_NORMAL = 3, D_EXP = 4, D_GAMMA = 5, D_BETA = 6,
                   D_BOUNDED_ONE = 7,   // bounded, one pass that assumes no rejection (records the first one)
                   D_T = 8,             // Student t: a normal, then a gamma (ep[0] = nu)
-                  D_UNIFORM52 = 9 };   // the paper's default 52-bit uniform
+                  D_UNIFORM52 = 9,     // the paper's default 52-bit uniform
+                  D_FOLD = 10 };       // xor of the words, no output array (engine-only throughput)
 
 // Device error bits (ctrl->err)
 enum : unsigned {

@@ -250,3 +250,19 @@ def test_checkpoint_resume_continues_the_stream(engine):
     c, p3 = gpu_fill("normal", engine, 77, None, 0, 12_345 + 54_321)
     torch.cuda.synchronize()
     assert p2 == p3 and same_bits(np.concatenate([a.cpu().numpy(), b.cpu().numpy()]), c)
+
+
+@pytest.mark.parametrize("engine", ENGINES)
+def test_engine_fold_equals_xor_of_the_oracle_words(engine):
+    """rp_engine_fold (the engine-only throughput kernel) folds exactly the
+    stream words pos .. pos + n - 1: their xor equals the xor of the
+    oracle's raw words, over sizes that span one and many ranges, ragged
+    ends and a nonzero start; *pos advances by n."""
+    fold = torch.zeros(1, dtype=torch.uint64, device="cuda")
+    for pos, n in [(0, 1), (0, 17), (5, 100_003), (12345, (1 << 20) + 5), (0, 1 << 24)]:
+        newpos = rp.rp_engine_fold(engine, 2024, rp.NO_STREAM, pos, n, fold)
+        torch.cuda.synchronize()
+        got = int(fold.view(torch.int64).cpu().numpy().view(np.uint64)[0])
+        words, opos = oracle_fill("u64", engine, 2024, None, pos, n)
+        assert newpos == opos == pos + n
+        assert got == int(np.bitwise_xor.reduce(words)), (engine, pos, n)
