@@ -329,6 +329,24 @@ rp_status rp_jump_state(rp_engine engine, uint64_t* words, uint64_t delta_hi, ui
  * values (Sec. 4.2 exactness, read as correct rounding).  For checks. */
 rp_status rp_log_cr(const double* d_x, double* d_y, size_t n, void* cuda_stream);
 
+/* The library's correctly rounded exp of n device doubles (d_y[i] =
+ * RN(exp d_x[i])), the routine that decides the ziggurat wedge tests when
+ * y lies within 2^-48 of the libm value (Sec. 3.1 wedges; Sec. 4.2
+ * exactness, read as correct rounding).  For checks. */
+rp_status rp_exp_cr(const double* d_x, double* d_y, size_t n, void* cuda_stream);
+
+/* How often the exact accept decisions fell back past their fast tests,
+ * since the last reset (for checks; Sec. 4.2 exactness): every wedge,
+ * normal-tail pair and Marsaglia-Tsang test is decided first in FP32 with a
+ * proven margin, then in FP64 with libm and a margin of its error, and only
+ * then with the correctly rounded exp/log.  h_counts[6] (host) receives
+ *   [0] wedge tests decided past the FP32 margin, [1] of those past the
+ *   libm margin (correctly rounded exp), [2], [3] the same for normal tail
+ *   pairs (correctly rounded logs), [4], [5] for Marsaglia-Tsang tests.
+ * reset != 0 zeroes the counters after reading them.  Reads device memory:
+ * call it after the fills it should count have completed. */
+rp_status rp_debug_counters(uint64_t* h_counts, int reset);
+
 /* Message of the last failed call on this host thread ("" if none). */
 const char* rp_last_error(void);
 

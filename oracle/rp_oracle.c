@@ -104,7 +104,8 @@ static void xoshiro_step(uint64_t s[4]) {
 }
 
 /* xoshiro256++: the "++" scrambler, rotl(s0 + s3, 23) + s0, of the current
- * state, then the transition. */
+ * state, then the transition.  Parity unpinned for the scrambler (see
+ * rp_oracle.h). */
 static uint64_t xoshiro_next(uint64_t s[4]) {
   uint64_t out = rotl64(s[0] + s[3], 23) + s[0];
   xoshiro_step(s);

@@ -11,9 +11,14 @@
  * 64-bit engine output after seeding.  A fill consumes exactly the words its
  * variates used and leaves `pos` at the next unconsumed word.
  *
- * Parity unpinned: the constants of the xoshiro256** scrambler (5, 7, 9),
- * taken from the engine's published definition; the rest of that engine is
- * pinned through xoshiro256++ (see tests/test_oracle_engines.py).
+ * Parity unpinned: the output functions of the xoshiro engines.  The
+ * xoshiro256++ scrambler, rotl(s0 + s3, 23) + s0, and the constants of the
+ * xoshiro256** scrambler (5, 7, 9) are taken from the engines' published
+ * definitions, and nothing on this machine gives their outputs (no test
+ * vectors; NumPy has no xoshiro).  Their shared transition is pinned by its
+ * primitive characteristic polynomial and by jump identities, and the
+ * xoshiro256** outputs are tied to that transition's state words (see
+ * tests/test_oracle_engines.py).
  */
 #ifndef RP_ORACLE_H
 #define RP_ORACLE_H

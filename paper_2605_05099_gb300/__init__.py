@@ -71,6 +71,8 @@ def lib():
             "rp_mvn": [i32, u64, u64, pu64, i32, sz, vp, vp, vp, vp, vp],
             "rp_mvn_grads": [i32, sz, vp, vp, vp, vp, vp],
             "rp_log_cr": [vp, vp, sz, vp],
+            "rp_exp_cr": [vp, vp, sz, vp],
+            "rp_debug_counters": [pu64, i32],
             "rp_substream_state": [i32, u64, u64, pu64, ctypes.POINTER(i32)],
             "rp_batch_plan_create": [ctypes.POINTER(Request), sz, i32, u64, i32, ctypes.POINTER(vp), vp],
             "rp_batch_plan_run": [vp, pu64, vp],
@@ -435,6 +437,26 @@ class MVN(torch.autograd.Function):
         gL = torch.empty((d, d), dtype=torch.float64, device="cuda")
         rp_mvn_grads(G.to(torch.float64).contiguous(), Z, gmu, gL)
         return gmu, gL, None, None, None, None, None
+
+
+DEBUG_COUNTERS = ("wedge_fp64", "wedge_cr", "tail_fp64", "tail_cr", "mt_fp64", "mt_cr")
+
+
+def rp_debug_counters(reset=False):
+    """Fallback counts of the exact accept decisions since the last reset, as
+    a dict over DEBUG_COUNTERS."""
+    c = (ctypes.c_uint64 * 6)()
+    _check(lib().rp_debug_counters(c, 1 if reset else 0))
+    return dict(zip(DEBUG_COUNTERS, (int(x) for x in c)))
+
+
+def rp_exp_cr(x, y=None, cuda_stream=None):
+    """Correctly rounded exp of a float64 CUDA tensor (element-wise)."""
+    if y is None:
+        y = torch.empty_like(x)
+    n = x.numel()
+    _check(lib().rp_exp_cr(_f64(x, x.shape, "x"), _f64(y, x.shape, "y"), n, _stream_handle(cuda_stream)))
+    return y
 
 
 def rp_log_cr(x, y=None, cuda_stream=None):

@@ -231,6 +231,15 @@ __device__ __forceinline__ double cr_log_fast(double y) {
 // Out-of-line copy for the samplers (keeps their register count down).
 __device__ __noinline__ static double cr_log_nl(double y) { return cr_log_fast(y); }
 
+// Counts of the exact decisions' fallback stages, for tests (one copy per
+// translation unit; read and reset through rp_debug_counters):
+//   0 wedge tests past the FP32 margin, 1 of those past the libm margin;
+//   2, 3 the same for normal tail pairs; 4, 5 for Marsaglia-Tsang tests.
+// Each is bumped only on its rare path.
+enum { DBG_WEDGE_FP64 = 0, DBG_WEDGE_CR, DBG_TAIL_FP64, DBG_TAIL_CR, DBG_MT_FP64, DBG_MT_CR, DBG_N = 8 };
+static __device__ unsigned long long g_dbg[DBG_N];
+__device__ __forceinline__ void dbg_count(int k) { atomicAdd(&g_dbg[k], 1ull); }
+
 // Exact decision y < RN(exp(t)): CUDA exp (max error a few ulp) decides
 // unless y lies within 2^-48 relative of it; then the correctly rounded value
 // decides.
@@ -239,6 +248,7 @@ __device__ __forceinline__ bool lt_cr_exp(double y, double t) {
   double m = __dmul_rn(e, 0x1.0p-48);
   if (y < __dsub_rn(e, m)) return true;
   if (y > __dadd_rn(e, m)) return false;
+  dbg_count(DBG_WEDGE_CR);
   return y < cr_exp_dev(t);
 }
 

@@ -81,6 +81,7 @@ __device__ __forceinline__ bool wedge_accept(u64 r, int i, u64 u2, const ZigDev&
   float m = 0x1.0p-19f * (1.0f - tf);
   if (yf < ef * (1.0f - m)) return true;
   if (yf > ef * (1.0f + m)) return false;
+  dbg_count(DBG_WEDGE_FP64);
   double x = mul_rn_int(r, z.msh[i], z.wtz[i], z.we[i]);
   double y = __dadd_rn(__dmul_rn(__dsub_rn(z.f[i - 1], z.f[i]), u53_bits(u2)), z.f[i]);
   double t = kNormal ? __dmul_rn(-0.5, __dmul_rn(x, x)) : -x;
@@ -97,6 +98,7 @@ __device__ __forceinline__ bool tail_pair_accept(u64 w1, u64 w2, const ZigDev& z
   float m = (lhs + rhs) * 0x1.0p-16f;
   if (lhs > rhs + m) return true;
   if (lhs < rhs - m) return false;
+  dbg_count(DBG_TAIL_FP64);
   // libm logs (one ulp) decide unless the sides are within their effect
   double o1 = __dsub_rn(1.0, u53_bits(w1)), o2 = __dsub_rn(1.0, u53_bits(w2));
   double a = __ddiv_rn(-log(o1), z.R), b = -log(o2);
@@ -104,6 +106,7 @@ __device__ __forceinline__ bool tail_pair_accept(u64 w1, u64 w2, const ZigDev& z
   double mg = (l2 + r2) * 0x1.0p-48;
   if (l2 > r2 + mg) return true;
   if (l2 < r2 - mg) return false;
+  dbg_count(DBG_TAIL_CR);
   a = __ddiv_rn(-cr_log_nl(o1), z.R);
   b = -cr_log_nl(o2);
   return __dadd_rn(b, b) > __dmul_rn(a, a);
@@ -736,6 +739,19 @@ __global__ void k_tails(FillArgs a) {
   }
 }
 
+// Adds this translation unit's fallback counts to out[DBG_N]; reset: zero them.
+inline int dbg_read(unsigned long long* out, int reset) {
+  unsigned long long h[DBG_N];
+  int e = (int)cudaMemcpyFromSymbol(h, g_dbg, sizeof(h));
+  if (e) return e;
+  for (int i = 0; i < DBG_N; ++i) out[i] += h[i];
+  if (reset) {
+    for (int i = 0; i < DBG_N; ++i) h[i] = 0;
+    e = (int)cudaMemcpyToSymbol(g_dbg, h, sizeof(h));
+  }
+  return e;
+}
+
 // ------------------------------------------------------------------ per-engine entry
 constexpr int NT_ = 128;
 constexpr int C_ = 384;     // chunk words of the one-word and ziggurat fills (measured best of 256, 384, 512)
@@ -845,5 +861,8 @@ int dispatch_dist(const FillArgs& a, int grid, cudaStream_t s, int* occ) {
   }                                                                                            \
   int upload_zig_##NAME(const void* host2) {                                                   \
     return (int)cudaMemcpyToSymbol(g_zig, host2, 2 * sizeof(ZigDev));                          \
+  }                                                                                            \
+  int dbg_##NAME(unsigned long long* out, int reset) {                                         \
+    return dbg_read(out, reset);                                                               \
   }                                                                                            \
   }

@@ -60,6 +60,7 @@ __device__ __forceinline__ bool mt_v_positive(int xk, u64 xa, u64 xb, const MTPa
 // unless the two sides are within the effect of one-ulp log errors, in which
 // case the correctly rounded logs decide.
 static __device__ bool mt_accept_exact(int xk, u64 xa, u64 xb, u64 u, const MTParams& p, const ZigDev& z) {
+  dbg_count(DBG_MT_FP64);
   double x = normal_x_exact(xk, xa, xb, z);
   double v = __dadd_rn(1.0, __dmul_rn(p.c, x));
   v = __dmul_rn(__dmul_rn(v, v), v);
@@ -75,6 +76,7 @@ static __device__ bool mt_accept_exact(int xk, u64 xa, u64 xb, u64 u, const MTPa
   double marg = 0x1.0p-48 * (fabs(lu) + p.d * (fabs(lv) + fabs(s)) + fabs(ds) + fabs(rhs));
   if (lu < rhs - marg) return true;
   if (lu > rhs + marg) return false;
+  dbg_count(DBG_MT_CR);
   rhs = __dadd_rn(__dmul_rn(0.5, x2), __dmul_rn(p.d, __dadd_rn(om, cr_log_nl(v))));
   return cr_log_nl(U) < rhs;
 }

@@ -1143,11 +1143,13 @@ extern "C" rp_status rp_fill_normal_philox_static(uint64_t seed, uint64_t stream
     a.n_tiles = tiles;
     a.out = d_out + done;
     // What must start at zero: the status words of this launch's tiles and
-    // the control block (its tail count included), except done_tile, which
-    // starts at all ones.  Tail entries are written before they are read.
+    // the control block (its tail count included), except done_tile and
+    // first_reject, which start at all ones as in the allocating path.  Tail
+    // entries are written before they are read.
     e = (int)cudaMemsetAsync(status, 0, tiles * 8, cs);
     if (!e) e = (int)cudaMemsetAsync(ctrl, 0, sizeof(rp::Ctrl), cs);
     if (!e) e = (int)cudaMemsetAsync(&ctrl->done_tile, 0xff, sizeof(ctrl->done_tile), cs);
+    if (!e) e = (int)cudaMemsetAsync(&ctrl->first_reject, 0xff, sizeof(ctrl->first_reject), cs);
     if (e) return cuda_fail(e, "scratch reset");
     e = rp::launch_fill(a, (int)grid, cuda_stream);
     if (e) return cuda_fail(e, "kernel launch");
@@ -1747,6 +1749,25 @@ extern "C" rp_status rp_mvn_grads(int d, size_t n, const double* d_G, const doub
   if (!e) e = (int)cudaStreamSynchronize((cudaStream_t)cuda_stream);
   if (e) return cuda_fail(e, "mvn grads");
   g_launches.fetch_add(4);
+  return RP_OK;
+}
+
+extern "C" rp_status rp_debug_counters(uint64_t* h_counts, int reset) {
+  if (!h_counts) return fail(RP_ERR_NULL, "NULL counts pointer");
+  std::lock_guard<std::mutex> lk(g_mu);
+  unsigned long long c[8];
+  const int e = rp::debug_counters(c, reset);
+  if (e) return cuda_fail(e, "debug counters");
+  for (int i = 0; i < 6; ++i) h_counts[i] = c[i];
+  return RP_OK;
+}
+
+extern "C" rp_status rp_exp_cr(const double* d_x, double* d_y, size_t n, void* cuda_stream) {
+  if (n && (!d_x || !d_y)) return fail(RP_ERR_NULL, "NULL device pointer");
+  int e = rp::launch_exp_cr(d_x, d_y, n, cuda_stream);
+  if (!e) e = (int)cudaStreamSynchronize((cudaStream_t)cuda_stream);
+  if (e) return cuda_fail(e, "exp");
+  g_launches.fetch_add(1);
   return RP_OK;
 }
 

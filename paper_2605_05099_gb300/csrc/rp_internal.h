@@ -160,6 +160,9 @@ static_assert(sizeof(Ctrl) <= kStaticCtrlWords * 8, "control block does not fit 
 static_assert(sizeof(TailEntry) % 8 == 0, "tail entries must be whole words");
 int static_scratch_address(void** p);
 int launch_log_cr(const double* x, double* y, unsigned long long n, void* stream);
+int launch_exp_cr(const double* x, double* y, unsigned long long n, void* stream);
+// Exact-decision fallback counts (rp_kernels.cu), 8 words; reset zeroes them.
+int debug_counters(unsigned long long* out, int reset);
 // Multivariate normal (rp_mvn.cu).
 int launch_mvn_apply(int d, unsigned long long n, const double* mu, const double* L, const double* Z, double* X,
                      void* stream);

@@ -18,6 +18,24 @@ int upload_zig_pcg(const void* host2);
 int upload_zig_ph(const void* host2);
 int upload_zig_ph64(const void* host2);
 int upload_zig_xss(const void* host2);
+int dbg_xo(unsigned long long* out, int reset);
+int dbg_pcg(unsigned long long* out, int reset);
+int dbg_ph(unsigned long long* out, int reset);
+int dbg_ph64(unsigned long long* out, int reset);
+int dbg_xss(unsigned long long* out, int reset);
+
+// Fallback counts summed over the translation units that decide (the engine
+// ones and this one); reset zeroes them.
+int debug_counters(unsigned long long* out, int reset) {
+  for (int i = 0; i < DBG_N; ++i) out[i] = 0;
+  int e = dbg_xo(out, reset);
+  if (!e) e = dbg_pcg(out, reset);
+  if (!e) e = dbg_ph(out, reset);
+  if (!e) e = dbg_ph64(out, reset);
+  if (!e) e = dbg_xss(out, reset);
+  if (!e) e = dbg_read(out, reset);
+  return e;
+}
 
 namespace {
 int dispatch(const FillArgs& a, int grid, void* s, int* occ) {
@@ -131,6 +149,17 @@ __global__ void k_log_cr(const double* __restrict__ x, double* __restrict__ y, u
 int launch_log_cr(const double* x, double* y, unsigned long long n, void* stream) {
   if (!n) return 0;
   k_log_cr<<<608, 256, 0, (cudaStream_t)stream>>>(x, y, n);
+  return (int)cudaGetLastError();
+}
+
+__global__ void k_exp_cr(const double* __restrict__ x, double* __restrict__ y, unsigned long long n) {
+  for (unsigned long long i = blockIdx.x * (u64)blockDim.x + threadIdx.x; i < n; i += (u64)gridDim.x * blockDim.x)
+    y[i] = cr_exp_dev(x[i]);
+}
+
+int launch_exp_cr(const double* x, double* y, unsigned long long n, void* stream) {
+  if (!n) return 0;
+  k_exp_cr<<<608, 256, 0, (cudaStream_t)stream>>>(x, y, n);
   return (int)cudaGetLastError();
 }
 

@@ -66,21 +66,25 @@ def test_config1_words_then_uniforms():
     assert same_bits(g1, o1) and same_bits(g2, o2)
 
 
-@pytest.mark.parametrize("engine", ENGINES)
-def test_full_size_normal_exp(engine):
-    """Single-stream workload size (n = 2^28) for the ziggurat samplers on
-    xoshiro256++, and a 2^24 prefix-sized fill for the other engines:
-    whole-array bit compare and consumed words."""
-    n = (1 << 28) if engine == "xoshiro256pp" else (1 << 24)
+CONFIG2_ENGINES = ["xoshiro256pp", "pcg64dxsm", "philox4x32_10"]
+
+
+@pytest.mark.parametrize("engine", CONFIG2_ENGINES)
+@pytest.mark.parametrize("dist,params", [("normal", ()), ("exp", ()), ("bounded", (6,)), ("bounded", (1_000_000_007,)),
+                                         ("bounded", (2 ** 63 + 1,))], ids=lambda x: str(x))
+def test_single_stream_workload_full_size(engine, dist, params):
+    """The single-stream workload at its own size: every (engine, sampler)
+    fill of n = 2^28 from seed 2024, word 0, as the bench launches it,
+    compared with the oracle over the whole array, with the consumed words
+    (bit-exact except ziggurat tail values, 2 ulp)."""
+    assert_parity(dist, engine, 2024, None, 0, 1 << 28, params)
+
+
+@pytest.mark.parametrize("engine", ["philox4x64_10", "xoshiro256ss"])
+def test_full_size_normal_exp_other_engines(engine):
+    """The two engines outside the single-stream workload, at 2^24."""
     for dist in ("normal", "exp"):
-        assert_parity(dist, engine, 2024, None, 0, n)
-
-
-def test_full_size_bounded_half_range():
-    n = 1 << 26
-    g, gpos = gpu_fill("bounded", "xoshiro256pp", 2024, None, 0, n, (2 ** 63 + 1,))
-    o, opos = oracle_fill("bounded", "xoshiro256pp", 2024, None, 0, n, (2 ** 63 + 1,))
-    assert gpos == opos and same_bits(g, o)
+        assert_parity(dist, engine, 2024, None, 0, 1 << 24)
 
 
 def test_bounded_edge_moduli():

@@ -50,7 +50,9 @@ def test_mvn_forward_matches_oracle(d, n):
     assert pos == int(g.pos)
     zg, zo = Zh.ravel(), zref
     bad = np.nonzero(zg.view(np.int64) != zo.view(np.int64))[0]
-    assert len(bad) <= max(4, zg.size // 500)
+    # only ziggurat tail outputs (|z| > R, values through a libm log) may differ, by 2 ulp
+    R = oracle.zig_table(0)[3]
+    assert np.all(np.abs(zo[bad]) > R), bad[:8]
     assert np.all(np.abs(zg.view(np.int64)[bad] - zo.view(np.int64)[bad]) <= 2)
     _check_x(mu, L, Zh, Xh)
 

@@ -1,0 +1,101 @@
+"""GPU parity on streams built around near-ties of the exact accept decisions
+(tests/tie_streams.py): ziggurat wedge tests (normal and exponential),
+normal tail pairs and Marsaglia-Tsang log tests decided within one ulp,
+each in both outcomes.  The fill must equal the oracle (bit for bit, tail
+values within 2 ulp) with the same consumed words, and the library's
+fallback counters must show that the FP64 stage and the correctly rounded
+stage of each decision ran (Sec. 3.1 samplers; Sec. 4.2 exactness)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2605_05099_gb300 as rp
+from gpu_util import ulp_diff
+from tie_streams import mt_ties, oracle_gen, tail_pair_ties, wedge_ties
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def _run(dist, words, pos, n, params=()):
+    out = torch.empty(n, dtype=torch.float64, device="cuda")
+    p = {"p0": params[0]} if params else {}
+    gpos = rp.rp_fill_state("philox4x32_10", words, pos, dist, out, **p)
+    torch.cuda.synchronize()
+    g = oracle_gen(words)
+    if pos:
+        oracle.next_words(g, pos)
+    ref, start = oracle.fill(g, dist, n, *params, with_start=True)
+    return out.cpu().numpy(), gpos, ref, int(g.pos), start
+
+
+def _check(dist, words, pos, n, params=()):
+    """GPU fill == oracle: consumed words, and values bit for bit except those
+    that go through a libm function on the device (ziggurat tail values, the
+    gamma boost for alpha < 1), within 2 ulp."""
+    got, gpos, ref, opos, start = _run(dist, words, pos, n, params)
+    assert gpos == opos, (dist, gpos, opos)
+    bad = np.nonzero(got.view(np.uint64) != ref.view(np.uint64))[0]
+    if dist == "gamma":
+        assert len(bad) == 0 or params[0] < 1.0, (dist, params, bad[:5])
+    else:
+        R = oracle.zig_table(1 if dist == "exp" else 0)[3]
+        assert np.all(np.abs(ref[bad]) > R), (dist, bad[:5])
+    for j in bad:
+        assert ulp_diff(got[j], ref[j]) <= 2, (dist, int(j), got[j], ref[j])
+    return start
+
+
+@pytest.mark.parametrize("dist", ["normal", "exp"])
+def test_wedge_ties(dist):
+    """Wedge tests whose y lies within one ulp of exp(t): accepted (the
+    first output comes from word 0) and rejected (it comes later)."""
+    rng = np.random.default_rng(101 if dist == "normal" else 202)
+    cases = wedge_ties(dist == "exp", rng, (1, 40, 128, 200, 254))
+    rp.rp_debug_counters(reset=True)
+    outcomes = set()
+    for words, pos in cases:
+        start = _check(dist, words, pos, 48)
+        outcomes.add(int(start[0]) == 0)
+    c = rp.rp_debug_counters()
+    assert outcomes == {True, False}
+    assert c["wedge_fp64"] >= len(cases) and c["wedge_cr"] >= len(cases), c
+
+
+def test_normal_tail_pair_ties():
+    """Normal tails whose first pair satisfies 2b = a^2 to within one ulp of
+    b: accepted (the tail ends after three words) and rejected (it goes on)."""
+    rng = np.random.default_rng(303)
+    cases = tail_pair_ties(rng, 6)
+    rp.rp_debug_counters(reset=True)
+    lengths = set()
+    for words, pos in cases:
+        start = _check("normal", words, pos, 48)
+        assert int(start[0]) == 1
+        lengths.add(int(start[1]) - 1)
+    c = rp.rp_debug_counters()
+    assert 3 in lengths and any(x > 3 for x in lengths), lengths
+    assert c["tail_fp64"] >= len(cases) and c["tail_cr"] >= len(cases), c
+
+
+@pytest.mark.parametrize("alpha", [2.5, 30.0, 0.3])
+def test_marsaglia_tsang_log_test_ties(alpha):
+    """Gamma attempts that fail the squeeze and whose log test is decided
+    within one ulp of U: accepted (the first variate comes from words 0-1)
+    and rejected (from a later attempt); alpha < 1 through the boost."""
+    rng = np.random.default_rng(int(alpha * 10) + 404)
+    cases = mt_ties(alpha, rng, 6)
+    rp.rp_debug_counters(reset=True)
+    firsts = set()
+    for words, pos in cases:
+        start = _check("gamma", words, pos, 32, (alpha,))
+        firsts.add(int(start[0]) == 0)
+    c = rp.rp_debug_counters()
+    assert firsts == {True, False}, firsts
+    assert c["mt_fp64"] >= len(cases) and c["mt_cr"] >= len(cases), c
