@@ -31,6 +31,13 @@
  *   completed (the call synchronises that stream once at the end to read
  *   the consumed-word count and the device status word).
  * - Threading: calls from several host threads are serialised internally.
+ * - Devices: the allocating entry points (fills, gradients, batch plans, the
+ *   MVN) keep their scratch, jump tables and uploaded tables for the device
+ *   that was current at their first call; a later call with another device
+ *   current fails with RP_ERR_PARAM before launching anything.  Only
+ *   rp_fill_normal_philox_static keeps its state per device.  The library
+ *   must not be used across cudaDeviceReset (its cached device pointers and
+ *   tables would be stale).
  * - n = 0 is a valid no-op that leaves *pos unchanged (Sec. 5.1, zero
  *   lengths must work).
  */
@@ -346,6 +353,19 @@ rp_status rp_exp_cr(const double* d_x, double* d_y, size_t n, void* cuda_stream)
  * reset != 0 zeroes the counters after reading them.  Reads device memory:
  * call it after the fills it should count have completed. */
 rp_status rp_debug_counters(uint64_t* h_counts, int reset);
+
+/* Test hooks of the device error paths (no counterpart in the paper): they
+ * make the bounded waits and capacity checks of later fills fail on purpose,
+ * without faulting or hanging the GPU.  kind 0 clears every hook; 1: the
+ * look-back waits give up after `value` spins (default 2^25) and report
+ * RP_ERR_TIMEOUT; 2: tile value - 1 of each launch publishes no count, so
+ * its successors' waits run out (0: none); 3: the tail queue holds at most
+ * `value` entries (a fill that needs more fails with RP_ERR_INTERNAL);
+ * 4: at most `value` tiles per launch for the sampled fills, so that the
+ * fill continues over further launches (more than 64 fail with
+ * RP_ERR_INTERNAL).  Host state only; returns RP_ERR_PARAM for an unknown
+ * kind. */
+rp_status rp_debug_faults(int kind, uint64_t value);
 
 /* Message of the last failed call on this host thread ("" if none). */
 const char* rp_last_error(void);

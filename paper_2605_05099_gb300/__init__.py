@@ -73,6 +73,7 @@ def lib():
             "rp_log_cr": [vp, vp, sz, vp],
             "rp_exp_cr": [vp, vp, sz, vp],
             "rp_debug_counters": [pu64, i32],
+            "rp_debug_faults": [i32, u64],
             "rp_substream_state": [i32, u64, u64, pu64, ctypes.POINTER(i32)],
             "rp_batch_plan_create": [ctypes.POINTER(Request), sz, i32, u64, i32, ctypes.POINTER(vp), vp],
             "rp_batch_plan_run": [vp, pu64, vp],
@@ -448,6 +449,15 @@ def rp_debug_counters(reset=False):
     c = (ctypes.c_uint64 * 6)()
     _check(lib().rp_debug_counters(c, 1 if reset else 0))
     return dict(zip(DEBUG_COUNTERS, (int(x) for x in c)))
+
+
+FAULTS = {"clear": 0, "spin_max": 1, "stall_tile": 2, "tail_cap": 3, "tile_cap": 4}
+
+
+def rp_debug_faults(kind, value=0):
+    """Set a test hook of the device error paths (see include/rp.h); kind is
+    a key of FAULTS or its number."""
+    _check(lib().rp_debug_faults(FAULTS.get(kind, kind), int(value)))
 
 
 def rp_exp_cr(x, y=None, cuda_stream=None):

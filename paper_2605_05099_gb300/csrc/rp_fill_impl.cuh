@@ -282,10 +282,14 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int* warp_sums, int* 
 // knows: the walk never goes past it, so a look-back spans at most one grid
 // of predecessors even when a whole round of tiles finishes together.
 // Returns the tile's exclusive prefix in all lanes, or ~0 if the bounded wait
-// ran out or the tile became unnecessary.
+// ran out or the tile became unnecessary.  spin_max (0: kSpinMax) bounds the
+// wait; stall_tile1 - 1 names a tile that publishes nothing (test hooks).
 __device__ unsigned long long lookback_warp(unsigned long long* st, unsigned long long k, unsigned long long cnt,
-                                           Ctrl* ctrl, long long kp = -1, unsigned long long incp = 0) {
+                                           Ctrl* ctrl, long long kp = -1, unsigned long long incp = 0,
+                                           unsigned long long spin_max = 0, unsigned long long stall_tile1 = 0) {
   constexpr int kW = 1;
+  if (stall_tile1 && k + 1 == stall_tile1) return ~0ull;   // test hook: this tile never publishes
+  const unsigned long long smax = spin_max ? spin_max : kSpinMax;
   const unsigned long long AGG = 1ull << 63, INC = 1ull << 62, VAL = INC - 1;
   const int lane = threadIdx.x & 31;
   if (k == 0) {
@@ -322,7 +326,7 @@ __device__ unsigned long long lookback_warp(unsigned long long* st, unsigned lon
       int stop = 0;
       if (lane == 0) {
         if (ld_volatile(&ctrl->done_tile) < k) stop = 1;
-        else if (++spins > kSpinMax) { set_err(ctrl, E_TIMEOUT, k); stop = 1; }
+        else if (++spins > smax) { set_err(ctrl, E_TIMEOUT, k); stop = 1; }
       }
       if (__shfl_sync(0xffffffffu, stop, 0)) return ~0ull;
       __nanosleep(64);
@@ -586,7 +590,8 @@ __device__ bool merge_tile(const FillArgs& a, u64 k, const E& e, MergeSmem<NT>& 
   // ---------------- offsets
   int off = block_exclusive_scan<NT>(cnt, sm.wsum, &sm.misc[1]);
   if (t < 32) {
-    unsigned long long ex = lookback_warp(a.tile_status, k, (unsigned long long)sm.misc[1], a.ctrl);
+    unsigned long long ex = lookback_warp(a.tile_status, k, (unsigned long long)sm.misc[1], a.ctrl, -1, 0,
+                                          a.spin_max, a.stall_tile1);
     if (t == 0) {
       sm.misc[2] = (int)(ex & 0x7fffffff);
       sm.misc[3] = (int)(ex >> 31);

@@ -40,6 +40,30 @@ rp_status cuda_fail(int e, const char* where) {
   return fail(RP_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString((cudaError_t)e));
 }
 
+// The allocating entry points keep their device state (scratch, jump
+// tables, the uploaded ziggurat tables, plans) for one device: the one
+// current at their first call.  A call with another device current is
+// refused before it launches anything.  Caller holds g_mu.
+int g_dev = -1;
+rp_status device_guard() {
+  int d = 0;
+  const int e = (int)cudaGetDevice(&d);
+  if (e) return cuda_fail(e, "current device");
+  if (g_dev < 0) g_dev = d;
+  else if (d != g_dev)
+    return fail(RP_ERR_PARAM, "this library's allocating entry points serve one device per process: first used on device " +
+                                  std::to_string(g_dev) + ", now called with device " + std::to_string(d) + " current");
+  return RP_OK;
+}
+
+// Test hooks of the device error paths (rp_debug_faults); zero: off.
+struct DebugFaults {
+  u64 spin_max = 0;     // look-back waits give up after this many spins
+  u64 stall_tile1 = 0;  // tile (value - 1) of each launch publishes nothing
+  u64 tail_cap = 0;     // tail queue capacity
+  u64 tile_cap = 0;     // tiles per launch of the sampled (non one-word) fills
+} g_faults;
+
 // ---------------------------------------------------------------- seeding
 // Seed and spawn key are hashed into a pool of four 32-bit words, then
 // hashed out to the requested number of state words (Sec. 2.3; NumPy
@@ -544,6 +568,8 @@ rp_status run_fill_state_locked(int engine, const u64 s_in[4], u64* pos, size_t 
     return RP_OK;
   }
   u64 s[4] = {s_in[0], s_in[1], s_in[2], s_in[3]};
+  rp_status dg = device_guard();
+  if (dg) return dg;
   int e = ensure_zig();
   if (e) return cuda_fail(e, "ziggurat table upload");
 
@@ -582,6 +608,7 @@ rp_status run_fill_state_locked(int engine, const u64 s_in[4], u64* pos, size_t 
       tiles = grid;
     } else {
       tiles = (u64)(need / (double)T) + 2;
+      if (g_faults.tile_cap && tiles > g_faults.tile_cap) tiles = g_faults.tile_cap;
       grid = std::min<u64>(tiles, (u64)sm_count() * occ);
     }
     // engine at word `cur`
@@ -625,8 +652,11 @@ rp_status run_fill_state_locked(int engine, const u64 s_in[4], u64* pos, size_t 
       a.ctrl = g_scr.ctrl;
       a.tailq = g_scr.tailq;
       a.tail_cap = queued ? g_scr.tail_cap : 0;
+      if (g_faults.tail_cap && a.tail_cap > g_faults.tail_cap) a.tail_cap = g_faults.tail_cap;
       a.tail_count = &g_scr.ctrl->n_tail;
       a.park = g_scr.park;
+      a.spin_max = g_faults.spin_max;
+      a.stall_tile1 = g_faults.stall_tile1;
       rp::Ctrl c0;
       memset(&c0, 0, sizeof(c0));
       c0.done_tile = ~0ull;
@@ -908,6 +938,7 @@ rp_status rp_gamma_grad(const double* d_z, double alpha, const double* d_g, size
   if (d_g && !h_grad_alpha) return fail(RP_ERR_NULL, "h_grad_alpha is NULL while upstream gradients are given");
   if (!d_g && !d_dzda) return fail(RP_ERR_NULL, "nothing to compute: both d_g and d_dzda are NULL");
   std::lock_guard<std::mutex> lk(g_mu);
+  if (rp_status dg = device_guard()) return dg;
   int e = ensure_grad_scratch();
   if (e) return fail(RP_ERR_NOMEM, "gradient scratch allocation failed");
   double* out = g_grad_part + 2 * (size_t)rp::grad_blocks();
@@ -934,6 +965,7 @@ rp_status rp_beta_grad(const double* d_z, double a, double b, const double* d_g,
   if (d_g && (!h_grad_a || !h_grad_b)) return fail(RP_ERR_NULL, "h_grad_a/h_grad_b is NULL while upstream gradients are given");
   if (!d_g && !d_dzda && !d_dzdb) return fail(RP_ERR_NULL, "nothing to compute");
   std::lock_guard<std::mutex> lk(g_mu);
+  if (rp_status dg = device_guard()) return dg;
   int e = ensure_grad_scratch();
   if (e) return fail(RP_ERR_NOMEM, "gradient scratch allocation failed");
   double* out = g_grad_part + 2 * (size_t)rp::grad_blocks();
@@ -1550,6 +1582,7 @@ extern "C" rp_status rp_batch_plan_create(const rp_request* reqs, size_t nreq, r
   if (nreq && !reqs) return fail(RP_ERR_NULL, "reqs is NULL");
   if (engine < 1 || engine > 5) return fail(RP_ERR_ENGINE, "unknown engine id " + std::to_string((int)engine));
   std::lock_guard<std::mutex> lk(g_mu);
+  if (rp_status dg = device_guard()) return dg;
   int e = ensure_zig();
   if (e) return cuda_fail(e, "ziggurat table upload");
   rp_batch_plan* P = new rp_batch_plan();
@@ -1661,6 +1694,7 @@ extern "C" rp_status rp_batch_plan_create(const rp_request* reqs, size_t nreq, r
 extern "C" rp_status rp_batch_plan_run(rp_batch_plan* plan, uint64_t* next_pos, void* cuda_stream) {
   if (!plan) return fail(RP_ERR_NULL, "plan is NULL");
   std::lock_guard<std::mutex> lk(g_mu);
+  if (rp_status dg = device_guard()) return dg;
   rp_status st = batch_launch(*plan, plan->exec, cuda_stream);
   if (st) return st;
   return batch_finish(*plan, plan->tiles, (u64*)next_pos, cuda_stream);
@@ -1728,6 +1762,7 @@ extern "C" rp_status rp_mvn_grads(int d, size_t n, const double* d_G, const doub
   if (!d_gmu || !d_gL) return fail(RP_ERR_NULL, "NULL device pointer");
   if (n && (!d_G || !d_Z)) return fail(RP_ERR_NULL, "NULL device pointer");
   std::lock_guard<std::mutex> lk(g_mu);
+  if (rp_status dg = device_guard()) return dg;
   if (n == 0) {
     int e = (int)cudaMemsetAsync(d_gmu, 0, (size_t)d * 8, (cudaStream_t)cuda_stream);
     if (!e) e = (int)cudaMemsetAsync(d_gL, 0, (size_t)d * d * 8, (cudaStream_t)cuda_stream);
@@ -1750,6 +1785,18 @@ extern "C" rp_status rp_mvn_grads(int d, size_t n, const double* d_G, const doub
   if (e) return cuda_fail(e, "mvn grads");
   g_launches.fetch_add(4);
   return RP_OK;
+}
+
+extern "C" rp_status rp_debug_faults(int kind, uint64_t value) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  switch (kind) {
+    case 0: g_faults = DebugFaults(); return RP_OK;
+    case 1: g_faults.spin_max = value; return RP_OK;
+    case 2: g_faults.stall_tile1 = value; return RP_OK;
+    case 3: g_faults.tail_cap = value; return RP_OK;
+    case 4: g_faults.tile_cap = value; return RP_OK;
+    default: return fail(RP_ERR_PARAM, "unknown debug fault kind " + std::to_string(kind));
+  }
 }
 
 extern "C" rp_status rp_debug_counters(uint64_t* h_counts, int reset) {

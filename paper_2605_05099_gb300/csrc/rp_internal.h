@@ -106,6 +106,11 @@ struct FillArgs {
   int tail_abs;                     // 1: TailEntry.g is the output's address (batches), 0: its index
   int req;                          // request index within a batch
   unsigned long long* park;         // one-pass bounded fill: grid x tile words of parked values
+  // test hooks (zero: off): look-back waits give up after spin_max spins
+  // instead of kSpinMax; tile stall_tile1 - 1 publishes nothing, so that its
+  // successors' waits run out
+  unsigned long long spin_max;
+  unsigned long long stall_tile1;
 };
 
 // Batched fills: one work item is one tile of one request.  Items of a

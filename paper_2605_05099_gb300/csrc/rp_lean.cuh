@@ -513,7 +513,8 @@ __device__ bool lean_tile(const FillArgs& a, u64 k, const E& e, LeanSmem<NT, C>&
     // ---------------- offsets
     const int off = block_exclusive_scan<NT>(cnt, sm.wsum, &sm.misc[1]);   // also orders the queue reads before staging
     if (t < 32) {
-      unsigned long long ex = lookback_warp(a.tile_status, k, (unsigned long long)sm.misc[1], a.ctrl);
+      unsigned long long ex = lookback_warp(a.tile_status, k, (unsigned long long)sm.misc[1], a.ctrl, -1, 0,
+                                            a.spin_max, a.stall_tile1);
       if (t == 0) {
         sm.misc[2] = (int)(ex & 0x7fffffff);
         sm.misc[3] = (int)(ex >> 31);

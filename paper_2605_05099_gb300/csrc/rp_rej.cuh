@@ -78,7 +78,8 @@ __device__ bool rej_tile(const FillArgs& a, u64 k, const E& e, RejSmem<NT>& sm, 
   // ---------------- offsets
   const int off = block_exclusive_scan<NT>(cnt, sm.wsum, &sm.misc[1]);   // also orders the parked runs before pass 2
   if (t < 32) {
-    unsigned long long ex = lookback_warp(a.tile_status, k, (unsigned long long)sm.misc[1], a.ctrl, fl.k, fl.inc);
+    unsigned long long ex = lookback_warp(a.tile_status, k, (unsigned long long)sm.misc[1], a.ctrl, fl.k, fl.inc,
+                                          a.spin_max, a.stall_tile1);
     fl.k = (long long)k;
     fl.inc = ex + (unsigned long long)sm.misc[1];
     if (t == 0) {
