@@ -916,12 +916,12 @@ rp_status rp_fill_derived(rp_engine engine, uint64_t seed, uint64_t stream, uint
 }
 
 namespace {
-double* g_grad_part = nullptr;   // device: block partials (2 per block) + 2 results
+double* g_grad_part = nullptr;   // device: block partials (2 per block), 2 results, gamma tables
 double* g_grad_h = nullptr;      // pinned host copy of the 2 results
 
 int ensure_grad_scratch() {
   if (!g_grad_part) {
-    int e = (int)cudaMalloc((void**)&g_grad_part, sizeof(double) * (2 * (size_t)rp::grad_blocks() + 2));
+    int e = (int)cudaMalloc((void**)&g_grad_part, sizeof(double) * rp::grad_scratch_doubles());
     if (e) { g_grad_part = nullptr; return e; }
     e = (int)cudaMallocHost((void**)&g_grad_h, 2 * sizeof(double));
     if (e) return e;

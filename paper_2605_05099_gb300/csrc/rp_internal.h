@@ -147,6 +147,8 @@ int launch_tails(const FillArgs& a, void* stream);
 int launch_pairs(const double* g, double* out, unsigned long long m, int mode, const double* p, void* stream);
 // gradients (rp_grad.cu)
 int grad_blocks();
+// block partials (2 per block), the 2 results, then the gamma gradient's tables
+size_t grad_scratch_doubles();
 int launch_gamma_grad(const double* z, const double* g, size_t n, double alpha, double* dz, double* part, double* out,
                       void* stream);
 int launch_beta_grad(const double* z, const double* g, size_t n, double a, double b, double* dza, double* dzb,

@@ -28,7 +28,7 @@ def _tol(ref, z, lo_tail, hi_tail):
     return t
 
 
-@pytest.mark.parametrize("alpha", [0.3, 1.0, 2.5, 30.0])
+@pytest.mark.parametrize("alpha", [0.05, 0.3, 1.0, 2.5, 3.0, 7.5, 30.0, 150.0])
 def test_gamma_dzda(alpha):
     z, _ = gpu_fill("gamma", "xoshiro256pp", 7, None, 0, 3000, (alpha,))
     # add grid points spanning both regimes and the extreme tails
@@ -44,6 +44,60 @@ def test_gamma_dzda(alpha):
     lo, hi = special.gammaincinv(alpha, 1e-6), special.gammaincinv(alpha, 1 - 1e-6)
     rel = np.abs(got - ref) / np.abs(ref)
     assert np.all(rel <= _tol(ref, z, lo, hi)), (alpha, float(rel.max()), z[np.argmax(rel)])
+
+
+def _gamma_grad(z, alpha, g=None):
+    zt = torch.tensor(z, device="cuda")
+    dz = torch.empty_like(zt)
+    gt = None if g is None else torch.tensor(g, device="cuda")
+    s = rp.rp_gamma_grad(zt, alpha, g=gt, dzda=dz)
+    return dz.cpu().numpy(), s
+
+
+@pytest.mark.parametrize("alpha", [2.5, 30.0, 1.0000001])
+def test_gamma_dzda_branch_boundary_and_edges(alpha):
+    """z at and next to alpha + 1 (where the series gives way to the
+    continued fraction), z <= 0 and NaN (gradient 0), in windows of every
+    ragged length around the 256-sample sort window and the 32-lane batch."""
+    a1 = alpha + 1.0
+    near = [np.nextafter(a1, 0.0), a1, np.nextafter(a1, 2 * a1), a1 * (1 - 1e-9), a1 * (1 + 1e-9)]
+    rng = np.random.default_rng(5)
+    for n in (1, 31, 33, 255, 257, 1000):
+        z = rng.gamma(alpha, size=n)
+        pos = rng.choice(n, size=min(n, 5), replace=False)
+        z[pos] = near[:len(pos)]
+        if n > 20:
+            z[7], z[11], z[13] = 0.0, -1.5, np.nan
+        got, _ = _gamma_grad(z, alpha)
+        ref = np.array([oracle.gamma_dzda(v, alpha) if v > 0 else 0.0 for v in z])
+        zero = ~(z > 0)
+        assert np.all(got[zero] == 0.0), (n, got[zero])
+        rel = np.abs(got[~zero] - ref[~zero]) / np.abs(ref[~zero])
+        assert np.all(rel <= 1e-12), (alpha, n, float(rel.max()), z[~zero][np.argmax(rel)])
+
+
+def test_gamma_grad_full_size_sampled():
+    """The timed workload (n = 2^26 gamma(2.5) variates, xoshiro256++ seed 7,
+    upstream g ~ N(0, 1)): sampled per-sample gradients against the oracle,
+    the reduced sum against the per-sample values, and a second call bit for
+    bit equal (the sums have a fixed order)."""
+    from paper_2605_05099_gb300 import inputs
+    n, alpha = 1 << 26, 2.5
+    z = torch.empty(n, dtype=torch.float64, device="cuda")
+    rp.rp_fill_gamma("xoshiro256pp", 7, rp.NO_STREAM, 0, alpha, z)
+    g = torch.tensor(inputs.upstream_grads(n), device="cuda")
+    dz = torch.empty_like(z)
+    s1 = rp.rp_gamma_grad(z, alpha, g=g, dzda=dz)
+    s2 = rp.rp_gamma_grad(z, alpha, g=g)
+    assert s1 == s2
+    idx = np.random.default_rng(9).choice(n, size=600, replace=False)
+    it = torch.tensor(idx, device="cuda")
+    zs, ds = z[it].cpu().numpy(), dz[it].cpu().numpy()
+    ref = np.array([oracle.gamma_dzda(v, alpha) for v in zs])
+    assert np.all(np.abs(ds - ref) <= 1e-12 * np.abs(ref))
+    # NumPy's pairwise sum is within about log2(n) 2^-53 sum|x| of the exact sum
+    prod = (g * dz).cpu().numpy()
+    assert abs(s1 - float(prod.sum())) <= 1e-12 * float(np.abs(prod).sum())
 
 
 @pytest.mark.parametrize("ab", [(0.5, 0.5), (2.0, 5.0)])

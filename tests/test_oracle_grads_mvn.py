@@ -16,7 +16,7 @@ from scipy import special
 U_GRID = [1e-9, 1e-4, 0.01, 0.2, 0.5, 0.8, 0.99, 1 - 1e-6]
 
 
-@pytest.mark.parametrize("alpha", [0.3, 1.0, 2.5, 30.0])
+@pytest.mark.parametrize("alpha", [0.05, 0.3, 1.0, 2.5, 3.0, 7.5, 30.0, 150.0])
 def test_gamma_dzda_vs_mpmath(orc, alpha):
     mp.mp.dps = 40
     for u in U_GRID:
