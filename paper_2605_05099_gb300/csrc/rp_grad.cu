@@ -201,71 +201,117 @@ __device__ double gamma_dzda_warp(double z, bool valid, double a, const double* 
   return d;
 }
 
-// Continued fraction K(p, q, x) of the incomplete beta with dK/dp, dK/dq:
-// K = 1/(1 + d1/(1 + d2/(1 + ...))), d_{2m+1} = -(p+m)(p+q+m) x / ((p+2m)(p+2m+1)),
-// d_{2m} = m (q-m) x / ((p+2m-1)(p+2m)); backward evaluation with a fixed depth.
-struct Tri {
-  double v, p, q;
-};
-__device__ __forceinline__ Tri tdiv(Tri a, Tri b) {
-  const double ib = rcp_nr(b.v);
-  const double r = a.v * ib;
-  return {r, (a.p - r * b.p) * ib, (a.q - r * b.q) * ib};
-}
+// ---------------------------------------------------------------------------
+// Beta: the continued fraction K(p, q, x) of the incomplete beta with dK/dp,
+// dK/dq, K = 1/(1 + d_1/(1 + d_2/(1 + ...))),
+//   d_{2m+1} = -(p+m)(p+q+m) x / ((p+2m)(p+2m+1)),
+//   d_{2m}   = m (q-m) x / ((p+2m-1)(p+2m)),
+// evaluated backward in triples (value, d/dp, d/dq).  Every d_j and both its
+// derivatives are x times a per-fill coefficient, tabled for the two
+// orientations o = 0 ((p, q, x) = (a, b, z)) and o = 1 ((b, a, 1 - z), the
+// reflection I_z(a, b) = 1 - I_{1-z}(b, a)); FP32 copies of the coefficients
+// and of derivative-safe magnitudes serve the depth bound.
+constexpr int kBetaMax = 600;                 // depth at most
+constexpr int kBJ = kBetaMax + 1;             // entries per orientation
+constexpr int kBE = 16, kBEp = kBE + 2 * kBJ, kBEq = kBEp + 2 * kBJ, kBF = kBEq + 2 * kBJ;
+constexpr int kBetaTabDoubles = kBF + 2 * kBJ;   // then 2 x 2 x kBJ floats (= 2 kBJ doubles)
+// constants: [0] split (a+1)/(a+b+2), [1] its mirror (b+1)/(a+b+2), then per
+// orientation [2+3o] 1/p, [3+3o] -1/p - psi(p) + psi(p+q), [4+3o] psi(p+q) - psi(q)
 
-__device__ Tri beta_cf(double p, double q, double x, int depth) {
-  Tri t = {1.0, 0.0, 0.0};
-  for (int j = depth; j >= 1; --j) {
-    Tri dj;
+__global__ void __launch_bounds__(kTabThreads) k_beta_tab(double a, double b, double* __restrict__ tab) {
+  float* Ff = (float*)(tab + kBF);    // [o][j] coefficient, then [o][j] magnitude
+  for (int idx = threadIdx.x; idx < 2 * kBJ; idx += kTabThreads) {
+    const int o = idx / kBJ, j = idx % kBJ;
+    const double p = o ? b : a, q = o ? a : b;
+    double v = 0.0, dp = 0.0, dq = 0.0, mag = 0.0;
     if (j & 1) {
-      int m = (j - 1) / 2;
-      double A = p + m, B = p + q + m, C = p + 2 * m, D = C + 1.0;
-      double num = -A * B * x, iden = rcp_nr(C * D);
-      double v = num * iden;
-      // d/dp: num' = -(B + A) x, den' = C + D ; d/dq: num' = -A x, den' = 0
-      double dp = (-(A + B) * x - v * (C + D)) * iden;
-      double dq = (-A * x) * iden;
-      dj = {v, dp, dq};
-    } else {
-      int m = j / 2;
-      double C = p + 2 * m - 1.0, D = C + 1.0;
-      double num = m * (q - m) * x, iden = rcp_nr(C * D);
-      double v = num * iden;
-      double dp = (-v * (C + D)) * iden;
-      double dq = (m * x) * iden;
-      dj = {v, dp, dq};
+      const int m = (j - 1) / 2;
+      const double A = p + m, B = p + q + m, C = p + 2 * m, D = C + 1.0;
+      v = -A * B / (C * D);
+      // d/dp: num' = -(B + A), den' = C + D; d/dq: num' = -A, den' = 0
+      dp = (-(A + B) - v * (C + D)) / (C * D);
+      dq = -A / (C * D);
+      mag = fabs(v);
+    } else if (j > 0) {
+      const int m = j / 2;
+      const double C = p + 2 * m - 1.0, D = C + 1.0;
+      v = m * (q - m) / (C * D);
+      dp = -v * (C + D) / (C * D);
+      dq = m / (C * D);
+      // at least m / (C D): a fraction that terminates (integer q) still
+      // gets the depth its q-derivative needs
+      mag = m * fmax(fabs(q - m), 1.0) / (C * D);
     }
-    Tri one_plus = {1.0 + 0.0, 0.0, 0.0};
-    Tri r = tdiv(dj, t);
-    t = {one_plus.v + r.v, r.p, r.q};
+    tab[kBE + idx] = v;
+    tab[kBEp + idx] = dp;
+    tab[kBEq + idx] = dq;
+    Ff[idx] = (float)v;
+    Ff[2 * kBJ + idx] = (float)mag;
   }
-  return tdiv(Tri{1.0, 0.0, 0.0}, t);
+  if (threadIdx.x == 0) {
+    const double pa = digamma_dev(a), pb = digamma_dev(b), pab = digamma_dev(a + b);
+    tab[0] = (a + 1.0) / (a + b + 2.0);
+    tab[1] = (b + 1.0) / (a + b + 2.0);
+    tab[2] = 1.0 / a;
+    tab[3] = -1.0 / a - pa + pab;
+    tab[4] = pab - pb;
+    tab[5] = 1.0 / b;
+    tab[6] = -1.0 / b - pb + pab;
+    tab[7] = pab - pa;
+  }
 }
 
-// d z / d a and d z / d b for z ~ Beta(a, b); pa, pb, pab = psi(a), psi(b),
-// psi(a + b) (fixed per fill)
-__device__ void beta_dzdab_dev(double z, double a, double b, double pa, double pb, double pab, double* dza,
-                               double* dzb) {
-  if (!(z > 0.0) || !(z < 1.0)) { *dza = 0.0; *dzb = 0.0; return; }
-  int depth = 40 + (int)(6.0 * sqrt(a + b));
-  if (depth > 600) depth = 600;
-  if (z < (a + 1.0) / (a + b + 2.0)) {
-    Tri K = beta_cf(a, b, z, depth);
-    double s = z * (1.0 - z) / a;
-    double dIa = s * ((log(z) - 1.0 / a - pa + pab) * K.v + K.p);
-    double dIb = s * ((log1p(-z) - pb + pab) * K.v + K.q);
-    *dza = -dIa;
-    *dzb = -dIb;
-  } else {
-    // I_z(a, b) = 1 - I_y(b, a), y = 1 - z: p = b, q = a
-    double y = 1.0 - z;
-    Tri K = beta_cf(b, a, y, depth);
-    double s = y * (1.0 - y) / b;
-    double dIy_dp = s * ((log(y) - 1.0 / b - pb + pab) * K.v + K.p);   // d/db
-    double dIy_dq = s * ((log1p(-y) - pa + pab) * K.v + K.q);          // d/da
-    *dza = dIy_dq;
-    *dzb = dIy_dp;
+// dz/da and dz/db for one sample per lane (lanes of similar z, as for the
+// gamma gradient); both orientations run the same loop at the warp's
+// largest depth.
+__device__ void beta_dzdab_warp(double z, bool valid, const double* __restrict__ tab, double* dza, double* dzb) {
+  const unsigned FULL = 0xffffffffu;
+  valid = valid && z > 0.0 && z < 1.0;
+  const int o = valid && !(z < __ldg(tab)) ? 1 : 0;
+  const double x = valid ? (o ? 1.0 - z : z) : 0.5;
+  const float* Ef = (const float*)(tab + kBF) + o * kBJ;
+  const float* Mf = Ef + 2 * kBJ;
+  // depth: eps_k = eps_{k-1} |d_k| / (|c_k| |e_{k-1}|), c and e the ratios
+  // of successive convergents' numerators and denominators; stop at 2^-60
+  const float xf = (float)x;
+  float c = 1.0f + xf * __ldg(Ef + 1), e = 1.0f;
+  float eps = __fdividef(xf * __ldg(Mf + 1), fabsf(c));
+  int kf = 1;
+  bool fin = !valid || !(eps >= 8.67361738e-19f);
+  while (!__all_sync(FULL, fin)) {
+    if (!fin) {
+      ++kf;
+      const float dk = xf * __ldg(Ef + kf), eprev = e;
+      c = 1.0f + __fdividef(dk, c);
+      e = 1.0f + __fdividef(dk, e);
+      if (fabsf(c) < 1e-30f) c = 1e-30f;
+      if (fabsf(e) < 1e-30f) e = 1e-30f;
+      eps = eps * __fdividef(xf * __ldg(Mf + kf), fabsf(c) * fabsf(eprev));
+      fin = !(eps >= 8.67361738e-19f) || kf >= kBetaMax - 2;
+    }
   }
+  const int N = (int)__reduce_max_sync(FULL, valid ? (unsigned)(kf + 2) : 0u);
+  const double* E = tab + kBE + o * kBJ;
+  const double* Ep = tab + kBEp + o * kBJ;
+  const double* Eq = tab + kBEq + o * kBJ;
+  double tv = 1.0, tp = 0.0, tq = 0.0;
+  for (int j = N; j >= 1; --j) {
+    // t <- 1 + d_j / t in triples; 1/t as for the gamma fraction
+    double r;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(tv));
+    const double ee = __fma_rn(-tv, r, 1.0);
+    r = __fma_rn(r, __fma_rn(ee, ee, ee), r);
+    const double xr = x * r, rv = __ldg(E + j) * xr;
+    tp = __fma_rn(-rv, tp * r, __ldg(Ep + j) * xr);
+    tq = __fma_rn(-rv, tq * r, __ldg(Eq + j) * xr);
+    tv = 1.0 + rv;
+  }
+  const double K = rcp_nr(tv), Kp = -K * tp * K, Kq = -K * tq * K;
+  const double s = x * (1.0 - x) * __ldg(tab + 2 + 3 * o);
+  const double dIp = s * ((log(x) + __ldg(tab + 3 + 3 * o)) * K + Kp);
+  const double dIq = s * ((log1p(-x) + __ldg(tab + 4 + 3 * o)) * K + Kq);
+  *dza = !valid ? 0.0 : (o ? dIq : -dIp);
+  *dzb = !valid ? 0.0 : (o ? dIp : -dIq);
 }
 
 __device__ __forceinline__ double block_sum(double v, double* sh) {
@@ -280,74 +326,87 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
   return s;
 }
 
-// One warp per window of 256 consecutive samples: the window is sorted by
-// a key of z (eighth-binades below and above alpha + 1, series side first)
-// with a deterministic counting sort in shared memory, then taken 32 at a
-// time, so that each batch of lanes runs the same branch with similar trip
-// counts.  Each lane's sum takes its samples in an order fixed by the data,
-// and the block sums have a fixed shape: the result is deterministic.
+// One warp per window of 256 consecutive samples: the window is sorted by a
+// key of z with a deterministic counting sort in shared memory, then taken 32
+// at a time, so that each batch of lanes runs the same branch with similar
+// trip counts.  Each lane's sum takes its samples in an order fixed by the
+// data, and the block sums have a fixed shape: the result is deterministic.
 constexpr int kWinPerLane = 8, kWin = 32 * kWinPerLane, kKeys = 32;
+constexpr int kWarps = kGradThreads / 32;
 
-__device__ __forceinline__ int gamma_key(double z, long long a1bits) {
-  const long long d = (__double_as_longlong(z) - a1bits) >> 49;   // eighth-binades from alpha + 1
-  const long long k = d < 0 ? 15 + max(d + 1, -15ll) : 16 + min(d, 15ll);
-  return (int)k;
+struct WindowSmem {
+  double z[kWarps][kWin];
+  unsigned char i[kWarps][kWin];
+  int cnt[kWarps][kKeys];
+};
+
+// Sorts window `base` of z into sm.z[wid] / sm.i[wid] (slot -> offset in the
+// window) by key(z) in [0, kKeys); entries past n get key kKeys - 1.
+template <class KeyFn>
+__device__ __forceinline__ void sort_window(const double* __restrict__ z, size_t n, size_t base, KeyFn key_of,
+                                            WindowSmem& sm, int wid, int lane) {
+  const unsigned FULL = 0xffffffffu, lt = (1u << lane) - 1u;
+  double zv[kWinPerLane];
+  int key[kWinPerLane], off[kWinPerLane];
+#pragma unroll
+  for (int m = 0; m < kWinPerLane; ++m) {
+    const size_t i = base + m * 32 + lane;
+    zv[m] = i < n ? z[i] : 0.0;
+    key[m] = i < n ? key_of(zv[m]) : kKeys - 1;
+  }
+  sm.cnt[wid][lane] = 0;
+  __syncwarp();
+#pragma unroll
+  for (int m = 0; m < kWinPerLane; ++m) {
+    const unsigned peers = __match_any_sync(FULL, key[m]);
+    const int before = sm.cnt[wid][key[m]];
+    __syncwarp();
+    if ((peers & lt) == 0) sm.cnt[wid][key[m]] = before + __popc(peers);
+    __syncwarp();
+    off[m] = before + __popc(peers & lt);
+  }
+  const int c = sm.cnt[wid][lane];
+  int incl = c;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int u = __shfl_up_sync(FULL, incl, o);
+    if (lane >= o) incl += u;
+  }
+  const int excl = incl - c;
+#pragma unroll
+  for (int m = 0; m < kWinPerLane; ++m) {
+    const int p = __shfl_sync(FULL, excl, key[m]) + off[m];
+    sm.z[wid][p] = zv[m];
+    sm.i[wid][p] = (unsigned char)(m * 32 + lane);
+  }
+  __syncwarp();
+}
+
+// eighth-binades of x below the bit pattern `ref` (x < ref: keys 0-15, the
+// nearest 15), or above it (keys 16-31)
+__device__ __forceinline__ int binade_key(double x, long long ref) {
+  const long long d = (__double_as_longlong(x) - ref) >> 49;
+  return (int)(d < 0 ? 15 + max(d + 1, -15ll) : 16 + min(d, 15ll));
 }
 
 __global__ void __launch_bounds__(kGradThreads) k_gamma_grad(const double* __restrict__ z, const double* __restrict__ g,
                                                                size_t n, double alpha, const double* __restrict__ tab,
                                                                double* __restrict__ dz, double* __restrict__ part) {
-  constexpr int W = kGradThreads / 32;
-  __shared__ double sh[W];
-  __shared__ double s_z[W][kWin];
-  __shared__ unsigned char s_i[W][kWin];
-  __shared__ int s_cnt[W][kKeys];
-  const unsigned FULL = 0xffffffffu;
+  __shared__ double sh[kWarps];
+  __shared__ WindowSmem sm;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const unsigned lt = (1u << lane) - 1u;
   const long long a1bits = __double_as_longlong(alpha + 1.0);
   const size_t nwin = (n + kWin - 1) / kWin;
   double acc = 0.0;
-  for (size_t win = (size_t)blockIdx.x * W + wid; win < nwin; win += (size_t)gridDim.x * W) {
+  for (size_t win = (size_t)blockIdx.x * kWarps + wid; win < nwin; win += (size_t)gridDim.x * kWarps) {
     const size_t base = win * kWin;
-    double zv[kWinPerLane];
-    int key[kWinPerLane], off[kWinPerLane];
-#pragma unroll
-    for (int m = 0; m < kWinPerLane; ++m) {
-      const size_t i = base + m * 32 + lane;
-      zv[m] = i < n ? z[i] : 0.0;
-      key[m] = i < n ? gamma_key(zv[m], a1bits) : kKeys - 1;
-    }
-    s_cnt[wid][lane] = 0;
-    __syncwarp();
-#pragma unroll
-    for (int m = 0; m < kWinPerLane; ++m) {
-      const unsigned peers = __match_any_sync(FULL, key[m]);
-      const int before = s_cnt[wid][key[m]];
-      __syncwarp();
-      if ((peers & lt) == 0) s_cnt[wid][key[m]] = before + __popc(peers);
-      __syncwarp();
-      off[m] = before + __popc(peers & lt);
-    }
-    int c = s_cnt[wid][lane], incl = c;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int u = __shfl_up_sync(FULL, incl, o);
-      if (lane >= o) incl += u;
-    }
-    const int excl = incl - c;
-#pragma unroll
-    for (int m = 0; m < kWinPerLane; ++m) {
-      const int p = __shfl_sync(FULL, excl, key[m]) + off[m];
-      s_z[wid][p] = zv[m];
-      s_i[wid][p] = (unsigned char)(m * 32 + lane);
-    }
-    __syncwarp();
+    // series side (z < alpha + 1) first, then the continued fraction's
+    sort_window(z, n, base, [&](double v) { return binade_key(v, a1bits); }, sm, wid, lane);
     for (int b = 0; b < kWinPerLane; ++b) {
       const int p = b * 32 + lane;
-      const size_t i = base + s_i[wid][p];
+      const size_t i = base + sm.i[wid][p];
       const bool valid = i < n;
-      const double d = gamma_dzda_warp(s_z[wid][p], valid, alpha, tab);
+      const double d = gamma_dzda_warp(sm.z[wid][p], valid, alpha, tab);
       if (valid) {
         if (dz) dz[i] = d;
         if (g) acc += g[i] * d;
@@ -360,21 +419,45 @@ __global__ void __launch_bounds__(kGradThreads) k_gamma_grad(const double* __res
 }
 
 __global__ void __launch_bounds__(kGradThreads) k_beta_grad(const double* __restrict__ z, const double* __restrict__ g,
-                                                              size_t n, double a, double b, double* __restrict__ dza,
-                                                              double* __restrict__ dzb, double* __restrict__ part) {
-  __shared__ double sh[kGradThreads / 32];
-  const double pa = digamma_dev(a), pb = digamma_dev(b), pab = digamma_dev(a + b);
+                                                              size_t n, const double* __restrict__ tab,
+                                                              double* __restrict__ dza, double* __restrict__ dzb,
+                                                              double* __restrict__ part) {
+  __shared__ double sh[kWarps];
+  __shared__ WindowSmem sm;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const double split = tab[0];
+  const long long s0 = __double_as_longlong(split), s1 = __double_as_longlong(tab[1]);
+  const size_t nwin = (n + kWin - 1) / kWin;
   double aa = 0.0, ab = 0.0;
-  for (size_t i = blockIdx.x * (size_t)kGradThreads + threadIdx.x; i < n; i += (size_t)gridDim.x * kGradThreads) {
-    double da, db;
-    beta_dzdab_dev(z[i], a, b, pa, pb, pab, &da, &db);
-    if (dza) dza[i] = da;
-    if (dzb) dzb[i] = db;
-    if (g) { aa += g[i] * da; ab += g[i] * db; }
+  for (size_t win = (size_t)blockIdx.x * kWarps + wid; win < nwin; win += (size_t)gridDim.x * kWarps) {
+    const size_t base = win * kWin;
+    // orientation 0 (x = z below the split) on keys 0-15, orientation 1
+    // (x = 1 - z at or below the mirrored split) on 16-31; within each, x's
+    // eighth-binades below its split, the slowest (nearest) last
+    auto key = [&](double v) {
+      if (!(v > 0.0 && v < 1.0)) return 0;
+      const bool o = !(v < split);
+      const int k = min(binade_key(o ? 1.0 - v : v, o ? s1 : s0), 15);
+      return o ? 16 + k : k;
+    };
+    sort_window(z, n, base, key, sm, wid, lane);
+    for (int b = 0; b < kWinPerLane; ++b) {
+      const int p = b * 32 + lane;
+      const size_t i = base + sm.i[wid][p];
+      const bool valid = i < n;
+      double da, db;
+      beta_dzdab_warp(sm.z[wid][p], valid, tab, &da, &db);
+      if (valid) {
+        if (dza) dza[i] = da;
+        if (dzb) dzb[i] = db;
+        if (g) { aa += g[i] * da; ab += g[i] * db; }
+      }
+    }
+    __syncwarp();
   }
-  double s1 = block_sum(aa, sh);
-  double s2 = block_sum(ab, sh);
-  if (threadIdx.x == 0) { part[2 * blockIdx.x] = s1; part[2 * blockIdx.x + 1] = s2; }
+  const double s1s = block_sum(aa, sh);
+  const double s2s = block_sum(ab, sh);
+  if (threadIdx.x == 0) { part[2 * blockIdx.x] = s1s; part[2 * blockIdx.x + 1] = s2s; }
 }
 
 // fixed-order final reduction of the block partials (k values of stride k)
@@ -391,7 +474,7 @@ __global__ void k_sum_parts(const double* __restrict__ part, int nblk, int k, do
 }  // namespace
 
 int grad_blocks() { return 1216; }
-size_t grad_scratch_doubles() { return 2 * (size_t)grad_blocks() + 2 + kTabDoubles; }
+size_t grad_scratch_doubles() { return 2 * (size_t)grad_blocks() + 2 + (size_t)max(kTabDoubles, kBetaTabDoubles); }
 
 int launch_gamma_grad(const double* z, const double* g, size_t n, double alpha, double* dz, double* part, double* out,
                       void* stream) {
@@ -406,7 +489,9 @@ int launch_gamma_grad(const double* z, const double* g, size_t n, double alpha, 
 int launch_beta_grad(const double* z, const double* g, size_t n, double a, double b, double* dza, double* dzb,
                      double* part, double* out, void* stream) {
   cudaStream_t s = (cudaStream_t)stream;
-  k_beta_grad<<<grad_blocks(), kGradThreads, 0, s>>>(z, g, n, a, b, dza, dzb, part);
+  double* tab = part + 2 * (size_t)grad_blocks() + 2;
+  k_beta_tab<<<1, kTabThreads, 0, s>>>(a, b, tab);
+  k_beta_grad<<<grad_blocks(), kGradThreads, 0, s>>>(z, g, n, tab, dza, dzb, part);
   k_sum_parts<<<1, kGradThreads, 0, s>>>(part, grad_blocks(), 2, out);
   return (int)cudaGetLastError();
 }

@@ -944,7 +944,7 @@ rp_status rp_gamma_grad(const double* d_z, double alpha, const double* d_g, size
   double* out = g_grad_part + 2 * (size_t)rp::grad_blocks();
   e = rp::launch_gamma_grad(d_z, d_g, n, alpha, d_dzda, g_grad_part, out, cuda_stream);
   if (e) return cuda_fail(e, "gamma gradient launch");
-  g_launches.fetch_add(2);
+  g_launches.fetch_add(3);
   e = (int)cudaMemcpyAsync(g_grad_h, out, sizeof(double), cudaMemcpyDeviceToHost, (cudaStream_t)cuda_stream);
   if (!e) e = (int)cudaStreamSynchronize((cudaStream_t)cuda_stream);
   if (e) return cuda_fail(e, "gamma gradient");
@@ -971,7 +971,7 @@ rp_status rp_beta_grad(const double* d_z, double a, double b, const double* d_g,
   double* out = g_grad_part + 2 * (size_t)rp::grad_blocks();
   e = rp::launch_beta_grad(d_z, d_g, n, a, b, d_dzda, d_dzdb, g_grad_part, out, cuda_stream);
   if (e) return cuda_fail(e, "beta gradient launch");
-  g_launches.fetch_add(2);
+  g_launches.fetch_add(3);
   e = (int)cudaMemcpyAsync(g_grad_h, out, 2 * sizeof(double), cudaMemcpyDeviceToHost, (cudaStream_t)cuda_stream);
   if (!e) e = (int)cudaStreamSynchronize((cudaStream_t)cuda_stream);
   if (e) return cuda_fail(e, "beta gradient");

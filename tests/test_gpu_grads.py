@@ -100,7 +100,7 @@ def test_gamma_grad_full_size_sampled():
     assert abs(s1 - float(prod.sum())) <= 1e-12 * float(np.abs(prod).sum())
 
 
-@pytest.mark.parametrize("ab", [(0.5, 0.5), (2.0, 5.0)])
+@pytest.mark.parametrize("ab", [(0.5, 0.5), (2.0, 5.0), (0.7, 3.0), (3.0, 2.0), (30.0, 40.0)])
 def test_beta_dzdab(ab):
     a, b = ab
     from scipy import special
@@ -116,6 +116,30 @@ def test_beta_dzdab(ab):
     for got, r in ((da.cpu().numpy(), ref[:, 0]), (db.cpu().numpy(), ref[:, 1])):
         rel = np.abs(got - r) / np.abs(r)
         assert np.all(rel <= _tol(r, z, lo, hi)), (ab, float(rel.max()), z[np.argmax(rel)])
+
+
+def test_beta_dzdab_split_and_edges():
+    """z at and next to the split (a+1)/(a+b+2) between the two orientations,
+    z outside (0, 1) and NaN (gradients 0), in ragged windows."""
+    a, b = 2.0, 5.0
+    sp = (a + 1) / (a + b + 2)
+    near = [np.nextafter(sp, 0.0), sp, np.nextafter(sp, 1.0)]
+    rng = np.random.default_rng(6)
+    for n in (1, 33, 257, 700):
+        z = rng.beta(a, b, size=n)
+        pos = rng.choice(n, size=min(n, 3), replace=False)
+        z[pos] = near[:len(pos)]
+        if n > 20:
+            z[5], z[9], z[12], z[15] = 0.0, 1.0, -0.5, np.nan
+        zt = torch.tensor(z, device="cuda")
+        da, db = torch.empty_like(zt), torch.empty_like(zt)
+        rp.rp_beta_grad(zt, a, b, dzda=da, dzdb=db)
+        ok = (z > 0) & (z < 1)
+        ref = np.array([oracle.beta_dzdab(v, a, b) if 0 < v < 1 else (0.0, 0.0) for v in z])
+        for got, r in ((da.cpu().numpy(), ref[:, 0]), (db.cpu().numpy(), ref[:, 1])):
+            assert np.all(got[~ok] == 0.0)
+            rel = np.abs(got[ok] - r[ok]) / np.abs(r[ok])
+            assert np.all(rel <= 1e-12), (n, float(rel.max()), z[ok][np.argmax(rel)])
 
 
 def test_autograd_gamma_and_beta():

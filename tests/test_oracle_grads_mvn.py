@@ -46,7 +46,7 @@ def test_gamma_dzda_alpha1_closed_form(orc):
         assert abs(orc.gamma_dzda(z, 1.0) - ref) <= 1e-13 * abs(ref), z
 
 
-@pytest.mark.parametrize("ab", [(0.5, 0.5), (2.0, 5.0)])
+@pytest.mark.parametrize("ab", [(0.5, 0.5), (2.0, 5.0), (0.7, 3.0), (3.0, 2.0), (30.0, 40.0)])
 def test_beta_dzdab_vs_mpmath(orc, ab):
     a, b = ab
     mp.mp.dps = 40
