@@ -496,7 +496,8 @@ def run_extras(rp, stream):
 
 def run_profile(args):
     """One workload alone, for ncu (--profile KIND; not a bench line):
-    gamma:ALPHA, beta:A:B, grad:ALPHA (gamma gradient), mvn:D (forward and
+    gamma:ALPHA, beta:A:B, grad:ALPHA (gamma gradient), bgrad:A:B (beta
+    gradient), mvn:D (forward and
     backward, n = 2^20) or batch:ENGINE (4096 requests; --log2n scales the
     request sizes' upper end).  Runs --warmup untimed and --steps timed
     repetitions and prints their mean time."""
@@ -508,10 +509,16 @@ def run_profile(args):
     stream = torch.cuda.current_stream()
     kind, _, rest = args.profile.partition(":")
     vals = [x for x in rest.split(":") if x]
-    if kind in ("gamma", "beta", "grad"):
+    if kind in ("gamma", "beta", "grad", "bgrad"):
         n = 1 << args.log2n
         z = torch.empty(n, dtype=torch.float64, device="cuda")
-        if kind == "beta":
+        if kind == "bgrad":
+            ab = (float(vals[0]), float(vals[1]))
+            rp.rp_fill_beta("xoshiro256pp", 7, rp.NO_STREAM, 0, ab[0], ab[1], z, stream)
+            g = torch.tensor(inputs.upstream_grads(n), device="cuda")
+            dz, dz2 = torch.empty_like(z), torch.empty_like(z)
+            f = lambda: rp.rp_beta_grad(z, ab[0], ab[1], g, dz, dz2, stream)
+        elif kind == "beta":
             f = lambda: rp.rp_fill_beta("xoshiro256pp", 7, rp.NO_STREAM, 0, float(vals[0]), float(vals[1]), z, stream)
         else:
             a_ = float(vals[0])

@@ -294,19 +294,21 @@ __device__ void beta_dzdab_warp(double z, bool valid, const double* __restrict__
   const double* E = tab + kBE + o * kBJ;
   const double* Ep = tab + kBEp + o * kBJ;
   const double* Eq = tab + kBEq + o * kBJ;
-  double tv = 1.0, tp = 0.0, tq = 0.0;
+  // t <- 1 + d_j / t in triples, with the derivative parts kept divided by
+  // x (every d_j is x times a coefficient): with r = 1/t and v = E_j x r,
+  // t_p / x <- r (E^p_j - v t_p / x); 1/t as for the gamma fraction
+  double tv = 1.0, up = 0.0, uq = 0.0;
   for (int j = N; j >= 1; --j) {
-    // t <- 1 + d_j / t in triples; 1/t as for the gamma fraction
     double r;
     asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(tv));
     const double ee = __fma_rn(-tv, r, 1.0);
     r = __fma_rn(r, __fma_rn(ee, ee, ee), r);
-    const double xr = x * r, rv = __ldg(E + j) * xr;
-    tp = __fma_rn(-rv, tp * r, __ldg(Ep + j) * xr);
-    tq = __fma_rn(-rv, tq * r, __ldg(Eq + j) * xr);
+    const double rv = __ldg(E + j) * (x * r);
+    up = r * __fma_rn(-rv, up, __ldg(Ep + j));
+    uq = r * __fma_rn(-rv, uq, __ldg(Eq + j));
     tv = 1.0 + rv;
   }
-  const double K = rcp_nr(tv), Kp = -K * tp * K, Kq = -K * tq * K;
+  const double K = rcp_nr(tv), Kp = -K * (x * up) * K, Kq = -K * (x * uq) * K;
   const double s = x * (1.0 - x) * __ldg(tab + 2 + 3 * o);
   const double dIp = s * ((log(x) + __ldg(tab + 3 + 3 * o)) * K + Kp);
   const double dIq = s * ((log1p(-x) + __ldg(tab + 4 + 3 * o)) * K + Kq);
