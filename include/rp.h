@@ -27,10 +27,29 @@
  *   and F with equal shapes, the skew normal) also allocate a temporary of
  *   16 min(n, 2^26) bytes for the call and free it before returning.
  * - Streams: `cuda_stream` is a cudaStream_t (NULL = legacy default stream).
- *   Fill calls enqueue their kernels on it and return after they have
- *   completed (the call synchronises that stream once at the end to read
- *   the consumed-word count and the device status word).
- * - Threading: calls from several host threads are serialised internally.
+ *   Fill calls enqueue their kernels on it.  When they return depends on
+ *   the fill and on *pos:
+ *   - one-word fills (rp_fill_u64, rp_fill_uniform, rp_fill_uniform52,
+ *     rp_engine_fold) consume exactly n words: *pos is set on the host and
+ *     the call returns without waiting for the kernel;
+ *   - the other fills of rp_fill_u64's family and rp_fill_state, when pos
+ *     points to host-pinned memory (cudaMallocHost, cudaHostRegister, a
+ *     pinned torch tensor), enqueue their kernels, a one-thread kernel that
+ *     forms the end position and a copy of it to *pos, and return without
+ *     waiting.  *pos is valid once the stream is synchronised; it is
+ *     UINT64_MAX if the fill failed on the device, and rp_async_status then
+ *     gives the reason.  A later call that reads the same *pos first waits
+ *     for the pending write (an event), so fills chained through one pinned
+ *     word stay correct, and fills on several streams are ordered on the
+ *     device around the library's shared scratch.  Bounded fills take the
+ *     exact two-pass path in this mode;
+ *   - otherwise (pos in pageable memory, and the fills drawn as pairs of
+ *     base variates) the call synchronises the stream once at the end, to
+ *     read the consumed-word count and the device status word.
+ *   Gradients synchronise their stream to return the reduced sums.
+ * - Threading: calls from several host threads are serialised internally;
+ *   the lock is held while a call enqueues work, and across its final
+ *   synchronisation only in the synchronous cases above.
  * - Devices: the allocating entry points (fills, gradients, batch plans, the
  *   MVN) keep their scratch, jump tables and uploaded tables for the device
  *   that was current at their first call; a later call with another device
@@ -78,7 +97,8 @@ typedef int rp_status;
  *   seed    user seed (Sec. 2.3 seeding: seed + spawn key hashed into a
  *           128-bit pool; NumPy SeedSequence semantics)
  *   stream  spawn key, or RP_NO_STREAM
- *   pos     in: first stream word to use; out: next unused word (host ptr)
+ *   pos     in: first stream word to use; out: next unused word (host ptr;
+ *           written asynchronously when it is host-pinned, see Streams)
  *   n       number of variates
  *   d_out   device array of n elements
  * ------------------------------------------------------------------- */
@@ -366,6 +386,16 @@ rp_status rp_debug_counters(uint64_t* h_counts, int reset);
  * RP_ERR_INTERNAL).  Host state only; returns RP_ERR_PARAM for an unknown
  * kind. */
 rp_status rp_debug_faults(int kind, uint64_t value);
+
+/* Failures of asynchronous fills (pinned *pos, see Streams): synchronises
+ * cuda_stream (NULL: the whole device), then returns RP_OK if no
+ * asynchronous fill has failed since the last call, else RP_ERR_TIMEOUT (a
+ * bounded device wait gave up) or RP_ERR_INTERNAL (a device check failed, or
+ * the fill needed more tiles than its one launch planned), with the count
+ * and the device bits in rp_last_error(), and clears the record.  Library
+ * state only; the paper's interface has no counterpart (its fills are
+ * synchronous CPU calls). */
+rp_status rp_async_status(void* cuda_stream);
 
 /* Message of the last failed call on this host thread ("" if none). */
 const char* rp_last_error(void);

@@ -74,6 +74,7 @@ def lib():
             "rp_exp_cr": [vp, vp, sz, vp],
             "rp_debug_counters": [pu64, i32],
             "rp_debug_faults": [i32, u64],
+            "rp_async_status": [vp],
             "rp_substream_state": [i32, u64, u64, pu64, ctypes.POINTER(i32)],
             "rp_batch_plan_create": [ctypes.POINTER(Request), sz, i32, u64, i32, ctypes.POINTER(vp), vp],
             "rp_batch_plan_run": [vp, pu64, vp],
@@ -125,11 +126,31 @@ def _out(out, dtype):
     return ctypes.c_void_p(out.data_ptr()), out.numel()
 
 
+def _pinned_pos(pos):
+    """A 1-element int64/uint64 tensor in pinned host memory as a uint64*."""
+    if not (pos.numel() == 1 and not pos.is_cuda and pos.is_pinned() and pos.dtype in (torch.int64, torch.uint64)):
+        raise ValueError("an asynchronous position is a pinned 1-element int64/uint64 CPU tensor")
+    return ctypes.cast(ctypes.c_void_p(pos.data_ptr()), ctypes.POINTER(ctypes.c_uint64))
+
+
 def _fill(fn, engine, seed, stream, pos, out, dtype, extra=(), cuda_stream=None):
+    """pos: an int (returns the new position after the fill completed), or a
+    pinned 1-element tensor holding it (the library writes the new position
+    there asynchronously; it is valid after the stream is synchronised, and
+    the call returns None)."""
     p, n = _out(out, dtype)
+    if isinstance(pos, torch.Tensor):
+        _check(fn(_engine(engine), seed, stream, _pinned_pos(pos), n, *extra, p, _stream_handle(cuda_stream)))
+        return None
     cpos = ctypes.c_uint64(pos)
     _check(fn(_engine(engine), seed, stream, ctypes.byref(cpos), n, *extra, p, _stream_handle(cuda_stream)))
     return cpos.value
+
+
+def rp_async_status(cuda_stream=None):
+    """Synchronises the stream and raises RPError if an asynchronous fill
+    (pinned position) failed since the last check."""
+    _check(lib().rp_async_status(_stream_handle(cuda_stream)))
 
 
 # ---- fills: same names and argument order as the C ABI; `out` is a CUDA

@@ -10,6 +10,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <unordered_map>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -466,6 +467,79 @@ struct Scratch {
 };
 Scratch g_scr;
 
+// Asynchronous position writes.  A fill whose *pos is host-pinned memory
+// enqueues its kernels, a finishing kernel that forms the end position on the
+// device, and a copy of it to *pos, and returns without waiting: *pos is
+// valid after the stream is synchronised (all ones if the fill failed; then
+// rp_async_status gives the reason).  Each such *pos has an event; a later
+// call that reads the same *pos first waits for that event, so chaining fills
+// through one pinned word stays correct.  The scratch (tile status words,
+// control block, tail queue) is shared: a fill on another stream than the
+// last user of it waits for that user's event on the device, not on the host.
+struct AsyncState {
+  u64* dev = nullptr;                       // [0] end position, [1..3] sticky failure bits, count, info
+  std::unordered_map<u64*, cudaEvent_t> pending;
+  std::vector<cudaEvent_t> free_ev;
+  cudaEvent_t scr_ev = nullptr;             // recorded after the last use of the scratch
+  void* scr_stream = nullptr;
+  bool scr_used = false;
+};
+AsyncState g_async;
+
+cudaEvent_t take_event() {
+  if (!g_async.free_ev.empty()) {
+    cudaEvent_t e = g_async.free_ev.back();
+    g_async.free_ev.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return nullptr;
+  return e;
+}
+
+bool pinned_host(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeHost;
+}
+
+// Waits for an asynchronous write still pending on *pos.
+int wait_pending_pos(u64* pos) {
+  auto it = g_async.pending.find(pos);
+  if (it == g_async.pending.end()) return 0;
+  const int e = (int)cudaEventSynchronize(it->second);
+  g_async.free_ev.push_back(it->second);
+  g_async.pending.erase(it);
+  return e;
+}
+
+// Orders this stream's use of the shared scratch after the previous user's.
+int scratch_acquire(void* cstream) {
+  if (!g_async.scr_used || g_async.scr_stream == cstream) return 0;
+  return (int)cudaStreamWaitEvent((cudaStream_t)cstream, g_async.scr_ev, 0);
+}
+
+int scratch_release(void* cstream) {
+  if (!g_async.scr_ev) {
+    const int e = (int)cudaEventCreateWithFlags(&g_async.scr_ev, cudaEventDisableTiming);
+    if (e) return e;
+  }
+  g_async.scr_stream = cstream;
+  g_async.scr_used = true;
+  return (int)cudaEventRecord(g_async.scr_ev, (cudaStream_t)cstream);
+}
+
+int ensure_async_dev() {
+  if (g_async.dev) return 0;
+  int e = (int)cudaMalloc((void**)&g_async.dev, 4 * sizeof(u64));
+  if (!e) e = (int)cudaMemset(g_async.dev, 0, 4 * sizeof(u64));
+  if (e) g_async.dev = nullptr;
+  return e;
+}
+
 int ensure_park(size_t words) {
   if (words > g_scr.park_cap) {
     if (g_scr.park) cudaFree(g_scr.park);
@@ -551,18 +625,24 @@ double words_per_variate(int dist, const rp::SampArgs& sp) {
 // Fill from explicit state words (the engine at word 0 of the stream; *pos
 // words in).  Caller holds g_mu.
 rp_status run_fill_state_locked(int engine, const u64 s_in[4], u64* pos, size_t n, int dist, const rp::SampArgs& sp,
-                                void* d_out, void* cstream, u64* first_reject = nullptr) {
-  if (dist == rp::D_BOUNDED && (double)n * ((double)sp.thresh * 0x1.0p-64) < 0.05) {
+                                void* d_out, void* cstream, u64* first_reject = nullptr, int async_mode = -1) {
+  if (async_mode < 0) {
+    // top-level call: an earlier asynchronous write to *pos lands first
+    int e = wait_pending_pos(pos);
+    if (e) return cuda_fail(e, "pending position write");
+    async_mode = pinned_host(pos) ? 1 : 0;
+  }
+  if (dist == rp::D_BOUNDED && !async_mode && (double)n * ((double)sp.thresh * 0x1.0p-64) < 0.05) {
     // Rejections are unlikely in this fill: one pass writes word p's value
     // at output p and reports the first rejected word q.  Outputs before q
     // are final (the serial sampler gives the same values up to its first
     // rejection); from word q + 1 the exact two-pass fill takes over.
     u64 q = ~0ull, p0 = *pos;
-    rp_status st = run_fill_state_locked(engine, s_in, &p0, n, rp::D_BOUNDED_ONE, sp, d_out, cstream, &q);
+    rp_status st = run_fill_state_locked(engine, s_in, &p0, n, rp::D_BOUNDED_ONE, sp, d_out, cstream, &q, 0);
     if (st) return st;
     if (q >= n) { *pos += n; return RP_OK; }
     u64 p1 = *pos + q + 1;
-    st = run_fill_state_locked(engine, s_in, &p1, n - q, rp::D_BOUNDED, sp, (char*)d_out + q * 8, cstream);
+    st = run_fill_state_locked(engine, s_in, &p1, n - q, rp::D_BOUNDED, sp, (char*)d_out + q * 8, cstream, nullptr, 0);
     if (st) return st;
     *pos = p1;
     return RP_OK;
@@ -586,6 +666,11 @@ rp_status run_fill_state_locked(int engine, const u64 s_in[4], u64* pos, size_t 
   const bool trivial = (dist == rp::D_U64 || dist == rp::D_UNIFORM || dist == rp::D_BOUNDED_ONE ||
                         dist == rp::D_UNIFORM52 || dist == rp::D_FOLD);
   const bool one_pass_check = dist == rp::D_BOUNDED_ONE;
+  if (!trivial || one_pass_check) {
+    e = scratch_acquire(cstream);
+    if (!e && async_mode) e = ensure_async_dev();
+    if (e) return cuda_fail(e, "scratch ordering");
+  }
 
   u64 cur = *pos;
   size_t done = 0;
@@ -657,13 +742,10 @@ rp_status run_fill_state_locked(int engine, const u64 s_in[4], u64* pos, size_t 
       a.park = g_scr.park;
       a.spin_max = g_faults.spin_max;
       a.stall_tile1 = g_faults.stall_tile1;
-      rp::Ctrl c0;
-      memset(&c0, 0, sizeof(c0));
-      c0.done_tile = ~0ull;
-      c0.first_reject = ~0ull;
       e = (int)cudaMemsetAsync(g_scr.status, 0, tiles * 8, (cudaStream_t)cstream);
-      if (!e) e = (int)cudaMemcpyAsync(g_scr.ctrl, &c0, sizeof(c0), cudaMemcpyHostToDevice, (cudaStream_t)cstream);
+      if (!e) e = rp::launch_ctrl_reset(g_scr.ctrl, cstream);
       if (e) return cuda_fail(e, "scratch reset");
+      g_launches.fetch_add(1);
     }
     e = rp::launch_fill(a, (int)grid, cstream);
     if (e) return cuda_fail(e, "kernel launch");
@@ -674,16 +756,48 @@ rp_status run_fill_state_locked(int engine, const u64 s_in[4], u64* pos, size_t 
       g_launches.fetch_add(1);
     }
     if (trivial) {
-      if (one_pass_check)
+      // every word is an output: the end position is known here, and
+      // nothing needs to come back (the one-pass bounded check excepted)
+      if (one_pass_check) {
         e = (int)cudaMemcpyAsync(g_scr.h_ctrl, g_scr.ctrl, sizeof(rp::Ctrl), cudaMemcpyDeviceToHost, (cudaStream_t)cstream);
-      if (!e) e = (int)cudaStreamSynchronize((cudaStream_t)cstream);
-      if (e) return cuda_fail(e, "fill");
-      if (one_pass_check && first_reject) *first_reject = g_scr.h_ctrl->first_reject;
+        if (!e) e = scratch_release(cstream);
+        if (!e) e = (int)cudaStreamSynchronize((cudaStream_t)cstream);
+        if (e) return cuda_fail(e, "fill");
+        if (first_reject) *first_reject = g_scr.h_ctrl->first_reject;
+      }
       done = n;
       cur += left;
       break;
     }
+    if (async_mode) {
+      // one launch, sized above with an eight-sigma margin; the device forms
+      // the end position and the copy lands in the pinned *pos
+      e = rp::launch_finish(g_scr.ctrl, cur, g_async.dev, g_async.dev + 1, cstream);
+      if (e) return cuda_fail(e, "finishing kernel launch");
+      g_launches.fetch_add(1);
+      e = (int)cudaMemcpyAsync(pos, g_async.dev, sizeof(u64), cudaMemcpyDeviceToHost, (cudaStream_t)cstream);
+      if (!e) e = scratch_release(cstream);
+      cudaEvent_t ev = e ? nullptr : take_event();
+      if (!e && !ev) e = (int)cudaErrorMemoryAllocation;
+      if (!e) e = (int)cudaEventRecord(ev, (cudaStream_t)cstream);
+      if (e) return cuda_fail(e, "asynchronous position write");
+      if (g_async.pending.size() >= 256) {
+        // positions never read again: recycle the events that have fired
+        for (auto it = g_async.pending.begin(); it != g_async.pending.end();) {
+          if (cudaEventQuery(it->second) == cudaSuccess) {
+            g_async.free_ev.push_back(it->second);
+            it = g_async.pending.erase(it);
+          } else {
+            ++it;
+          }
+        }
+        cudaGetLastError();
+      }
+      g_async.pending[pos] = ev;
+      return RP_OK;
+    }
     e = (int)cudaMemcpyAsync(g_scr.h_ctrl, g_scr.ctrl, sizeof(rp::Ctrl), cudaMemcpyDeviceToHost, (cudaStream_t)cstream);
+    if (!e) e = scratch_release(cstream);
     if (!e) e = (int)cudaStreamSynchronize((cudaStream_t)cstream);
     if (e) return cuda_fail(e, "fill");
     const rp::Ctrl& c = *g_scr.h_ctrl;
@@ -760,6 +874,23 @@ rp_status pairs_fill(int engine, u64 seed, u64 stream, u64* pos, size_t n, int b
 extern "C" {
 
 const char* rp_last_error(void) { return g_err.c_str(); }
+
+rp_status rp_async_status(void* cuda_stream) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (!g_async.dev) return RP_OK;
+  int e = cuda_stream ? (int)cudaStreamSynchronize((cudaStream_t)cuda_stream) : (int)cudaDeviceSynchronize();
+  u64 h[4] = {0, 0, 0, 0};
+  if (!e) e = (int)cudaMemcpy(h, g_async.dev, sizeof h, cudaMemcpyDeviceToHost);
+  if (e) return cuda_fail(e, "asynchronous fill status");
+  if (!h[2]) return RP_OK;
+  e = (int)cudaMemset(g_async.dev + 1, 0, 3 * sizeof(u64));
+  if (e) return cuda_fail(e, "asynchronous fill status reset");
+  char buf[256];
+  snprintf(buf, sizeof buf, "%llu asynchronous fill(s) failed (device bits 0x%llx%s%s; first at tile %llu)",
+           (unsigned long long)h[2], (unsigned long long)h[1], (h[1] & rp::E_TIMEOUT) ? ", a bounded wait gave up" : "",
+           (h[1] & rp::E_INCOMPLETE) ? ", ran out of the planned tiles" : "", (unsigned long long)h[3]);
+  return fail((h[1] & rp::E_TIMEOUT) ? RP_ERR_TIMEOUT : RP_ERR_INTERNAL, buf);
+}
 const char* rp_version(void) { return "rp 0.1 (sm_103a)"; }
 uint64_t rp_kernel_launches(void) { return g_launches.load(); }
 

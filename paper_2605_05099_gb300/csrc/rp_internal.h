@@ -18,6 +18,7 @@ enum : unsigned {
   E_LANDING = 2u,     // a segment walk jumped over the next sync point
   E_OVERFLOW = 4u,    // a candidate needed words beyond the tile halo
   E_NOSYNC = 8u,      // no tile-start sync point within the search window
+  E_INCOMPLETE = 16u, // an asynchronous fill ran out of its planned tiles
 };
 
 // Per-launch control block in device memory (scratch).
@@ -142,6 +143,14 @@ struct TileGeom;
 TileGeom batch_geom(int cls, int cvar);
 int launch_fill(const FillArgs& a, int grid, void* stream);
 int launch_tails(const FillArgs& a, void* stream);
+// Sets a control block to its initial state on the stream (no host copy: a
+// copy from pageable memory would wait for the stream).
+int launch_ctrl_reset(Ctrl* ctrl, void* stream);
+// Asynchronous fills: writes start + ctrl->next_pos to d_pos (~0 when the
+// fill failed), and ORs the failure bits into sticky[0], counts failures in
+// sticky[1] and keeps the first failure's tile in sticky[2].
+int launch_finish(const Ctrl* ctrl, unsigned long long start, unsigned long long* d_pos, unsigned long long* sticky,
+                  void* stream);
 // Pairwise outputs from 2m base variates g: mode 0 beta X/(X+Y), 1 F
 // (X/p0)/(Y/p1), 2 skew normal p0 + p1 (p2 |u0| + p3 u1).
 int launch_pairs(const double* g, double* out, unsigned long long m, int mode, const double* p, void* stream);

@@ -103,6 +103,36 @@ TileGeom batch_geom(int cls, int cvar) {
   return TileGeom{NT_, c, NT_ * c, 0};
 }
 
+__global__ void k_ctrl_reset(Ctrl* __restrict__ c) {
+  Ctrl c0;
+  memset(&c0, 0, sizeof(c0));
+  c0.done_tile = ~0ull;
+  c0.first_reject = ~0ull;
+  *c = c0;
+}
+
+int launch_ctrl_reset(Ctrl* ctrl, void* stream) {
+  k_ctrl_reset<<<1, 1, 0, (cudaStream_t)stream>>>(ctrl);
+  return (int)cudaGetLastError();
+}
+
+__global__ void k_finish(const Ctrl* __restrict__ c, u64 start, u64* __restrict__ d_pos, u64* __restrict__ sticky) {
+  const unsigned err = c->err | (c->done_tile == ~0ull ? E_INCOMPLETE : 0u);
+  if (err) {
+    atomicOr(sticky, (u64)err);
+    if (atomicAdd(sticky + 1, 1ull) == 0) sticky[2] = c->err_info;
+    *d_pos = ~0ull;
+  } else {
+    *d_pos = start + c->next_pos;
+  }
+}
+
+int launch_finish(const Ctrl* ctrl, unsigned long long start, unsigned long long* d_pos, unsigned long long* sticky,
+                  void* stream) {
+  k_finish<<<1, 1, 0, (cudaStream_t)stream>>>(ctrl, start, d_pos, sticky);
+  return (int)cudaGetLastError();
+}
+
 int launch_tails(const FillArgs& a, void* stream) {
   cudaStream_t s = (cudaStream_t)stream;
   if (a.dist == D_NORMAL) k_tails<SampNormal><<<304, 256, 0, s>>>(a);
