@@ -54,6 +54,13 @@ TRAFFIC = {
 # these give the derived integer peak that the measured engine-only rates
 # (rp_engine_fold) are compared with.
 ENGINE_OPS = {"xoshiro256pp": 20, "pcg64dxsm": 42, "philox4x32_10": 42}
+
+# FP64 flops per gradient (DADD + DMUL + 2 DFMA, thread level, predicated on)
+# counted by ncu on n = 2^24 samples of the same workloads
+# (profiles/k_gamma_grad_n2e24.md, profiles/k_beta_grad_a2_b5_n2e24.md); the
+# kernels are bound by the FP64 pipe: 2 DFMA per SM per clock.
+GRAD_FLOPS = {"gamma(2.5)": 252.5, "gamma(30.0)": 371.9, "beta(2.0, 5.0)": 483.1}
+FP64_FLOPS_PER_SM_CLK = 4
 ISSUE_LANES_PER_SM = 128
 
 
@@ -386,8 +393,11 @@ def run_extras(rp, stream):
         p = rp.rp_fill_u64("xoshiro256pp", 12345, rp.NO_STREAM, 0, w, stream)
         rp.rp_fill_uniform("xoshiro256pp", 12345, rp.NO_STREAM, p, u, stream)
     c1()
-    ms = _ev_ms(stream, c1, reps=5)
-    ex["config1_words_then_uniforms"] = {"variates_per_s": 2 * (1 << 20) / (ms / 1e3), "ms": ms}
+    # one-word fills do not wait for their kernels: 100 back-to-back pairs
+    # between the events time the device work, not host round trips
+    ms = _ev_ms(stream, lambda: [c1() for _ in range(100)], reps=3) / 100
+    ex["config1_words_then_uniforms"] = {"variates_per_s": 2 * (1 << 20) / (ms / 1e3), "ms": ms,
+                                         "replays": 100}
     del w, u
     # gamma / beta forward and gradients (config 3)
     n = 1 << 26
@@ -412,8 +422,15 @@ def run_extras(rp, stream):
         bg()
         grads[f"beta{ab}"] = n / (_ev_ms(stream, bg) / 1e3)
     ex["gamma_beta_fill"] = {"unit": "variates/s", "n": n, **{k: round(v) for k, v in fwd.items()}}
+    props = torch.cuda.get_device_properties(0)
+    fp64_peak = props.multi_processor_count * FP64_FLOPS_PER_SM_CLK * 2.07e9
     ex["gamma_beta_grads"] = {"unit": "grads/s (per-sample dz/dtheta and the reduced sum)", "n": n,
-                              **{k: round(v) for k, v in grads.items()}}
+                              **{k: round(v) for k, v in grads.items()},
+                              "fp64_roofline": {k: {"flops_per_grad": f, "achieved_tflops": grads[k] * f / 1e12,
+                                                    "peak_tflops": fp64_peak / 1e12,
+                                                    "frac": grads[k] * f / fp64_peak}
+                                                for k, f in GRAD_FLOPS.items() if k in grads},
+                              "fp64_peak": "SMs x 2 DFMA x 2 flops x 2070 MHz (derived, not measured)"}
     # derived distributions (Table "continuous"), fused output transforms of
     # the base fills; xoshiro seed 7, n = 2^26
     dv = {}
