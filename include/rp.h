@@ -153,15 +153,15 @@ rp_status rp_fill_gamma(rp_engine engine, uint64_t seed, uint64_t stream, uint64
 
 /* Beta(a, b) = X / (X + Y), X ~ Gamma(a) drawn before Y ~ Gamma(b)
  * (Table "continuous", beta).  a, b > 0.  Equal shapes run as a gamma fill
- * of 2n and a pairwise ratio.  Unequal shapes run on merge-point seams,
- * which need the two shapes' draws to consume different word counts now
- * and then.  Shapes close to each other or both large (2 and 2.01, 10 and
- * 11) leave many chunks without a merge point; a thread's walk then crosses
- * them (up to 64 chunks), which costs time but not correctness.  Shapes
- * whose draws almost never differ in length (2 and 2.0000001, 30 and 31)
- * exceed that, and the fill fails with RP_ERR_INTERNAL and a message
- * saying so.  The same holds for F (rp_fill_derived) with unequal degrees
- * of freedom. */
+ * of 2n and a pairwise ratio.  Unequal shapes run on phased merge-point
+ * seams: a seam is a word after which every chain that can enter the chunk
+ * sits at a gamma boundary, in either phase (X or Y next), and each thread
+ * carries a map from its entry phase to its exit phase and output count
+ * that the scan and the look-back compose.  Shapes whose draws consume
+ * words alike (2 and 2.0000001, 30 and 31) therefore need no special case;
+ * a chunk without such a point is crossed by the walk before it (up to 64
+ * chunks; more fails with RP_ERR_INTERNAL, which no tested shape reaches).
+ * The same holds for F (rp_fill_derived) with unequal degrees of freedom. */
 rp_status rp_fill_beta(rp_engine engine, uint64_t seed, uint64_t stream, uint64_t* pos,
                        size_t n, double a, double b, double* d_out, void* cuda_stream);
 

@@ -552,13 +552,25 @@ struct MergeSmem {
   int wsum[32];
   int misc[8];
   u64 sh4[4];
+  int sig[NT];    // each chunk's merge point (-1: none)
+  int surv[NT];   // phased fills: the phases left there
+};
+
+// A merge-seam tile holds NT - 1 chunks.  Its last thread starts at the
+// next tile's first chunk and only finds that chunk's merge point, so that
+// every walk of the tile can stop at a merge point the tile already knows
+// instead of searching for it a second time.
+template <int NT, int C>
+struct MergeGeom {
+  static constexpr int kChunks = NT - 1;
+  static constexpr int T = kChunks * C;
 };
 
 // One tile of a merge-seam fill (gamma, beta).  Returns false when the fill
 // needs no further tiles (or a device check failed): the caller stops.
 template <int NT, int C, class E, class S>
 __device__ bool merge_tile(const FillArgs& a, u64 k, const E& e, MergeSmem<NT>& sm) {
-  constexpr int T = NT * C;
+  constexpr int T = MergeGeom<NT, C>::T;
   const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
   const ZigDev& z = g_zig[0];   // read through L1 (keeps shared memory small)
   double* out = (double*)a.out;
@@ -574,12 +586,24 @@ __device__ bool merge_tile(const FillArgs& a, u64 k, const E& e, MergeSmem<NT>& 
     sig = merge_search<E, S>(g, C, a.sp, z, nullptr, nullptr);
     if (sig < 0) ok = false;   // no merge point in this chunk: no segment
   }
+  sm.sig[t] = ok ? sig : -1;
+  __syncthreads();
+  if (t == NT - 1) ok = false;   // the next tile's first chunk: looked at, not walked
   typename S::M m;
   m.reset();
   if (ok) {
     for (int p = sig; p < C; ++p) cnt += m.feed(g.next(), a.sp, z);
     int q = -1, u = 1;
     for (; u <= kSkipMax; ++u) {
+      if (t + u < NT) {
+        // a merge point this tile knows: walk to it
+        const int qn = sm.sig[t + u];
+        const int lim = qn < 0 ? C : qn;
+        for (int p = 0; p < lim; ++p) cnt += m.feed(g.next(), a.sp, z);
+        if (qn < 0) continue;      // no merge point in that chunk: the walk crosses it
+        q = m.idle() ? qn : -2;
+        break;
+      }
       q = merge_search<E, S>(g, C, a.sp, z, &m, &cnt);
       if (q != -1) break;       // else: the own chain has crossed that chunk; try the next
     }
@@ -674,13 +698,365 @@ __device__ bool merge_tile(const FillArgs& a, u64 k, const E& e, MergeSmem<NT>& 
   return true;
 }
 
+// ------------------------------------------------------------------ phased merge seams
+// Beta (and F) draw X ~ Gamma(a), then Y ~ Gamma(b), from one stream.  When
+// the two shapes consume words alike, chains that enter a chunk at different
+// offsets soon sit at the same gamma boundary but one gamma apart, and stay
+// so: full merge points become rare.  A phased merge point only needs every
+// hypothesis (entry offset, entry phase) at a gamma boundary after the same
+// word; at most two states remain there, one per phase (0: X next, 1: Y
+// next).  Each thread walks from its phased merge point once per entry phase
+// to the next one, which gives a map: entry phase -> (exit phase, outputs).
+// The warp scan and the decoupled look-back compose these maps.  A variate
+// in progress at a seam (phase 1: X drawn, Y not) belongs to the walk that
+// reaches the seam: it goes on until Y is complete, and the next thread,
+// entering in phase 1, skips that first completion.  Every walk thus ends
+// at a variate boundary, as in the unphased fills.
+
+struct PMap {
+  int f;        // bit p: exit phase for entry phase p
+  int c0, c1;   // outputs for entry phase 0, 1
+};
+__device__ __forceinline__ PMap pm_identity() { return PMap{2, 0, 0}; }
+// (a after b)(x) = a(b(x))
+__device__ __forceinline__ PMap pm_compose(PMap a, PMap b) {
+  const int b0 = b.f & 1, b1 = (b.f >> 1) & 1;
+  PMap r;
+  r.f = ((a.f >> b0) & 1) | (((a.f >> b1) & 1) << 1);
+  r.c0 = b.c0 + (b0 ? a.c1 : a.c0);
+  r.c1 = b.c1 + (b1 ? a.c1 : a.c0);
+  return r;
+}
+__device__ __forceinline__ PMap pm_shfl_up(PMap m, int o) {
+  return PMap{__shfl_up_sync(0xffffffffu, m.f, o), __shfl_up_sync(0xffffffffu, m.c0, o),
+              __shfl_up_sync(0xffffffffu, m.c1, o)};
+}
+__device__ __forceinline__ PMap pm_shfl_down(PMap m, int o) {
+  return PMap{__shfl_down_sync(0xffffffffu, m.f, o), __shfl_down_sync(0xffffffffu, m.c0, o),
+              __shfl_down_sync(0xffffffffu, m.c1, o)};
+}
+__device__ __forceinline__ PMap pm_shfl(PMap m, int l) {
+  return PMap{__shfl_sync(0xffffffffu, m.f, l), __shfl_sync(0xffffffffu, m.c0, l), __shfl_sync(0xffffffffu, m.c1, l)};
+}
+
+// The two walks of a thread (entry phase 0 and 1), fed in lockstep until
+// they meet (both at a gamma boundary in one phase: the same state), then as
+// one.
+template <class S>
+struct PhWalk {
+  typename S::L m[2];
+  int cnt[2];
+  bool same;
+  __device__ __forceinline__ void feed(u64 u, const SampArgs& sp, const ZigDev& z) {
+    if (!same && m[0].idle() && m[1].idle() && m[0].phase() == m[1].phase()) same = true;
+    const int c = m[0].feed(u, sp, z);
+    cnt[0] += c;
+    if (same) cnt[1] += c;
+    else cnt[1] += m[1].feed(u, sp, z);
+  }
+};
+
+// Phased merge point of the chunk at the engine's position, within `limit`
+// words: hypotheses typename S::L started at each offset below kE in both
+// phases, all fed the same words, until every one is at a gamma boundary
+// after the same word (at most one state per phase is then left).  *surv:
+// bit p set if a state in phase p is left.  `w` (nullable) is fed the same
+// words; *bad gets bit x when walk x is not in a surviving state there (that
+// walk cannot be the true chain).  Returns the point (relative) or -1 if
+// none within `limit` words.  (Requiring full coalescence first, where it
+// comes within a few hundred words, was measured slower: the 12 extra
+// hypotheses run longer than the second walk they save.)
+template <class E, class S>
+__device__ int seam_search(E& g, int limit, const SampArgs& sp, const ZigDev& z, int* surv, PhWalk<S>* w, int* bad) {
+  typename S::L hyp[2 * kE];   // hypothesis 2e + p: entry offset e, phase p
+  unsigned alive = 0;
+  for (int q = 0; q < limit; ++q) {
+    if (q < kE) {
+      hyp[2 * q].reset(0);
+      hyp[2 * q + 1].reset(1);
+      alive |= 3u << (2 * q);
+    }
+    unsigned idle = 0, ph1 = 0;
+    for (int h = 0; h < 2 * kE; ++h)
+      if (((alive >> h) & 1u) && hyp[h].idle()) {
+        idle |= 1u << h;
+        if (hyp[h].phase()) ph1 |= 1u << h;
+      }
+    if (idle) {
+      // at a boundary after the same word, equal phases are equal states
+      const unsigned i0 = idle & ~ph1, i1 = idle & ph1;
+      const unsigned keep = (i0 & (~i0 + 1u)) | (i1 & (~i1 + 1u));
+      alive &= ~(idle ^ keep);
+    }
+    if (q >= kE - 1 && (alive & ~idle) == 0) {
+      *surv = ((alive & ~ph1) ? 1 : 0) | ((alive & ph1) ? 2 : 0);
+      if (w) {
+        for (int x = 0; x < 2; ++x) {
+          const typename S::L& m = w->m[w->same ? 0 : x];
+          if (!(m.idle() && ((*surv >> m.phase()) & 1))) *bad |= 1 << x;
+        }
+      }
+      return q;
+    }
+    const u64 u = g.next();
+    for (int h = 0; h < 2 * kE; ++h)
+      if ((alive >> h) & 1u) (void)hyp[h].feed(u, sp, z);
+    if (w) w->feed(u, sp, z);
+  }
+  return -1;
+}
+
+// Decoupled look-back over phase maps, run by one warp (as lookback_warp).
+// Status word: bit 63 aggregate (bits 60-61 the map's exit phases, 30-59 and
+// 0-29 its counts), bit 62 inclusive (bit 61 the phase, 0-60 the count).
+// Returns the state entering tile k as an inclusive payload, or ~0 if the
+// bounded wait ran out or the tile became unnecessary.
+__device__ unsigned long long lookback_warp_ph(unsigned long long* st, unsigned long long k, PMap agg, Ctrl* ctrl,
+                                              unsigned long long spin_max, unsigned long long stall_tile1) {
+  if (stall_tile1 && k + 1 == stall_tile1) return ~0ull;   // test hook: this tile never publishes
+  const unsigned long long smax = spin_max ? spin_max : kSpinMax;
+  const unsigned long long AGG = 1ull << 63, INC = 1ull << 62, CNT = (1ull << 61) - 1, C30 = (1ull << 30) - 1;
+  const int lane = threadIdx.x & 31;
+  auto apply = [&](PMap m, unsigned long long in) {
+    const int p = (int)((in >> 61) & 1);
+    return ((unsigned long long)((m.f >> p) & 1) << 61) | ((in & CNT) + (unsigned long long)(p ? m.c1 : m.c0));
+  };
+  unsigned long long entry = 0;   // the fill starts in phase 0 with no outputs
+  if (k > 0) {
+    if (lane == 0)
+      *(volatile unsigned long long*)(st + k) =
+          AGG | ((unsigned long long)agg.f << 60) | ((unsigned long long)agg.c0 << 30) | (unsigned long long)agg.c1;
+    PMap acc = pm_identity();   // aggregates passed so far, later tiles outermost
+    long long j = (long long)k - 1;
+    unsigned long long spins = 0;
+    for (;;) {
+      const long long idx = j - lane;
+      const unsigned long long v = idx >= 0 ? ld_volatile(st + idx) : INC;
+      const unsigned incm = __ballot_sync(0xffffffffu, (v & INC) != 0);
+      const unsigned rdym = __ballot_sync(0xffffffffu, (v & (INC | AGG)) != 0);
+      const int fi = incm ? __ffs(incm) - 1 : 32;
+      const unsigned need = fi < 32 ? (2u << fi) - 1u : 0xffffffffu;
+      if ((rdym & need) != need) {
+        int stop = 0;
+        if (lane == 0) {
+          if (ld_volatile(&ctrl->done_tile) < k) stop = 1;
+          else if (++spins > smax) { set_err(ctrl, E_TIMEOUT, k); stop = 1; }
+        }
+        if (__shfl_sync(0xffffffffu, stop, 0)) return ~0ull;
+        __nanosleep(64);
+        continue;
+      }
+      PMap m = lane < fi ? PMap{(int)((v >> 60) & 3), (int)((v >> 30) & C30), (int)(v & C30)} : pm_identity();
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const PMap other = pm_shfl_down(m, o);
+        if (lane + o < 32) m = pm_compose(m, other);   // lane l: tiles j-l (latest) down to j-l-2o+1
+      }
+      acc = pm_compose(acc, pm_shfl(m, 0));
+      if (fi < 32) {
+        const unsigned long long inc = __shfl_sync(0xffffffffu, v, fi) & ~(AGG | INC);
+        entry = apply(acc, inc);
+        break;
+      }
+      j -= 32;
+    }
+  }
+  if (lane == 0) *(volatile unsigned long long*)(st + k) = INC | apply(agg, entry);
+  return entry;
+}
+
+// One tile of a phased merge-seam fill (beta, F), one warp per tile.
+// Returns false when the fill needs no further tiles (or a device check
+// failed): the caller stops.
+template <int NT, int C, class E, class S>
+__device__ bool merge_tile_ph(const FillArgs& a, u64 k, const E& e, MergeSmem<NT>& sm) {
+  static_assert(NT == 32, "one warp per tile");
+  constexpr int T = MergeGeom<NT, C>::T;
+  const int lane = threadIdx.x;
+  const ZigDev& z = g_zig[0];
+  double* out = (double*)a.out;
+  if (lane == 0) sm.misc[5] = ld_volatile(&a.ctrl->done_tile) < k;
+  __syncwarp();
+  if (sm.misc[5]) return false;
+  // ---------------- pass 1: phased merge point, both walks, next point
+  E g = e;
+  int sig = 0, surv = 1;   // the fill's first word: phase 0
+  bool ok = true;
+  if (!(k == 0 && lane == 0)) {
+    int nobad = 0;
+    sig = seam_search<E, S>(g, C, a.sp, z, &surv, nullptr, &nobad);
+    if (sig < 0) ok = false;   // no merge point in this chunk: no segment
+  }
+  sm.sig[lane] = ok ? sig : -1;
+  sm.surv[lane] = surv;
+  __syncwarp();
+  if (lane == NT - 1) ok = false;   // the next tile's first chunk: looked at, not walked
+  // an entry phase that no hypothesis has here cannot occur: take the other
+  const int sp0 = (surv & 1) ? 0 : 1, sp1 = (surv & 2) ? 1 : 0;
+  PhWalk<S> w;
+  w.m[0].reset(sp0);
+  w.m[1].reset(sp1);
+  w.cnt[0] = sp0 ? -1 : 0;   // entering in phase 1: the first completion is the previous walk's
+  w.cnt[1] = sp1 ? -1 : 0;
+  w.same = sp0 == sp1;
+  int endp[2] = {0, 0}, f = 2, bad = 0;
+  if (ok) {
+    for (int p = sig; p < C; ++p) w.feed(g.next(), a.sp, z);
+    int q = -1, u = 1, dummy = 0;
+    for (; u <= kSkipMax; ++u) {
+      if (lane + u < NT) {
+        // a merge point this tile knows: walk to it
+        const int qn = sm.sig[lane + u];
+        const int lim = qn < 0 ? C : qn;
+        for (int p = 0; p < lim; ++p) w.feed(g.next(), a.sp, z);
+        if (qn < 0) continue;      // no merge point in that chunk: the walks cross it
+        const int sv = sm.surv[lane + u];
+        for (int x = 0; x < 2; ++x) {
+          const typename S::L& mx = w.m[w.same ? 0 : x];
+          if (!(mx.idle() && ((sv >> mx.phase()) & 1))) bad |= 1 << x;
+        }
+        q = qn;
+        break;
+      }
+      q = seam_search<E, S>(g, C, a.sp, z, &dummy, &w, &bad);
+      if (q != -1) break;       // else: the walks have crossed that chunk; try the next
+    }
+    if (q == -1) { set_err(a.ctrl, E_NOSYNC, k); ok = false; }
+    else {
+      // (once the walks have met, m[1] is no longer fed: m[0] stands for both)
+      const int p0 = w.m[0].phase(), p1 = w.same ? p0 : w.m[1].phase();
+      f = p0 | (p1 << 1);
+      // a walk in phase 1 at the seam completes its variate's Y
+      for (int x = 0; x < (w.same ? 1 : 2); ++x) {
+        int len = 0;
+        if ((x ? p1 : p0) == 1) {
+          E gx = g;
+          bool done = false;
+          for (; len < C && !done; ++len) done = w.m[x].feed(gx.next(), a.sp, z) != 0;
+          if (!done) { set_err(a.ctrl, E_LANDING, k); ok = false; }
+          w.cnt[x] += 1;
+          if (w.same) w.cnt[1] += 1;
+        }
+        endp[x] = u * C + q + len;
+      }
+      if (w.same) endp[1] = endp[0];
+    }
+  }
+  // ---------------- warp scan of the maps, look-back
+  PMap mine = ok ? PMap{f, w.cnt[0], w.cnt[1]} : pm_identity();
+  PMap inc = mine;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const PMap other = pm_shfl_up(inc, o);
+    if (lane >= o) inc = pm_compose(inc, other);
+  }
+  PMap ex = pm_shfl_up(inc, 1);
+  if (lane == 0) ex = pm_identity();
+  const PMap agg = pm_shfl(inc, 31);
+  const unsigned long long ent = lookback_warp_ph(a.tile_status, k, agg, a.ctrl, a.spin_max, a.stall_tile1);
+  if (ent == ~0ull) return false;
+  const int ph_in = (int)((ent >> 61) & 1);
+  const u64 base = ent & ((1ull << 61) - 1);
+  const int ph = (ex.f >> ph_in) & 1;                       // this thread's entry phase
+  const bool missed = ok && ((bad >> ph) & 1);
+  if (__any_sync(0xffffffffu, missed)) {
+    // the true chain is a walk that missed the seam: the seam rule's premise
+    // (a gamma variate overhangs a chunk by less than kE words) failed
+    if (missed) set_err(a.ctrl, E_LANDING, k);
+    return false;
+  }
+  const int off = ph_in ? ex.c1 : ex.c0;
+  const int cnt = ok ? (ph ? w.cnt[1] : w.cnt[0]) : 0;
+  const u64 total = (u64)(ph_in ? agg.c1 : agg.c0);
+  const u64 chunk0 = k * (u64)T + (u64)lane * C;
+  if (k + 1 == a.n_tiles && base + total < a.n) {
+    // ran out of tiles: the tile's last walk ends where the chain continues,
+    // at a variate boundary
+    u64 np = ok ? chunk0 + (u64)endp[ph] : 0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const u64 y = __shfl_xor_sync(0xffffffffu, np, o);
+      np = y > np ? y : np;
+    }
+    if (lane == 0) {
+      a.ctrl->total = base + total;
+      a.ctrl->next_pos = np;
+      a.ctrl->last_tile = k;
+    }
+  }
+  // ---------------- pass 2: regenerate, stage records, evaluate while writing
+  if (base < a.n) {
+    g = e;
+    for (int q = 0; q < sig; ++q) (void)g.next();
+    typename S::M m;
+    const int st = ph ? sp1 : sp0;
+    m.reset(st);
+    bool skip = st == 1;
+    const u64 my0 = base + (u64)off;
+    int emitted = 0;
+    int p = sig;
+    bool active = ok && cnt > 0;
+    u64* myrow = &sm.stage[0][lane * (kRecS + 1) * kRecW];
+    while (__any_sync(0xffffffffu, active)) {
+      int ns = 0;
+      while (active && ns < kRecS) {
+        u64 u = g.next();
+        ++p;
+        if (!m.feed(u, a.sp, z)) continue;
+        if (skip) { skip = false; continue; }
+        u64* r = myrow + ns * kRecW;
+        m.record(r);
+        const u64 gi = my0 + emitted + ns;
+        r[7] = 0;
+        if (S::needs_tail(r) && gi < a.n) {
+          unsigned long long qi = atomicAdd(a.tail_count, 1ull);
+          if (qi < a.tail_cap) {
+            TailEntry te;
+            te.g = a.tail_abs ? (u64)(out + gi) : gi;
+            te.w0 = r[0];
+            te.w1 = (u64)a.req;
+            for (int j = 0; j < 6; ++j) te.x[j] = r[1 + j];
+            a.tailq[qi] = te;
+            r[7] = 1;
+          }
+        }
+        ++ns;
+        if (gi == a.n - 1) {
+          a.ctrl->next_pos = chunk0 + (u64)p;
+          atomicMin(&a.ctrl->done_tile, k);
+        }
+        if (emitted + ns == cnt) active = false;
+      }
+      __syncwarp();
+      const u64 dst = my0 + emitted;
+      for (int it = 0; it < kRecS; ++it) {
+        int ent2 = it * 32 + lane;
+        int rr = ent2 / kRecS, col = ent2 % kRecS;
+        u64 d = __shfl_sync(0xffffffffu, dst, rr);
+        int c = __shfl_sync(0xffffffffu, ns, rr);
+        if (col < c && d + col < a.n) {
+          const u64* r = &sm.stage[0][(rr * (kRecS + 1) + col) * kRecW];
+          if (!r[7]) out[d + col] = S::value(r, a.sp, z);
+        }
+      }
+      __syncwarp();
+      emitted += ns;
+    }
+  }
+  __syncwarp();
+  return true;
+}
+
 template <int NT, int C, class E, class S>
 __global__ void __launch_bounds__(NT, 512 / NT) k_merge(FillArgs a) {
   __shared__ MergeSmem<NT> sm;
   E e;
   e.init_tile(a.eng, blockIdx.x, threadIdx.x, sm.sh4);
   for (u64 k = blockIdx.x; k < a.n_tiles; k += gridDim.x) {
-    if (!merge_tile<NT, C, E, S>(a, k, e, sm)) break;
+    bool more;
+    if constexpr (S::kPhased) more = merge_tile_ph<NT, C, E, S>(a, k, e, sm);
+    else more = merge_tile<NT, C, E, S>(a, k, e, sm);
+    if (!more) break;
     e.advance(a.eng);
   }
 }
@@ -712,7 +1088,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_merge_batch(BatchArgs b) {
     E e;
     e.init_tile(fa.eng, bi.tile, threadIdx.x, sm.sh4);
     if (fa.dist == D_GAMMA) merge_tile<NT, C, E, SampGamma>(fa, bi.tile, e, sm);
-    else merge_tile<NT, C, E, SampBeta>(fa, bi.tile, e, sm);
+    else merge_tile_ph<NT, C, E, SampBeta>(fa, bi.tile, e, sm);
   }
 }
 

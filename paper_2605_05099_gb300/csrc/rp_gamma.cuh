@@ -211,6 +211,7 @@ struct NormalMach {
 // xb, ub), r[4..6] = Y (beta only).
 struct SampGamma {
   static constexpr int kChunk = 2048;   // words per thread chunk in a single fill
+  static constexpr bool kPhased = false;
   struct M {
     GammaMach g;
     __device__ __forceinline__ void reset() { g.reset(); }
@@ -237,12 +238,31 @@ struct SampGammaBoost : SampGamma {
 struct SampBeta {
   // two gamma chains coalesce more slowly at a seam: longer chunks amortise the search
   static constexpr int kChunk = 4096;
+  // Seams are phased merge points (merge_tile_ph): a chain's state at a gamma
+  // boundary is its phase, 0 (next gamma is X) or 1 (next is Y).
+  static constexpr bool kPhased = true;
+  // Control state only (no records): the seam searches and the counting walks.
+  struct L {
+    GammaMach g;
+    int ph;
+    __device__ __forceinline__ void reset(int p) { g.reset(); ph = p; }
+    __device__ __forceinline__ bool idle() const { return g.idle(); }   // at a gamma boundary
+    __device__ __forceinline__ int phase() const { return ph; }
+    __device__ __forceinline__ int feed(u64 u, const SampArgs& a, const ZigDev& z) {
+      if (!g.feed(u, ph ? a.gb : a.ga, z)) return 0;
+      ph ^= 1;
+      return ph == 0;
+    }
+  };
   struct M {
     GammaMach g;
     int ph;        // 0 drawing X, 1 drawing Y
     int xk;
     u64 xa, xb, xub;
     __device__ __forceinline__ void reset() { g.reset(); ph = 0; }
+    // entering at a gamma boundary in phase p (with p = 1 the first output
+    // completes a variate whose X this machine has not seen)
+    __device__ __forceinline__ void reset(int p) { g.reset(); ph = p; }
     __device__ __forceinline__ bool idle() const { return g.idle() && ph == 0; }
     __device__ __forceinline__ int feed(u64 u, const SampArgs& a, const ZigDev& z) {
       if (!g.feed(u, ph ? a.gb : a.ga, z)) return 0;
@@ -277,6 +297,7 @@ struct SampBeta {
 // = the gamma record of V.  ep[0] = nu.
 struct SampT {
   static constexpr int kChunk = 4096;   // two sub-variates per output, as beta
+  static constexpr bool kPhased = false;
   struct M {
     NormalMach nm;
     GammaMach g;

@@ -98,7 +98,7 @@ int launch_batch_tails(int cls, const BatchArgs& b, void* stream) {
 }
 
 TileGeom batch_geom(int cls, int cvar) {
-  if (cls == BC_MERGE) return TileGeom{NTM_, CM_, NTM_ * CM_, 0};
+  if (cls == BC_MERGE) return TileGeom{NTM_, CM_, MergeGeom<NTM_, CM_>::T, 0};
   const int c = cvar == 1 ? 128 : C_;
   return TileGeom{NT_, c, NT_ * c, 0};
 }
@@ -205,10 +205,11 @@ int occupancy_blocks(int engine, int dist, int epi) {
 
 TileGeom tile_geom(int engine, int dist, int gamma_boost) {
   (void)engine;
-  if (dist == D_GAMMA && gamma_boost) return TileGeom{NTM_, SampGammaBoost::kChunk, NTM_ * SampGammaBoost::kChunk, 0};
-  if (dist == D_GAMMA) return TileGeom{NTM_, SampGamma::kChunk, NTM_ * SampGamma::kChunk, 0};
-  if (dist == D_BETA) return TileGeom{NTM_, SampBeta::kChunk, NTM_ * SampBeta::kChunk, 0};
-  if (dist == D_T) return TileGeom{NTM_, SampT::kChunk, NTM_ * SampT::kChunk, 0};
+  if (dist == D_GAMMA && gamma_boost)
+    return TileGeom{NTM_, SampGammaBoost::kChunk, MergeGeom<NTM_, SampGammaBoost::kChunk>::T, 0};
+  if (dist == D_GAMMA) return TileGeom{NTM_, SampGamma::kChunk, MergeGeom<NTM_, SampGamma::kChunk>::T, 0};
+  if (dist == D_BETA) return TileGeom{NTM_, SampBeta::kChunk, MergeGeom<NTM_, SampBeta::kChunk>::T, 0};
+  if (dist == D_T) return TileGeom{NTM_, SampT::kChunk, MergeGeom<NTM_, SampT::kChunk>::T, 0};
   if (dist == D_BOUNDED) return TileGeom{NT_, CR_, NT_ * CR_, 0};
   return TileGeom{NT_, C_, NT_ * C_, 0};
 }

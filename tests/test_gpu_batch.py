@@ -123,6 +123,23 @@ def test_autotuned_plan_replays_and_matches_state_fills(engine):
         assert np.array_equal(_host(ref).view(np.uint64), first[i].view(np.uint64)), (engine, i, r["dist"])
 
 
+@pytest.mark.parametrize("engine", ENGINES)
+def test_batch_beta_with_shapes_that_consume_alike(engine):
+    """Beta requests whose shapes draw alike (phased merge points) among
+    other requests of one batch."""
+    reqs = [{"stream": s, "dist": d, "n": n, "p0": p0, "p1": p1, "m": 0, "pos": pos}
+            for s, d, n, p0, p1, pos in ((3, "beta", 300_000, 30.0, 31.0, 0), (4, "normal", 50_000, 0.0, 0.0, 7),
+                                         (5, "beta", 120_001, 2.0, 2.0000001, 99), (6, "gamma", 80_000, 2.5, 0.0, 0),
+                                         (7, "beta", 200_000, 0.5, 0.5000001, 0))]
+    outs, arr = _alloc(reqs)
+    pos = rp.rp_batch_run(arr, engine, BASE)
+    torch.cuda.synchronize()
+    for i, (r, o) in enumerate(zip(reqs, outs)):
+        ref, opos = _oracle(engine, r)
+        assert pos[i] == opos, (engine, i, r, pos[i], opos)
+        _compare(_host(o), ref, r, (engine, i, r["dist"], r["n"]))
+
+
 def test_medium_batch_matches_oracle():
     reqs = inputs.batch_workload(n_req=64, lo=1e3, hi=1e6, seed=7)
     outs, arr = _alloc(reqs)

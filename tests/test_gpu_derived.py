@@ -47,6 +47,8 @@ CASES = [
     ("gpd", (-1.0, 2.0, 0.0), 0),
     ("f", (5.0, 7.0), 0),
     ("f", (3.0, 3.0), 0),
+    ("f", (60.0, 62.0), 0),            # Gamma(30), Gamma(31): draws consume words alike
+    ("f", (4.0, 4.0000002), 0),
     ("f", (1.0, 4.0), BOOST_ULP["f"]),
     ("skew_normal", (1.0, 2.0, 4.0), "skew"),
     ("skew_normal", (0.0, 1.0, -2.0), "skew"),

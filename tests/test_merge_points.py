@@ -1,6 +1,6 @@
 """Host checks of the chunk seams of the fill kernels.
 
-Merge points of the gamma, beta and t kernels
+Merge points of the gamma and t kernels
 (Sec. 3.1 samplers; the seams are this library's, not the paper's).  A
 chunk's merge point is found by starting the sampler at each of the first
 12 word offsets of the chunk (a hypothesis that a variate starts there),
@@ -12,7 +12,8 @@ lengths (the words one variate consumes from any start word) and checked
 against the true chain of the sequential sampler, for the shapes the
 library runs on these kernels: every chunk of the kernel's length (2048 or
 4096 words) has a merge point, and every merge point lies on the true
-chain.
+chain.  The beta kernel's seams are phased merge points (hypotheses in
+both phases of the X, Y alternation; _phased_point), checked the same way.
 
 Sync points of the ziggurat normal kernel: the first position s >= G of a
 chunk such that every candidate starting in [0, s) ends by s.  A true-chain
@@ -80,6 +81,55 @@ def test_merge_points_exist_and_lie_on_the_true_chain(orc, dist, params, chunk):
         q = _merge_point(length, k * window, window)
         assert q >= KE - 1, (dist, params, k)
         assert k * window + q in bounds, (dist, params, k, q)
+
+
+def _phased_point(len_ab, c, limit):
+    """Phased merge point of the beta kernel: hypotheses (entry offset e < 12,
+    phase p: 0 = X ~ Gamma(a) next, 1 = Y ~ Gamma(b) next) advance one gamma
+    at a time; those at a gamma boundary after the same word in the same
+    phase are one state; the point is the first word, at or after offset 11,
+    after which every state left is at a gamma boundary.  Returns (q, the
+    phases left) or (-1, None)."""
+    pos, alive = {}, []
+    for q in range(limit):
+        if q < KE:
+            for p in (0, 1):
+                alive.append((q, p))
+                pos[(q, p)] = (c + q, p)
+        idle = [h for h in alive if pos[h][0] == c + q]
+        for p in (0, 1):
+            same = [h for h in idle if pos[h][1] == p]
+            if len(same) > 1:
+                drop = set(same[1:])
+                alive = [h for h in alive if h not in drop]
+        if q >= KE - 1 and all(pos[h][0] == c + q for h in alive):
+            return q, {pos[h][1] for h in alive}
+        for h in alive:
+            w, p = pos[h]
+            if w == c + q:
+                pos[h] = (w + len_ab[p](w), 1 - p)
+    return -1, None
+
+
+@pytest.mark.parametrize("ab", [(2.0, 5.0), (2.0, 2.0000001), (30.0, 31.0), (0.5, 0.5000001), (3.0, 0.7)])
+def test_phased_merge_points_lie_on_the_true_chain(orc, ab):
+    """The beta kernel's seams: for shapes whose draws consume words alike
+    (full merge points are then rare or absent) as well as for others, every
+    4096-word chunk has a phased merge point, and the true chain (X, Y, X, ...
+    drawn in turn by the sequential sampler) is at a gamma boundary there in
+    one of the phases left."""
+    seed, nchunks, window = 7, 8, 4096
+    len_ab = (_length_fn(orc, "gamma", (ab[0],), seed), _length_fn(orc, "gamma", (ab[1],), seed))
+    g = orc.gen("philox4x32_10", seed)
+    bounds, p = {0: 0}, 0
+    while max(bounds) < window * (nchunks + 1):
+        orc.fill(g, "gamma", 1, ab[p])
+        p = 1 - p
+        bounds[int(g.pos)] = p
+    for k in range(1, nchunks + 1):
+        q, phases = _phased_point(len_ab, k * window, window)
+        assert q >= KE - 1, (ab, k)
+        assert k * window + q in bounds and bounds[k * window + q] in phases, (ab, k, q, phases)
 
 
 # Normal ziggurat tails that consume 11 words (four rejected pairs), found by
