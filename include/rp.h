@@ -146,6 +146,34 @@ rp_status rp_fill_normal(rp_engine engine, uint64_t seed, uint64_t stream, uint6
 rp_status rp_fill_exp(rp_engine engine, uint64_t seed, uint64_t stream, uint64_t* pos,
                       size_t n, double* d_out, void* cuda_stream);
 
+/* Float variants (Table "continuous": the functions with suffix f; Sec. 3.1
+ * reads the engines' bits as 32-bit words, Sec. 4.4 notes that floats save
+ * space and time).  The paper gives no more than "analogous"; the readings:
+ * each 64-bit stream word gives two 32-bit words, its low half first; a
+ * float fill starts at the low half of word *pos, and when it ends on a low
+ * half the high half goes unused, so *pos stays a whole word (the next one).
+ *   rp_fill_uniformf  floor(h / 2^9) 2^-23 (the default method in float),
+ *                     two outputs per word; d_out must be 8-byte aligned
+ *                     (RP_ERR_PARAM otherwise).
+ *   rp_fill_normalf   bits 0-7 strip, bit 8 sign, bits 9-31 r (23 bits):
+ *                     x = RN_f(r wf_i), wf_i = RN_f(2^29 w_i); fast accept
+ *                     r < k_i / 2^29; the wedge y = RN_f((f_{i-1} - f_i) U + f_i)
+ *                     in float operations, f_i = RN_f(F_i), U = floor(h / 2^8)
+ *                     2^-24 of the next 32-bit word, accepted when
+ *                     y < exp(-x^2 / 2) (correctly rounded, in double);
+ *                     tails as the double sampler's with those U, in double,
+ *                     rounded once to float.
+ *   rp_fill_expf      bits 0-7 strip, bits 8-31 r (24 bits), likewise, with
+ *                     the tail RN_f(R - log(1 - U)).
+ * d_out: n floats (4-byte aligned for normalf and expf).  Errors and the
+ * asynchronous *pos as for the double fills. */
+rp_status rp_fill_uniformf(rp_engine engine, uint64_t seed, uint64_t stream, uint64_t* pos,
+                           size_t n, float* d_out, void* cuda_stream);
+rp_status rp_fill_normalf(rp_engine engine, uint64_t seed, uint64_t stream, uint64_t* pos,
+                          size_t n, float* d_out, void* cuda_stream);
+rp_status rp_fill_expf(rp_engine engine, uint64_t seed, uint64_t stream, uint64_t* pos,
+                       size_t n, float* d_out, void* cuda_stream);
+
 /* Gamma(alpha, 1) by Marsaglia & Tsang (Sec. 3.1, gamma); alpha < 1 by the
  * boost Gamma(alpha+1) U^(1/alpha).  alpha > 0. */
 rp_status rp_fill_gamma(rp_engine engine, uint64_t seed, uint64_t stream, uint64_t* pos,

@@ -75,6 +75,9 @@ def lib():
             "rp_debug_counters": [pu64, i32],
             "rp_debug_faults": [i32, u64],
             "rp_async_status": [vp],
+            "rp_fill_uniformf": [i32, u64, u64, pu64, sz, vp, vp],
+            "rp_fill_normalf": [i32, u64, u64, pu64, sz, vp, vp],
+            "rp_fill_expf": [i32, u64, u64, pu64, sz, vp, vp],
             "rp_substream_state": [i32, u64, u64, pu64, ctypes.POINTER(i32)],
             "rp_batch_plan_create": [ctypes.POINTER(Request), sz, i32, u64, i32, ctypes.POINTER(vp), vp],
             "rp_batch_plan_run": [vp, pu64, vp],
@@ -199,6 +202,20 @@ def rp_fill_normal_philox_static(seed, stream, pos, out, cuda_stream=None):
 
 def rp_fill_exp(engine, seed, stream, pos, out, cuda_stream=None):
     return _fill(lib().rp_fill_exp, engine, seed, stream, pos, out, torch.float64, cuda_stream=cuda_stream)
+
+
+# Float variants (suffix f): `out` a float32 CUDA tensor; the stream read as
+# 32-bit words, low half of each word first.
+def rp_fill_uniformf(engine, seed, stream, pos, out, cuda_stream=None):
+    return _fill(lib().rp_fill_uniformf, engine, seed, stream, pos, out, torch.float32, cuda_stream=cuda_stream)
+
+
+def rp_fill_normalf(engine, seed, stream, pos, out, cuda_stream=None):
+    return _fill(lib().rp_fill_normalf, engine, seed, stream, pos, out, torch.float32, cuda_stream=cuda_stream)
+
+
+def rp_fill_expf(engine, seed, stream, pos, out, cuda_stream=None):
+    return _fill(lib().rp_fill_expf, engine, seed, stream, pos, out, torch.float32, cuda_stream=cuda_stream)
 
 
 def rp_fill_gamma(engine, seed, stream, pos, alpha, out, cuda_stream=None):

@@ -228,6 +228,95 @@ struct SampBoundedOne32 {
   __device__ static __forceinline__ u64 value1(u64 u, const SampArgs& a) { u64 lo; return value_lo(u, a, lo); }
 };
 
+// ------------------------------------------------------------------ float variants
+// Table "continuous" (suffix f), Sec. 3.1 and Sec. 4.4: the engines' bit
+// stream read as 32-bit words.  Each 64-bit word gives its low half, then its
+// high half; a float fill starts at the low half of word *pos, and a fill
+// that ends on a low half leaves the high half unused.
+
+// u24(h) = floor(h / 2^8) 2^-24, exact in float and double.
+__device__ __forceinline__ double u24d(u64 h) { return (double)((unsigned)h >> 8) * 0x1.0p-24; }
+
+// A word engine read as half-words, each returned in the low 32 bits.  The
+// launch geometry in EngineArgs is in words (chunks and tiles of an even
+// number of half-words start on whole words).
+template <class E>
+struct HalfWords {
+  E e;
+  u64 hi;
+  int have;   // the high half of the last word is next
+  static constexpr int kStep = 2 * E::kStep, kLeanCtas = E::kLeanCtas;
+  __device__ void init_tile(const EngineArgs& a, unsigned c, int t, u64* sh) {
+    e.init_tile(a, c, t, sh);
+    have = 0;
+  }
+  __device__ __forceinline__ void advance(const EngineArgs& a) {
+    e.advance(a);
+    have = 0;
+  }
+  __device__ __forceinline__ u64 next() {
+    if (have) {
+      have = 0;
+      return hi;
+    }
+    const u64 w = e.next();
+    hi = w >> 32;
+    have = 1;
+    return w & 0xffffffffull;
+  }
+  __device__ __forceinline__ void next_step(u64 (&u)[kStep]) {
+    if (have) {   // not on a word boundary (the kernels step from chunk starts: never)
+#pragma unroll
+      for (int i = 0; i < kStep; ++i) u[i] = next();
+      return;
+    }
+    u64 w[E::kStep];
+    e.next_step(w);
+#pragma unroll
+    for (int i = 0; i < E::kStep; ++i) {
+      u[2 * i] = w[i] & 0xffffffffull;
+      u[2 * i + 1] = w[i] >> 32;
+    }
+  }
+};
+
+// uniformf, the paper's default method in float: the top 23 bits of the
+// half-word as the fraction of a float in [1, 2), minus 1, which is exactly
+// floor(h / 2^9) 2^-23.  Both halves of a word at once, as the 8 bytes of two
+// consecutive floats (low half first).
+__device__ __forceinline__ unsigned uniformf_bits(unsigned h) {
+  const unsigned v = h >> 9;
+  if (v == 0) return 0u;
+  const int lz = __clz(v);                          // >= 9
+  return ((unsigned)(135 - lz) << 23) + ((v << (lz - 8)) & 0x7fffffu);
+}
+struct SampUniformF2 {
+  static constexpr bool kOnePerWord = true;
+  static constexpr bool kCheckReject = false;
+  typedef u64 out_t;
+  __device__ static __forceinline__ u64 value1(u64 u, const SampArgs&) {
+    return (u64)uniformf_bits((unsigned)u) | ((u64)uniformf_bits((unsigned)(u >> 32)) << 32);
+  }
+};
+
+// Float ziggurat tail values from the queued half-words, computed in double
+// with the correctly rounded log and rounded once to float (the reading of
+// the float tails).
+struct SampNormalF {
+  typedef float out_t;
+  __device__ static double tail_value(u64 u0, u64 w1, const ZigDev& z) {
+    const double a = __ddiv_rn(-cr_log_nl(__dsub_rn(1.0, u24d(w1))), z.R);
+    const float v = __double2float_rn(__dadd_rn(z.R, a));
+    return ((u0 >> 8) & 1) ? -(double)v : (double)v;
+  }
+};
+struct SampExpF {
+  typedef float out_t;
+  __device__ static double tail_value(u64, u64 w1, const ZigDev& z) {
+    return (double)__double2float_rn(__dsub_rn(z.R, cr_log_nl(__dsub_rn(1.0, u24d(w1)))));
+  }
+};
+
 // Values of ziggurat tail outputs (FP64 libm log, within 2 ulp of the
 // correctly rounded value), evaluated by k_tails from the queued words.
 struct SampNormal {
@@ -1107,7 +1196,7 @@ __global__ void k_tails_rec(FillArgs a) {
 
 template <class S>
 __global__ void k_tails(FillArgs a) {
-  const ZigDev& z = g_zig[a.dist == D_EXP ? 1 : 0];
+  const ZigDev& z = g_zig[(a.dist == D_EXP || a.dist == D_EXPF) ? 1 : 0];
   unsigned long long n = ld_volatile(a.tail_count);
   if (n > a.tail_cap) n = a.tail_cap;
   typedef typename S::out_t OT;
@@ -1219,6 +1308,9 @@ int dispatch_dist(const FillArgs& a, int grid, cudaStream_t s, int* occ) {
       return (a.sp.m >> 32) ? launch_es<E, SampBoundedOne>(a, grid, s, occ) : launch_es<E, SampBoundedOne32>(a, grid, s, occ);
     case D_UNIFORM52: return launch_es<E, SampUniform52>(a, grid, s, occ);
     case D_FOLD: return launch_fold<E>(a, grid, s, occ);
+    case D_UNIFORMF2: return launch_es<E, SampUniformF2>(a, grid, s, occ);
+    case D_NORMALF: return launch_lean<HalfWords<E>, LeanNormalF>(a, grid, s, occ);
+    case D_EXPF: return launch_lean<HalfWords<E>, LeanExpF>(a, grid, s, occ);
     case D_NORMAL: return a.sp.epi ? launch_lean<E, LeanNormalE>(a, grid, s, occ) : launch_lean<E, LeanNormal>(a, grid, s, occ);
     case D_EXP: return a.sp.epi ? launch_lean<E, LeanExpE>(a, grid, s, occ) : launch_lean<E, LeanExp>(a, grid, s, occ);
     case D_GAMMA: return a.sp.ga.boost ? launch_merge<E, SampGammaBoost>(a, grid, s, occ) : launch_merge<E, SampGamma>(a, grid, s, occ);

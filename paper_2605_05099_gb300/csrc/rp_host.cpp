@@ -485,6 +485,7 @@ struct AsyncState {
   bool scr_used = false;
 };
 AsyncState g_async;
+u64* g_f1 = nullptr;   // device scratch word of the float uniform fill's odd last output
 
 cudaEvent_t take_event() {
   if (!g_async.free_ev.empty()) {
@@ -615,6 +616,8 @@ double words_per_variate(int dist, const rp::SampArgs& sp) {
     case rp::D_BOUNDED: return sp.m ? 1.0 / (1.0 - (double)sp.thresh * 0x1.0p-64) : 1.0;
     case rp::D_NORMAL: return 1.0235;
     case rp::D_EXP: return 1.036;
+    case rp::D_NORMALF: return 1.0235 / 2;   // half-words: words per variate
+    case rp::D_EXPF: return 1.036 / 2;
     case rp::D_GAMMA: return gamma_wpv(sp.ga);
     case rp::D_BETA: return gamma_wpv(sp.ga) + gamma_wpv(sp.gb);
     case rp::D_T: return 1.0235 + gamma_wpv(sp.ga);
@@ -663,7 +666,7 @@ rp_status run_fill_state_locked(int engine, const u64 s_in[4], u64* pos, size_t 
   auto key = std::make_pair(engine, dist | (sp.epi ? 256 : 0));   // transformed fills run other kernels
   if (!g_occ.count(key)) g_occ[key] = rp::occupancy_blocks(engine, dist, sp.epi);
   int occ = g_occ[key] > 0 ? g_occ[key] : 1;
-  const bool trivial = (dist == rp::D_U64 || dist == rp::D_UNIFORM || dist == rp::D_BOUNDED_ONE ||
+  const bool trivial = (dist == rp::D_U64 || dist == rp::D_UNIFORM || dist == rp::D_BOUNDED_ONE || dist == rp::D_UNIFORMF2 ||
                         dist == rp::D_UNIFORM52 || dist == rp::D_FOLD);
   const bool one_pass_check = dist == rp::D_BOUNDED_ONE;
   if (!trivial || one_pass_check) {
@@ -672,9 +675,13 @@ rp_status run_fill_state_locked(int engine, const u64 s_in[4], u64* pos, size_t 
     if (e) return cuda_fail(e, "scratch ordering");
   }
 
+  // Half-word fills (float ziggurats) count positions in half-words on the
+  // device; `half` is the first half-word of the next launch within word cur.
+  const bool halves = dist == rp::D_NORMALF || dist == rp::D_EXPF;
+  int half = 0;
   u64 cur = *pos;
   size_t done = 0;
-  const size_t esz = 8;
+  const size_t esz = halves ? 4 : 8;
   for (int launch = 0; done < n; ++launch) {
     if (launch > 64) return fail(RP_ERR_INTERNAL, "too many continuation launches");
     size_t left = n - done;
@@ -726,10 +733,11 @@ rp_status run_fill_state_locked(int engine, const u64 s_in[4], u64* pos, size_t 
     a.n = left;
     a.n_tiles = tiles;
     a.out = (char*)d_out + done * esz;
+    a.sp.half0 = half;
     if (!trivial || one_pass_check) {
       e = ensure_scratch(tiles);
       const bool queued = dist == rp::D_NORMAL || dist == rp::D_EXP || dist == rp::D_GAMMA || dist == rp::D_BETA ||
-                          dist == rp::D_T;
+                          dist == rp::D_T || dist == rp::D_NORMALF || dist == rp::D_EXPF;
       if (!e && queued) e = ensure_tailq(left / 256 + 4096);
       if (!e && dist == rp::D_BOUNDED) e = ensure_park((size_t)(grid * T));
       if (e) return fail(RP_ERR_NOMEM, std::string("scratch allocation: ") + cudaGetErrorString((cudaError_t)e));
@@ -772,7 +780,7 @@ rp_status run_fill_state_locked(int engine, const u64 s_in[4], u64* pos, size_t 
     if (async_mode) {
       // one launch, sized above with an eight-sigma margin; the device forms
       // the end position and the copy lands in the pinned *pos
-      e = rp::launch_finish(g_scr.ctrl, cur, g_async.dev, g_async.dev + 1, cstream);
+      e = rp::launch_finish(g_scr.ctrl, cur, g_async.dev, g_async.dev + 1, halves ? 1 : 0, cstream);
       if (e) return cuda_fail(e, "finishing kernel launch");
       g_launches.fetch_add(1);
       e = (int)cudaMemcpyAsync(pos, g_async.dev, sizeof(u64), cudaMemcpyDeviceToHost, (cudaStream_t)cstream);
@@ -811,31 +819,35 @@ rp_status run_fill_state_locked(int engine, const u64 s_in[4], u64* pos, size_t 
                    : "");
       return fail(c.err & rp::E_TIMEOUT ? RP_ERR_TIMEOUT : RP_ERR_INTERNAL, buf);
     }
-    if (c.done_tile != ~0ull) {
-      cur += c.next_pos;
-      done = n;
+    if (c.total == 0 && c.next_pos == 0 && c.done_tile == ~0ull) return fail(RP_ERR_INTERNAL, "launch produced no output");
+    done = c.done_tile != ~0ull ? n : done + c.total;
+    if (halves) {
+      const u64 h = c.next_pos;   // half-words from the low half of word cur (the launch began at `half`)
+      cur += h >> 1;
+      half = (int)(h & 1);
     } else {
-      if (c.total == 0 && c.next_pos == 0) return fail(RP_ERR_INTERNAL, "launch produced no output");
-      done += c.total;
       cur += c.next_pos;
     }
   }
-  *pos = cur;
+  // a half-word fill that ends on a low half leaves the high half unused
+  *pos = cur + (u64)half;
   return RP_OK;
 }
 
-rp_status check_fill_args(int engine, u64* pos, size_t n, void* d_out) {
+// Output alignment: the element size (4 for the float fills, else 8).
+rp_status check_fill_args(int engine, u64* pos, size_t n, void* d_out, int align = 8) {
   if (!pos) return fail(RP_ERR_NULL, "pos is NULL");
   if (n == 0) return RP_OK;
   if (!d_out) return fail(RP_ERR_NULL, "output pointer is NULL");
-  if ((uintptr_t)d_out & 7) return fail(RP_ERR_PARAM, "output pointer must be 8-byte aligned");
+  if ((uintptr_t)d_out & (uintptr_t)(align - 1))
+    return fail(RP_ERR_PARAM, "output pointer must be " + std::to_string(align) + "-byte aligned");
   if (engine < 1 || engine > 5) return fail(RP_ERR_ENGINE, "unknown engine id " + std::to_string(engine));
   return RP_OK;
 }
 
 rp_status run_fill(int engine, u64 seed, u64 stream, u64* pos, size_t n, int dist, const rp::SampArgs& sp,
                    void* d_out, void* cstream) {
-  rp_status st = check_fill_args(engine, pos, n, d_out);
+  rp_status st = check_fill_args(engine, pos, n, d_out, (dist == rp::D_NORMALF || dist == rp::D_EXPF) ? 4 : 8);
   if (st || n == 0) return st;
   std::lock_guard<std::mutex> lk(g_mu);
   u64 s[4] = {0, 0, 0, 0};
@@ -942,6 +954,52 @@ rp_status rp_fill_exp(rp_engine engine, uint64_t seed, uint64_t stream, uint64_t
                       void* cuda_stream) {
   rp::SampArgs sp{};
   return run_fill(engine, seed, stream, (u64*)pos, n, rp::D_EXP, sp, d_out, cuda_stream);
+}
+
+rp_status rp_fill_normalf(rp_engine engine, uint64_t seed, uint64_t stream, uint64_t* pos, size_t n, float* d_out,
+                          void* cuda_stream) {
+  rp::SampArgs sp{};
+  return run_fill(engine, seed, stream, (u64*)pos, n, rp::D_NORMALF, sp, d_out, cuda_stream);
+}
+
+rp_status rp_fill_expf(rp_engine engine, uint64_t seed, uint64_t stream, uint64_t* pos, size_t n, float* d_out,
+                       void* cuda_stream) {
+  rp::SampArgs sp{};
+  return run_fill(engine, seed, stream, (u64*)pos, n, rp::D_EXPF, sp, d_out, cuda_stream);
+}
+
+// Float uniforms: two per word, each word's pair written as 8 bytes; an odd
+// n takes the low half of one more word, through a one-word fill into a
+// scratch word and a 4-byte device copy.
+rp_status rp_fill_uniformf(rp_engine engine, uint64_t seed, uint64_t stream, uint64_t* pos, size_t n, float* d_out,
+                           void* cuda_stream) {
+  rp_status st = check_fill_args(engine, (u64*)pos, n, d_out);
+  if (st || n == 0) return st;
+  std::lock_guard<std::mutex> lk(g_mu);
+  u64 s[4] = {0, 0, 0, 0};
+  st = seed_state(engine, seed, stream, s);
+  if (st) return st;
+  rp::SampArgs sp{};
+  const size_t pairs = n / 2;
+  if (pairs) {
+    st = run_fill_state_locked(engine, s, (u64*)pos, pairs, rp::D_UNIFORMF2, sp, d_out, cuda_stream);
+    if (st) return st;
+  }
+  if (n & 1) {
+    if (!g_f1) {
+      const int e = (int)cudaMalloc((void**)&g_f1, sizeof(u64));
+      if (e) { g_f1 = nullptr; return fail(RP_ERR_NOMEM, "scratch word allocation failed"); }
+    }
+    // the scratch word is shared: order its use as the fill scratch's
+    int e = scratch_acquire(cuda_stream);
+    if (e) return cuda_fail(e, "scratch ordering");
+    st = run_fill_state_locked(engine, s, (u64*)pos, 1, rp::D_UNIFORMF2, sp, g_f1, cuda_stream);
+    if (st) return st;
+    e = (int)cudaMemcpyAsync(d_out + (n - 1), g_f1, sizeof(float), cudaMemcpyDeviceToDevice, (cudaStream_t)cuda_stream);
+    if (!e) e = scratch_release(cuda_stream);
+    if (e) return cuda_fail(e, "float uniform");
+  }
+  return RP_OK;
 }
 
 rp_status rp_fill_gamma(rp_engine engine, uint64_t seed, uint64_t stream, uint64_t* pos, size_t n, double alpha,

@@ -10,7 +10,10 @@ enum Dist : int { D_U64 = 0, D_UNIFORM = 1, D_BOUNDED = 2, D_NORMAL = 3, D_EXP =
                   D_BOUNDED_ONE = 7,   // bounded, one pass that assumes no rejection (records the first one)
                   D_T = 8,             // Student t: a normal, then a gamma (ep[0] = nu)
                   D_UNIFORM52 = 9,     // the paper's default 52-bit uniform
-                  D_FOLD = 10 };       // xor of the words, no output array (engine-only throughput)
+                  D_FOLD = 10,         // xor of the words, no output array (engine-only throughput)
+                  D_UNIFORMF2 = 11,    // float uniforms, two per word (the output as 8-byte pairs)
+                  D_NORMALF = 12,      // float ziggurat normal over 32-bit half-words
+                  D_EXPF = 13 };       // float ziggurat exponential over 32-bit half-words
 
 // Device error bits (ctrl->err)
 enum : unsigned {
@@ -89,7 +92,7 @@ struct SampArgs {
   MTParams ga, gb;            // gamma: ga; beta: X ~ ga, Y ~ gb
   double ep[4];               // output transform parameters
   int epi;                    // output transform (Epi), 0 for the base distributions
-  int pad;
+  int half0;                  // half-word fills: the first half-word of the launch to use (0 or 1)
 };
 
 struct FillArgs {
@@ -146,11 +149,11 @@ int launch_tails(const FillArgs& a, void* stream);
 // Sets a control block to its initial state on the stream (no host copy: a
 // copy from pageable memory would wait for the stream).
 int launch_ctrl_reset(Ctrl* ctrl, void* stream);
-// Asynchronous fills: writes start + ctrl->next_pos to d_pos (~0 when the
-// fill failed), and ORs the failure bits into sticky[0], counts failures in
+// Asynchronous fills: writes start + ctrl->next_pos to d_pos (halves: the
+// device counted half-words, start + ceil(next_pos / 2); ~0 when the fill failed), and ORs the failure bits into sticky[0], counts failures in
 // sticky[1] and keeps the first failure's tile in sticky[2].
 int launch_finish(const Ctrl* ctrl, unsigned long long start, unsigned long long* d_pos, unsigned long long* sticky,
-                  void* stream);
+                  int halves, void* stream);
 // Pairwise outputs from 2m base variates g: mode 0 beta X/(X+Y), 1 F
 // (X/p0)/(Y/p1), 2 skew normal p0 + p1 (p2 |u0| + p3 u1).
 int launch_pairs(const double* g, double* out, unsigned long long m, int mode, const double* p, void* stream);

@@ -116,20 +116,21 @@ int launch_ctrl_reset(Ctrl* ctrl, void* stream) {
   return (int)cudaGetLastError();
 }
 
-__global__ void k_finish(const Ctrl* __restrict__ c, u64 start, u64* __restrict__ d_pos, u64* __restrict__ sticky) {
+__global__ void k_finish(const Ctrl* __restrict__ c, u64 start, u64* __restrict__ d_pos, u64* __restrict__ sticky,
+                         int halves) {
   const unsigned err = c->err | (c->done_tile == ~0ull ? E_INCOMPLETE : 0u);
   if (err) {
     atomicOr(sticky, (u64)err);
     if (atomicAdd(sticky + 1, 1ull) == 0) sticky[2] = c->err_info;
     *d_pos = ~0ull;
   } else {
-    *d_pos = start + c->next_pos;
+    *d_pos = start + (halves ? (c->next_pos + 1) / 2 : c->next_pos);
   }
 }
 
 int launch_finish(const Ctrl* ctrl, unsigned long long start, unsigned long long* d_pos, unsigned long long* sticky,
-                  void* stream) {
-  k_finish<<<1, 1, 0, (cudaStream_t)stream>>>(ctrl, start, d_pos, sticky);
+                  int halves, void* stream) {
+  k_finish<<<1, 1, 0, (cudaStream_t)stream>>>(ctrl, start, d_pos, sticky, halves);
   return (int)cudaGetLastError();
 }
 
@@ -137,6 +138,8 @@ int launch_tails(const FillArgs& a, void* stream) {
   cudaStream_t s = (cudaStream_t)stream;
   if (a.dist == D_NORMAL) k_tails<SampNormal><<<304, 256, 0, s>>>(a);
   else if (a.dist == D_EXP) k_tails<SampExp><<<304, 256, 0, s>>>(a);
+  else if (a.dist == D_NORMALF) k_tails<SampNormalF><<<304, 256, 0, s>>>(a);
+  else if (a.dist == D_EXPF) k_tails<SampExpF><<<304, 256, 0, s>>>(a);
   else if (a.dist == D_GAMMA) k_tails_rec<SampGamma><<<304, 256, 0, s>>>(a);
   else if (a.dist == D_BETA) k_tails_rec<SampBeta><<<304, 256, 0, s>>>(a);
   else if (a.dist == D_T) k_tails_rec<SampT><<<304, 256, 0, s>>>(a);
@@ -210,6 +213,8 @@ TileGeom tile_geom(int engine, int dist, int gamma_boost) {
   if (dist == D_GAMMA) return TileGeom{NTM_, SampGamma::kChunk, MergeGeom<NTM_, SampGamma::kChunk>::T, 0};
   if (dist == D_BETA) return TileGeom{NTM_, SampBeta::kChunk, MergeGeom<NTM_, SampBeta::kChunk>::T, 0};
   if (dist == D_T) return TileGeom{NTM_, SampT::kChunk, MergeGeom<NTM_, SampT::kChunk>::T, 0};
+  // half-word fills: the kernel's chunk of C_ half-words is C_ / 2 words
+  if (dist == D_NORMALF || dist == D_EXPF) return TileGeom{NT_, C_ / 2, NT_ * C_ / 2, 0};
   if (dist == D_BOUNDED) return TileGeom{NT_, CR_, NT_ * CR_, 0};
   return TileGeom{NT_, C_, NT_ * C_, 0};
 }

@@ -40,6 +40,26 @@ __device__ __forceinline__ double mul_rn_fma(u64 r, double w) {
   return __fma_rn(D, w, (r >> 52) ? 0.0 : c);
 }
 
+// The walk's view of a word, per sampler:
+//   fast_hi   the 32-bit fast-accept test (top significand bits below the
+//             bound's), exact unless tie() (equal top bits: fast_exact decides);
+//   pack_pos  the wedge queue's second word with the candidate's position in
+//             bits the wedge test does not read (pos_of reads it back);
+//   tail_pair the normal tail's pair test;   tab_w  the table's w_i.
+#define LEAN_WORD_HOOKS                                                                               \
+  __device__ static __forceinline__ bool fast_hi(u64 u, const LeanTab& tb) {                          \
+    return (unsigned)(u >> 29) < tb.khi[u & 0xff];                                                    \
+  }                                                                                                   \
+  __device__ static __forceinline__ bool tie(u64 u, const LeanTab& tb) {                              \
+    return (unsigned)(u >> 29) == tb.khi[u & 0xff];                                                   \
+  }                                                                                                   \
+  __device__ static __forceinline__ u64 pack_pos(u64 u1, int pos) { return (u1 & ~0x7ffull) | (u64)pos; } \
+  __device__ static __forceinline__ int pos_of(u64 u1) { return (int)(u1 & 0x7ff); }                  \
+  __device__ static __forceinline__ bool tail_pair(u64 w1, u64 w2, const ZigDev& z) {                 \
+    return tail_pair_nl(w1, w2, z);                                                                   \
+  }                                                                                                   \
+  __device__ static __forceinline__ double tab_w(double w) { return w; }
+
 // Normal ziggurat (Sec. 3.1): bits 0-7 strip, bit 8 sign, bits 9-60 r.
 // kEpi: the base of a derived distribution, each value transformed as written.
 template <bool kEpi>
@@ -61,6 +81,7 @@ struct LeanNormalT {
     if (rh != kh) return rh < kh;
     return fast_exact(u, z);
   }
+  LEAN_WORD_HOOKS
   __device__ static __forceinline__ double value(u64 u, const LeanTab& tb, const SampArgs& a) {
     const double x = mul_rn_fma((u >> 9) & M52, tb.w[u & 0xff]);
     const double v = __longlong_as_double(__double_as_longlong(x) ^ (long long)((u >> 8 & 1) << 63));
@@ -103,6 +124,7 @@ struct LeanExpT {
     if (rh != kh) return rh < kh;
     return fast_exact(u, z);
   }
+  LEAN_WORD_HOOKS
   __device__ static __forceinline__ double value(u64 u, const LeanTab& tb, const SampArgs& a) {
     const double v = mul_rn_fma((u >> 8) & M53, tb.w[u & 0xff]);
     if constexpr (kEpi) return epi_value(v, a);
@@ -120,6 +142,119 @@ struct LeanExpT {
 using LeanExp = LeanExpT<false>;
 using LeanExpE = LeanExpT<true>;
 
+// ------------------------------------------------------------------ float ziggurats
+// The float variants (Table "continuous", suffix f) over 32-bit half-words
+// (HalfWords: each u holds one in its low 32 bits).  Normal: bits 0-7 strip,
+// bit 8 sign, bits 9-31 r (23 bits); exponential: bits 8-31 r (24 bits).
+// x = RN_f(r wf_i) with wf_i = RN_f(2^29 w_i); fast accept r < k_i / 2^29
+// (integer division); the wedge takes y = RN_f((f_{i-1} - f_i) U + f_i) in
+// float operations with f_i = RN_f(F_i) and U = u24 of the next half-word,
+// and accepts y < exp(t) (t = -x^2/2 or -x, exact in double) against the
+// correctly rounded exp; tails are the double samplers' with U = u24 of the
+// next half-words, in double, rounded once to float (k_tails).
+
+// Wedge test of the float samplers: FP32 with the margin of wedge_accept,
+// then the exact decision.
+template <bool kNormal>
+__device__ __noinline__ bool wedge_f(unsigned r, int i, unsigned h1, const ZigDev& z) {
+  const float x = __fmul_rn((float)r, __fmul_rn(z.wf[i], 0x1.0p29f));
+  const float U = (float)(h1 >> 8) * 0x1.0p-24f;
+  const float y = __fadd_rn(__fmul_rn(__fsub_rn(z.ff[i - 1], z.ff[i]), U), z.ff[i]);
+  const float tf = kNormal ? __fmul_rn(__fmul_rn(-0.5f, x), x) : -x;
+  const float ef = expf(tf);
+  const float m = 0x1.0p-19f * (1.0f - tf);
+  if (y < ef * (1.0f - m)) return true;
+  if (y > ef * (1.0f + m)) return false;
+  dbg_count(DBG_WEDGE_FP64);
+  const double xd = (double)x;
+  const double t = kNormal ? __dmul_rn(-0.5, __dmul_rn(xd, xd)) : -xd;
+  return lt_cr_exp((double)y, t);
+}
+
+// Normal tail pair over half-words: a = -log(1 - U1)/R, b = -log(1 - U2),
+// accept when 2b > a^2; libm logs decide unless within their error, then
+// the correctly rounded ones.
+__device__ __noinline__ bool tail_pair_f(u64 w1, u64 w2, const ZigDev& z) {
+  const double o1 = __dsub_rn(1.0, u24d(w1)), o2 = __dsub_rn(1.0, u24d(w2));
+  double a = __ddiv_rn(-log(o1), z.R), b = -log(o2);
+  double l2 = __dadd_rn(b, b), r2 = __dmul_rn(a, a);
+  const double mg = (l2 + r2) * 0x1.0p-48;
+  if (l2 > r2 + mg) return true;
+  if (l2 < r2 - mg) return false;
+  dbg_count(DBG_TAIL_CR);
+  a = __ddiv_rn(-cr_log_nl(o1), z.R);
+  b = -cr_log_nl(o2);
+  return __dadd_rn(b, b) > __dmul_rn(a, a);
+}
+
+#define LEAN_HALF_HOOKS                                                                               \
+  __device__ static __forceinline__ bool fast_exact(u64 u, const ZigDev& z) {                         \
+    return r_of(u) < (unsigned)(z.k[u & 0xff] >> 29);                                                 \
+  }                                                                                                   \
+  __device__ static __forceinline__ bool fast(u64 u, const LeanTab& tb, const ZigDev&) {              \
+    return r_of(u) < tb.khi[u & 0xff];                                                                \
+  }                                                                                                   \
+  __device__ static __forceinline__ bool fast_hi(u64 u, const LeanTab& tb) { return r_of(u) < tb.khi[u & 0xff]; } \
+  __device__ static __forceinline__ bool tie(u64, const LeanTab&) { return false; }                   \
+  __device__ static __forceinline__ u64 pack_pos(u64 u1, int pos) { return (u1 & 0xffffffffull) | ((u64)pos << 32); } \
+  __device__ static __forceinline__ int pos_of(u64 u1) { return (int)(u1 >> 32); }                   \
+  __device__ static __forceinline__ bool tail_pair(u64 w1, u64 w2, const ZigDev& z) {                 \
+    return tail_pair_f(w1, w2, z);                                                                    \
+  }                                                                                                   \
+  __device__ static __forceinline__ double tab_w(double w) {                                          \
+    return (double)__fmul_rn(__double2float_rn(w), 0x1.0p29f);                                        \
+  }
+
+struct LeanNormalF {
+  static constexpr bool kSync = true;
+  static constexpr int kWhich = 0;
+  static constexpr int kKShift = 29;   // k_i >> 29: the 23-bit bound itself
+  static constexpr int kG = 16, kS = 16;
+  static constexpr bool kTailPairs = true;
+  typedef float out_t;
+  __device__ static __forceinline__ unsigned r_of(u64 u) { return ((unsigned)u >> 9) & 0x7fffffu; }
+  LEAN_HALF_HOOKS
+  __device__ static __forceinline__ float value(u64 u, const LeanTab& tb, const SampArgs&) {
+    const float x = __fmul_rn((float)r_of(u), (float)tb.w[u & 0xff]);
+    return ((u >> 8) & 1) ? -x : x;
+  }
+  __device__ static __forceinline__ bool wedge(u64 u0, u64 u1, const ZigDev& z) {
+    return wedge_f<true>(r_of(u0), (int)(u0 & 0xff), (unsigned)u1, z);
+  }
+  template <class E>
+  __device__ static __forceinline__ int len(u64 u, const E& g, const LeanTab& tb, const ZigDev& z) {
+    if (fast(u, tb, z)) return 1;
+    if ((u & 0xff) != 0) return 2;
+    E h = g;
+    for (int k = 1; k <= kTailPairsMax; ++k) {
+      u64 a = h.next(), b = h.next();
+      if (tail_pair_f(a, b, z)) return 1 + 2 * k;
+    }
+    return 1 << 20;
+  }
+};
+
+struct LeanExpF {
+  static constexpr bool kSync = true;
+  static constexpr int kWhich = 1;
+  static constexpr int kKShift = 29;   // k_i >> 29: the 24-bit bound itself
+  static constexpr int kG = 2, kS = 24;
+  static constexpr bool kTailPairs = false;
+  typedef float out_t;
+  __device__ static __forceinline__ unsigned r_of(u64 u) { return (unsigned)u >> 8; }
+  LEAN_HALF_HOOKS
+  __device__ static __forceinline__ float value(u64 u, const LeanTab& tb, const SampArgs&) {
+    return __fmul_rn((float)r_of(u), (float)tb.w[u & 0xff]);
+  }
+  __device__ static __forceinline__ bool wedge(u64 u0, u64 u1, const ZigDev& z) {
+    return wedge_f<false>(r_of(u0), (int)(u0 & 0xff), (unsigned)u1, z);
+  }
+  template <class E>
+  __device__ static __forceinline__ int len(u64 u, const E&, const LeanTab& tb, const ZigDev& z) {
+    return fast(u, tb, z) ? 1 : 2;
+  }
+};
+
 // Lemire (Sec. 3.2): one word per attempt, no seams to synchronise.
 struct LeanBounded {
   static constexpr bool kSync = false;
@@ -129,6 +264,7 @@ struct LeanBounded {
   static constexpr bool kTailPairs = false;
   typedef u64 out_t;
   __device__ static __forceinline__ bool fast_exact(u64, const ZigDev&) { return true; }
+  LEAN_WORD_HOOKS
   __device__ static __forceinline__ u64 value(u64 u, const LeanTab&, const SampArgs& a) {
     return __umul64hi(u, a.m);
   }
@@ -172,13 +308,13 @@ __device__ __forceinline__ void lean_rare(u64 u, int p, int b, unsigned& mw, Lea
   };
   if (c.st == 0) {
     // a candidate that missed the 32-bit test: only equal top bits need the full compare
-    if ((unsigned)(u >> 29) == tb.khi[u & 0xff] && S::fast_exact(u, z)) { mark(p); return; }
+    if (S::tie(u, tb) && S::fast_exact(u, z)) { mark(p); return; }
     c.pu0 = u;
     c.pp = p;
     c.st = (u & 0xff) ? 1 : (S::kTailPairs ? 2 : 4);
   } else if (c.st == 1) {
     c.st = 0;
-    const u64 u1 = (u & ~0x7ffull) | (u64)c.pp;   // U uses bits 11-63: the position rides in the low bits
+    const u64 u1 = S::pack_pos(u, c.pp);   // the position rides in bits the wedge test does not read
     if (c.np < kLPend) {
       queue[(c.np * NT + t) * 2] = c.pu0;
       queue[(c.np * NT + t) * 2 + 1] = u1;
@@ -193,7 +329,7 @@ __device__ __forceinline__ void lean_rare(u64 u, int p, int b, unsigned& mw, Lea
   } else if (c.st == 2) {
     c.pw1 = u;
     c.st = 3;
-  } else if (tail_pair_nl(c.pw1, u, z)) {
+  } else if (S::tail_pair(c.pw1, u, z)) {
     c.st = 0;
     mark(c.pp);
     tail_rec(c.pw1);
@@ -207,8 +343,7 @@ template <int NT, class S>
 __device__ __forceinline__ void lean_step(u64 u, int p, int b, unsigned& mw, LeanChain& c, const LeanTab& tb,
                                           const ZigDev& z, unsigned (*msk)[NT], u64* queue, u64 (*tails)[3],
                                           int* ntails, Ctrl* ctrl, u64 k) {
-  const unsigned rh = (unsigned)(u >> 29), kh = tb.khi[u & 0xff];
-  if (c.st == 0 && rh < kh) mw |= 1u << (p & 31);
+  if (c.st == 0 && S::fast_hi(u, tb)) mw |= 1u << (p & 31);
   else lean_rare<NT, S>(u, p, b, mw, c, tb, z, msk, queue, tails, ntails, ctrl, k);
 }
 
@@ -253,7 +388,7 @@ template <int NT, class S>
 __device__ __forceinline__ void lean_push_wedge(u64 u0, u64 u1, int pos, int b, unsigned& mw, LeanChain& c,
                                                 const ZigDev& z, unsigned (*msk)[NT], u64* queue) {
   const int t = threadIdx.x;
-  const u64 u1p = (u1 & ~0x7ffull) | (u64)pos;   // U uses bits 11-63: the position rides in the low bits
+  const u64 u1p = S::pack_pos(u1, pos);   // the position rides in bits the wedge test does not read
   if (c.np < kLPend) {
     queue[(c.np * NT + t) * 2] = u0;
     queue[(c.np * NT + t) * 2 + 1] = u1p;
@@ -333,7 +468,7 @@ __device__ __forceinline__ void lean_half(int P0, int from, unsigned F, const u6
       const int j = __ffs(W) - 1;
       W &= W - 1;
       const u64 u0 = wb[j * NT + t];
-      if ((unsigned)(u0 >> 29) == tb.khi[u0 & 0xff] && S::fast_exact(u0, z)) {
+      if (S::tie(u0, tb) && S::fast_exact(u0, z)) {
         stop = j;
         tie = true;
         break;
@@ -364,7 +499,7 @@ __device__ __forceinline__ void lean_half(int P0, int from, unsigned F, const u6
     int q = t0 + 1;
     bool acc = false;
     for (; q + 1 < 16; q += 2) {
-      if (tail_pair_nl(wb[q * NT + t], wb[(q + 1) * NT + t], z)) {
+      if (S::tail_pair(wb[q * NT + t], wb[(q + 1) * NT + t], z)) {
         lean_exp_tail<NT>(wb[t0 * NT + t], wb[q * NT + t], P0 + t0, b, mw, msk, tails, ntails, ctrl, k);
         acc = true;
         q += 2;
@@ -404,7 +539,7 @@ __device__ __forceinline__ void lean_load_tab(LeanTab& tb, int nt) {
   const ZigDev& z = g_zig[S::kWhich];
   for (int i = threadIdx.x; i < 256; i += nt) {
     tb.khi[i] = (unsigned)(z.k[i] >> S::kKShift);
-    tb.w[i] = z.w[i];
+    tb.w[i] = S::tab_w(z.w[i]);
   }
 }
 
@@ -416,7 +551,7 @@ template <int NT, int C, class E, class S>
 __device__ bool lean_tile(const FillArgs& a, u64 k, const E& e, LeanSmem<NT, C>& sm, const LeanTab& tb, int par) {
   static_assert(C % 32 == 0, "chunks are whole mask words");
   typedef typename S::out_t OT;
-  static_assert(sizeof(OT) == 8, "staging holds 8-byte outputs");
+  static_assert(sizeof(OT) == 8 || sizeof(OT) == 4, "staging holds 8- or 4-byte outputs");
   constexpr int T = NT * C;
   constexpr int kMW = LeanSmem<NT, C>::kMW;
   const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
@@ -429,7 +564,7 @@ __device__ bool lean_tile(const FillArgs& a, u64 k, const E& e, LeanSmem<NT, C>&
   if (sm.misc[5]) return false;
     int* nts = &sm.ntails[par];
     // ---------------- pass 1: sync point, chain walk with output bitmap
-    int s = 0, endp = C;
+    int s = (k == 0 && t == 0) ? a.sp.half0 : 0, endp = C;   // half0: a half-word fill resumed mid-word
     bool ok = true;
     if (S::kSync && !(k == 0 && t == 0)) {
       E h = e;
@@ -474,7 +609,7 @@ __device__ bool lean_tile(const FillArgs& a, u64 k, const E& e, LeanSmem<NT, C>&
 #pragma unroll
             for (int i = 0; i < E::kStep; ++i) {
               wb[(j + i) * NT + t] = u[i];
-              F |= (unsigned)((unsigned)(u[i] >> 29) < tb.khi[u[i] & 0xff]) << (j + i);
+              F |= (unsigned)S::fast_hi(u[i], tb) << (j + i);
             }
           }
           const int from = max(0, min(16, s - P0));
@@ -501,7 +636,7 @@ __device__ bool lean_tile(const FillArgs& a, u64 k, const E& e, LeanSmem<NT, C>&
       for (int j = 0; j < c.np; ++j) {
         const u64 u0 = sm.sbuf[(j * NT + t) * 2], u1 = sm.sbuf[(j * NT + t) * 2 + 1];
         if (S::wedge(u0, u1, z)) {
-          const int q = (int)(u1 & 0x7ff);
+          const int q = S::pos_of(u1);
           sm.msk[q >> 5][t] |= 1u << (q & 31);
         }
       }
