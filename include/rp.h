@@ -193,6 +193,13 @@ rp_status rp_fill_gamma(rp_engine engine, uint64_t seed, uint64_t stream, uint64
 rp_status rp_fill_beta(rp_engine engine, uint64_t seed, uint64_t stream, uint64_t* pos,
                        size_t n, double a, double b, double* d_out, void* cuda_stream);
 
+/* rp_fill_beta that also writes each output's gamma pair: d_x[i] = X_i,
+ * d_y[i] = Y_i with z_i = X_i / (X_i + Y_i) (the same z as rp_fill_beta,
+ * bit for bit), for the composed gradient (rp_beta_grad_composed).  No
+ * counterpart in the paper.  d_x, d_y: n doubles each, 8-byte aligned. */
+rp_status rp_fill_beta_xy(rp_engine engine, uint64_t seed, uint64_t stream, uint64_t* pos, size_t n, double a,
+                          double b, double* d_z, double* d_x, double* d_y, void* cuda_stream);
+
 /* Derived distributions (Table "continuous"; Sec. 3.1 "Gamma and related
  * distributions", "Extreme value and Weibull distributions").  Each output
  * transforms the base sampler's variate as it is written, in the formula's
@@ -343,6 +350,17 @@ rp_status rp_gamma_grad(const double* d_z, double alpha, const double* d_g, size
                         double* h_grad_alpha, void* cuda_stream);
 rp_status rp_beta_grad(const double* d_z, double a, double b, const double* d_g, size_t n, double* d_dzda,
                        double* d_dzdb, double* h_grad_a, double* h_grad_b, void* cuda_stream);
+
+/* Beta gradient through the gamma composition (the alternative to the CDF
+ * derivative above; not in the paper): with z = X / (X + Y) and X ~ Gamma(a),
+ * Y ~ Gamma(b) each reparameterised by its own CDF,
+ *   dz/da = Y / (X + Y)^2 dX/da,   dz/db = -X / (X + Y)^2 dY/db,
+ * dX/da and dY/db being rp_gamma_grad's implicit derivatives.  d_x, d_y: the
+ * n gamma pairs of the beta draws (rp_fill_beta_xy); other arguments as for
+ * rp_beta_grad.  NULL d_dzda/d_dzdb are replaced by temporaries for the call. */
+rp_status rp_beta_grad_composed(const double* d_x, const double* d_y, double a, double b, const double* d_g,
+                                size_t n, double* d_dzda, double* d_dzdb, double* h_grad_a, double* h_grad_b,
+                                void* cuda_stream);
 
 /* ---------------------------------------------------------------------
  * Multivariate normal (Sec. 3.1, multivariate normal): x = mu + L z for n

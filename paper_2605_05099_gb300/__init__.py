@@ -76,6 +76,8 @@ def lib():
             "rp_debug_faults": [i32, u64],
             "rp_async_status": [vp],
             "rp_fill_uniformf": [i32, u64, u64, pu64, sz, vp, vp],
+            "rp_fill_beta_xy": [i32, u64, u64, pu64, sz, dbl, dbl, vp, vp, vp, vp],
+            "rp_beta_grad_composed": [vp, vp, dbl, dbl, vp, sz, vp, vp, ctypes.POINTER(dbl), ctypes.POINTER(dbl), vp],
             "rp_fill_normalf": [i32, u64, u64, pu64, sz, vp, vp],
             "rp_fill_expf": [i32, u64, u64, pu64, sz, vp, vp],
             "rp_substream_state": [i32, u64, u64, pu64, ctypes.POINTER(i32)],
@@ -277,6 +279,31 @@ def rp_beta_grad(z, a, b, g=None, dzda=None, dzdb=None, cuda_stream=None):
     ga, gb = ctypes.c_double(), ctypes.c_double()
     _check(lib().rp_beta_grad(_ptr_or_null(z, n), float(a), float(b), _ptr_or_null(g, n), n, _ptr_or_null(dzda, n),
                               _ptr_or_null(dzdb, n), ctypes.byref(ga), ctypes.byref(gb), _stream_handle(cuda_stream)))
+    return (ga.value, gb.value) if g is not None else None
+
+
+def rp_fill_beta_xy(engine, seed, stream, pos, a, b, z, x, y, cuda_stream=None):
+    """rp_fill_beta that also keeps each output's gamma pair in x and y
+    (float64 CUDA tensors of the same length); returns the new position."""
+    p, n = _out(z, torch.float64)
+    px, nx = _out(x, torch.float64)
+    py, ny = _out(y, torch.float64)
+    if nx != n or ny != n:
+        raise ValueError("z, x and y must have the same length")
+    cpos = ctypes.c_uint64(pos)
+    _check(lib().rp_fill_beta_xy(_engine(engine), seed, stream, ctypes.byref(cpos), n, float(a), float(b), p, px, py,
+                                 _stream_handle(cuda_stream)))
+    return cpos.value
+
+
+def rp_beta_grad_composed(x, y, a, b, g=None, dzda=None, dzdb=None, cuda_stream=None):
+    """Beta gradient through the gamma pairs (x, y): dz/da, dz/db per sample
+    (optional) and the sums with g (None without g)."""
+    n = x.numel()
+    ga, gb = ctypes.c_double(), ctypes.c_double()
+    _check(lib().rp_beta_grad_composed(_ptr_or_null(x, n), _ptr_or_null(y, n), float(a), float(b), _ptr_or_null(g, n), n,
+                                       _ptr_or_null(dzda, n), _ptr_or_null(dzdb, n), ctypes.byref(ga), ctypes.byref(gb),
+                                       _stream_handle(cuda_stream)))
     return (ga.value, gb.value) if g is not None else None
 
 

@@ -1125,7 +1125,7 @@ __device__ bool merge_tile_ph(const FillArgs& a, u64 k, const E& e, MergeSmem<NT
         int c = __shfl_sync(0xffffffffu, ns, rr);
         if (col < c && d + col < a.n) {
           const u64* r = &sm.stage[0][(rr * (kRecS + 1) + col) * kRecW];
-          if (!r[7]) out[d + col] = S::value(r, a.sp, z);
+          if (!r[7]) S::store(out, d + col, r, a.sp, z);
         }
       }
       __syncwarp();
@@ -1190,7 +1190,8 @@ __global__ void k_tails_rec(FillArgs a) {
   for (unsigned long long i = blockIdx.x * (u64)blockDim.x + threadIdx.x; i < n; i += (u64)gridDim.x * blockDim.x) {
     TailEntry te = a.tailq[i];
     u64 r[8] = {te.w0, te.x[0], te.x[1], te.x[2], te.x[3], te.x[4], te.x[5], 0};
-    out[te.g] = S::value(r, a.sp, z);
+    if constexpr (S::kPhased) S::store(out, te.g, r, a.sp, z);   // beta: keeps the gamma pair when asked
+    else out[te.g] = S::value(r, a.sp, z);
   }
 }
 

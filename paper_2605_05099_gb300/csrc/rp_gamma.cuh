@@ -289,6 +289,18 @@ struct SampBeta {
     if (a.epi == EPI_F) return __ddiv_rn(__ddiv_rn(X, a.ep[0]), __ddiv_rn(Y, a.ep[1]));   // F(nu1, nu2)
     return __ddiv_rn(X, __dadd_rn(X, Y));
   }
+  // Writes output i, and its gamma pair when the fill keeps them (sp.outx).
+  __device__ static __forceinline__ void store(double* out, u64 i, const u64* r, const SampArgs& a, const ZigDev& z) {
+    if (!a.outx) {
+      out[i] = value(r, a, z);
+      return;
+    }
+    const double X = gamma_value((int)(r[0] & 0xff), r[1], r[2], r[3], a.ga, z);
+    const double Y = gamma_value((int)((r[0] >> 8) & 0xff), r[4], r[5], r[6], a.gb, z);
+    out[i] = __ddiv_rn(X, __dadd_rn(X, Y));
+    a.outx[i] = X;
+    a.outy[i] = Y;
+  }
 };
 
 // Student t (Table "continuous": the normal-gamma mixture Z / sqrt(V / nu)),

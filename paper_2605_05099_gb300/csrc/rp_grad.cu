@@ -462,6 +462,33 @@ __global__ void __launch_bounds__(kGradThreads) k_beta_grad(const double* __rest
   if (threadIdx.x == 0) { part[2 * blockIdx.x] = s1s; part[2 * blockIdx.x + 1] = s2s; }
 }
 
+// Beta through its gamma pair (z = X / (X + Y), each gamma reparameterised by
+// its own CDF): dz/da = Y / (X + Y)^2 dX/da, dz/db = -X / (X + Y)^2 dY/db.
+// dzda and dzdb hold dX/da and dY/db on entry (the gamma gradient kernel's
+// outputs) and the beta gradients on exit; the sums with g as for k_beta_grad.
+__global__ void __launch_bounds__(kGradThreads) k_beta_compose(const double* __restrict__ x,
+                                                                 const double* __restrict__ y,
+                                                                 const double* __restrict__ g, size_t n,
+                                                                 double* __restrict__ dzda, double* __restrict__ dzdb,
+                                                                 double* __restrict__ part) {
+  __shared__ double sh[kWarps];
+  double aa = 0.0, ab = 0.0;
+  for (size_t i = blockIdx.x * (size_t)kGradThreads + threadIdx.x; i < n; i += (size_t)gridDim.x * kGradThreads) {
+    const double X = x[i], Y = y[i];
+    const double s = X + Y, s2 = s * s;
+    const double da = Y / s2 * dzda[i], db = -X / s2 * dzdb[i];
+    dzda[i] = da;
+    dzdb[i] = db;
+    if (g) {
+      aa += g[i] * da;
+      ab += g[i] * db;
+    }
+  }
+  const double s1 = block_sum(aa, sh);
+  const double s2s = block_sum(ab, sh);
+  if (threadIdx.x == 0) { part[2 * blockIdx.x] = s1; part[2 * blockIdx.x + 1] = s2s; }
+}
+
 // fixed-order final reduction of the block partials (k values of stride k)
 __global__ void k_sum_parts(const double* __restrict__ part, int nblk, int k, double* __restrict__ out) {
   __shared__ double sh[kGradThreads / 32];
@@ -485,6 +512,14 @@ int launch_gamma_grad(const double* z, const double* g, size_t n, double alpha, 
   k_gamma_tab<<<1, kTabThreads, 0, s>>>(alpha, tab);
   k_gamma_grad<<<grad_blocks(), kGradThreads, 0, s>>>(z, g, n, alpha, tab, dz, part);
   k_sum_parts<<<1, kGradThreads, 0, s>>>(part, grad_blocks(), 1, out);
+  return (int)cudaGetLastError();
+}
+
+int launch_beta_compose(const double* x, const double* y, const double* g, size_t n, double* dzda, double* dzdb,
+                        double* part, double* out, void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  k_beta_compose<<<grad_blocks(), kGradThreads, 0, s>>>(x, y, g, n, dzda, dzdb, part);
+  k_sum_parts<<<1, kGradThreads, 0, s>>>(part, grad_blocks(), 2, out);
   return (int)cudaGetLastError();
 }
 

@@ -734,6 +734,10 @@ rp_status run_fill_state_locked(int engine, const u64 s_in[4], u64* pos, size_t 
     a.n_tiles = tiles;
     a.out = (char*)d_out + done * esz;
     a.sp.half0 = half;
+    if (sp.outx) {   // beta keeping its gamma pairs: the same output index
+      a.sp.outx = sp.outx + done;
+      a.sp.outy = sp.outy + done;
+    }
     if (!trivial || one_pass_check) {
       e = ensure_scratch(tiles);
       const bool queued = dist == rp::D_NORMAL || dist == rp::D_EXP || dist == rp::D_GAMMA || dist == rp::D_BETA ||
@@ -1025,6 +1029,46 @@ rp_status rp_fill_beta(rp_engine engine, uint64_t seed, uint64_t stream, uint64_
   return pairs_fill(engine, seed, stream, (u64*)pos, n, rp::D_GAMMA, sg, 0, nullptr, d_out, cuda_stream);
 }
 
+// Beta(a, b) that also keeps each output's gamma pair (X, Y): unequal shapes
+// store them from the merge kernel; equal shapes take a gamma fill of 2n and
+// a pairwise kernel, as rp_fill_beta does.
+rp_status rp_fill_beta_xy(rp_engine engine, uint64_t seed, uint64_t stream, uint64_t* pos, size_t n, double a, double b,
+                          double* d_z, double* d_x, double* d_y, void* cuda_stream) {
+  if (!(a > 0.0) || !(b > 0.0) || !std::isfinite(a) || !std::isfinite(b))
+    return fail(RP_ERR_PARAM, "beta parameters must be positive and finite");
+  if (n && (!d_x || !d_y)) return fail(RP_ERR_NULL, "d_x/d_y is NULL");
+  if (((uintptr_t)d_x | (uintptr_t)d_y) & 7) return fail(RP_ERR_PARAM, "d_x/d_y must be 8-byte aligned");
+  rp::SampArgs sp{};
+  sp.ga = mt_params(a);
+  sp.gb = mt_params(b);
+  if (a != b) {
+    sp.outx = d_x;
+    sp.outy = d_y;
+    return run_fill(engine, seed, stream, (u64*)pos, n, rp::D_BETA, sp, d_z, cuda_stream);
+  }
+  rp_status st = check_fill_args(engine, (u64*)pos, n, d_z);
+  if (st || n == 0) return st;
+  const size_t blk = (size_t)1 << 26;
+  double* tmp = nullptr;
+  const size_t cap = std::min(n, blk);
+  int e = (int)cudaMalloc((void**)&tmp, cap * 2 * sizeof(double));
+  if (e) return fail(RP_ERR_NOMEM, "beta scratch allocation failed");
+  u64 p = *pos;
+  rp::SampArgs sg{};
+  sg.ga = sp.ga;
+  for (size_t done = 0; done < n && st == RP_OK; done += cap) {
+    const size_t m = std::min(cap, n - done);
+    st = run_fill(engine, seed, stream, &p, 2 * m, rp::D_GAMMA, sg, tmp, cuda_stream);
+    if (st) break;
+    e = rp::launch_pairs_xy(tmp, d_z + done, d_x + done, d_y + done, m, cuda_stream);
+    if (!e) e = (int)cudaStreamSynchronize((cudaStream_t)cuda_stream);
+    if (e) st = cuda_fail(e, "beta pairs");
+  }
+  cudaFree(tmp);
+  if (st == RP_OK) *pos = p;
+  return st;
+}
+
 // Derived distributions (Table "continuous"): a base fill whose outputs are
 // transformed as they are written (see the Epi codes), or, for two draws of
 // one law per output, a base fill of 2n and a pairwise kernel.
@@ -1164,6 +1208,48 @@ rp_status rp_beta_grad(const double* d_z, double a, double b, const double* d_g,
   e = (int)cudaMemcpyAsync(g_grad_h, out, 2 * sizeof(double), cudaMemcpyDeviceToHost, (cudaStream_t)cuda_stream);
   if (!e) e = (int)cudaStreamSynchronize((cudaStream_t)cuda_stream);
   if (e) return cuda_fail(e, "beta gradient");
+  if (d_g) { *h_grad_a = g_grad_h[0]; *h_grad_b = g_grad_h[1]; }
+  return RP_OK;
+}
+
+rp_status rp_beta_grad_composed(const double* d_x, const double* d_y, double a, double b, const double* d_g, size_t n,
+                                double* d_dzda, double* d_dzdb, double* h_grad_a, double* h_grad_b, void* cuda_stream) {
+  if (!(a > 0.0) || !(b > 0.0) || !std::isfinite(a) || !std::isfinite(b))
+    return fail(RP_ERR_PARAM, "beta parameters must be positive and finite");
+  if (n == 0) {
+    if (h_grad_a) *h_grad_a = 0.0;
+    if (h_grad_b) *h_grad_b = 0.0;
+    return RP_OK;
+  }
+  if (!d_x || !d_y) return fail(RP_ERR_NULL, "d_x/d_y is NULL");
+  if (d_g && (!h_grad_a || !h_grad_b)) return fail(RP_ERR_NULL, "h_grad_a/h_grad_b is NULL while upstream gradients are given");
+  if (!d_g && !d_dzda && !d_dzdb) return fail(RP_ERR_NULL, "nothing to compute");
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (rp_status dg = device_guard()) return dg;
+  int e = ensure_grad_scratch();
+  if (e) return fail(RP_ERR_NOMEM, "gradient scratch allocation failed");
+  // dX/da and dY/db land in the output arrays (or in temporaries), then the
+  // composition rewrites them in place
+  double *ta = d_dzda, *tb = d_dzdb, *tmp = nullptr;
+  if (!ta || !tb) {
+    e = (int)cudaMalloc((void**)&tmp, (size_t)n * sizeof(double) * ((!ta && !tb) ? 2 : 1));
+    if (e) return fail(RP_ERR_NOMEM, "gradient temporaries allocation failed");
+    if (!ta) ta = tmp;
+    if (!tb) tb = tmp + (d_dzda ? 0 : n);
+  }
+  double* out = g_grad_part + 2 * (size_t)rp::grad_blocks();
+  e = rp::launch_gamma_grad(d_x, nullptr, n, a, ta, g_grad_part, out, cuda_stream);
+  if (!e) e = rp::launch_gamma_grad(d_y, nullptr, n, b, tb, g_grad_part, out, cuda_stream);
+  if (!e) e = rp::launch_beta_compose(d_x, d_y, d_g, n, ta, tb, g_grad_part, out, cuda_stream);
+  if (e) {
+    if (tmp) cudaFree(tmp);
+    return cuda_fail(e, "composed beta gradient launch");
+  }
+  g_launches.fetch_add(8);
+  e = (int)cudaMemcpyAsync(g_grad_h, out, 2 * sizeof(double), cudaMemcpyDeviceToHost, (cudaStream_t)cuda_stream);
+  if (!e) e = (int)cudaStreamSynchronize((cudaStream_t)cuda_stream);
+  if (tmp) cudaFree(tmp);
+  if (e) return cuda_fail(e, "composed beta gradient");
   if (d_g) { *h_grad_a = g_grad_h[0]; *h_grad_b = g_grad_h[1]; }
   return RP_OK;
 }

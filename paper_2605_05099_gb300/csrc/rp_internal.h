@@ -93,6 +93,8 @@ struct SampArgs {
   double ep[4];               // output transform parameters
   int epi;                    // output transform (Epi), 0 for the base distributions
   int half0;                  // half-word fills: the first half-word of the launch to use (0 or 1)
+  double* outx;               // beta: when not NULL, each output's gamma pair X, Y is also
+  double* outy;               //   written here (same index as the output)
 };
 
 struct FillArgs {
@@ -165,6 +167,12 @@ int launch_gamma_grad(const double* z, const double* g, size_t n, double alpha, 
                       void* stream);
 int launch_beta_grad(const double* z, const double* g, size_t n, double a, double b, double* dza, double* dzb,
                      double* part, double* out, void* stream);
+// Beta gradient through the gamma pair: dzda <- Y/(X+Y)^2 dzda (dX/da on
+// entry), dzdb <- -X/(X+Y)^2 dzdb (dY/db on entry), and the two sums with g.
+int launch_beta_compose(const double* x, const double* y, const double* g, size_t n, double* dzda, double* dzdb,
+                        double* part, double* out, void* stream);
+// Beta with equal shapes from 2m consecutive gammas g: z = X/(X+Y), and X, Y kept.
+int launch_pairs_xy(const double* g, double* z, double* x, double* y, unsigned long long m, void* stream);
 // Fixed scratch of the normal fill that allocates nothing
 // (rp_static_scratch.cu).  Sized for at most kStaticMaxN outputs per call:
 // a Philox normal fill of n outputs needs at most

@@ -165,6 +165,24 @@ __global__ void k_pairs(const double* __restrict__ g, double* __restrict__ out, 
   }
 }
 
+// Beta with equal shapes, keeping each output's gamma pair.
+__global__ void k_pairs_xy(const double* __restrict__ g, double* __restrict__ z, double* __restrict__ x,
+                           double* __restrict__ y, u64 m) {
+  for (u64 j = blockIdx.x * (u64)blockDim.x + threadIdx.x; j < m; j += (u64)gridDim.x * blockDim.x) {
+    const double2 xy = reinterpret_cast<const double2*>(g)[j];
+    z[j] = __ddiv_rn(xy.x, __dadd_rn(xy.x, xy.y));
+    x[j] = xy.x;
+    y[j] = xy.y;
+  }
+}
+
+int launch_pairs_xy(const double* g, double* z, double* x, double* y, unsigned long long m, void* stream) {
+  if (m == 0) return 0;
+  const unsigned long long blocks = (m + 255) / 256;
+  k_pairs_xy<<<(unsigned)(blocks < 4096 ? blocks : 4096), 256, 0, (cudaStream_t)stream>>>(g, z, x, y, m);
+  return (int)cudaGetLastError();
+}
+
 int launch_pairs(const double* g, double* out, unsigned long long m, int mode, const double* p, void* stream) {
   if (!m) return 0;
   const double q[4] = {p ? p[0] : 0.0, p ? p[1] : 0.0, p ? p[2] : 0.0, p ? p[3] : 0.0};
