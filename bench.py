@@ -269,39 +269,35 @@ def run_gpu(args):
         roof[f"engine_issue_frac:{eng}"] = round(ceil[eng] * ENGINE_OPS[eng] / issue_peak, 3)
     roof.update(flat)
 
-    # ---- end to end through the public API with host buffers: every fill's
-    # result is copied back to pinned host memory inside the timed region.
-    # Two device buffers: fill i + 1 runs while fill i is copied back on a
-    # second stream; the device-to-host copy, not the fills, bounds this leg.
+    # ---- end to end through the C ABI with host buffers: rp_fill_to_host
+    # fills a device staging slot and copies it to pinned host memory inside
+    # the library (its copy stream overlaps the next fill); the positions are
+    # pinned words written by the stream.  Timed from the first call to the
+    # device synchronisation after the last copy.
     e2e = None
     if rank == 0 or world > 1:
-        dbuf = [torch.empty(N_FILL * 8, dtype=torch.uint8, device="cuda") for _ in range(2)]
-        hbuf = [torch.empty(N_FILL * 8, dtype=torch.uint8, pin_memory=True) for _ in range(2)]
-        cstream = torch.cuda.Stream()
-        copied = [None, None]
         e_steps = max(1, args.steps)
+        hbuf = [torch.empty(N_FILL, dtype=torch.int64, pin_memory=True) for _ in range(2)]
+        hpos = torch.zeros(e_steps * len(fills), dtype=torch.int64, pin_memory=True)
+        codes = {"normal": 3, "exp": 4, "bounded": 2}
+        # untimed: staging slots and tables in place
+        rp.rp_fill_to_host(fills[0][0], SEED, spawn, 0, codes[fills[0][1]], hbuf[0],
+                           m=fills[0][2][0] if fills[0][2] else 0, cuda_stream=stream)
         torch.cuda.synchronize()
-        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a0.record(stream)
+        h0 = time.perf_counter()
         i = 0
         for _ in range(e_steps):
             for e, d, p in fills:
-                slot = i % 2
-                if copied[slot] is not None:
-                    stream.wait_event(copied[slot])   # the buffer's previous copy is done
-                one_fill(e, d, p, dbuf[slot])
-                cstream.wait_stream(stream)
-                with torch.cuda.stream(cstream):
-                    hbuf[slot].copy_(dbuf[slot], non_blocking=True)
-                copied[slot] = torch.cuda.Event()
-                copied[slot].record(cstream)
+                rp.rp_fill_to_host(e, SEED, spawn, hpos[i:i + 1], codes[d], hbuf[i % 2], m=p[0] if p else 0,
+                                   cuda_stream=stream)
                 i += 1
-        a1.record(cstream)
         torch.cuda.synchronize()
-        ems = a0.elapsed_time(a1)
-        e2e = {"value": len(fills) * N_FILL * e_steps / (ems / 1e3), "unit": "variates/s",
-               "h2d_bytes_per_step": 0, "d2h_bytes_per_step": len(fills) * N_FILL * 8}
-        del dbuf, hbuf
+        esec = time.perf_counter() - h0
+        rp.rp_async_status(None)
+        e2e = {"value": len(fills) * N_FILL * e_steps / esec, "unit": "variates/s",
+               "h2d_bytes_per_step": 0, "d2h_bytes_per_step": len(fills) * N_FILL * 8,
+               "api": "rp_fill_to_host (C ABI, host buffers; copies inside the library)"}
+        del hbuf
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -421,6 +417,13 @@ def run_extras(rp, stream):
         bg = lambda: rp.rp_beta_grad(z, ab[0], ab[1], g, dz, dz2, stream)
         bg()
         grads[f"beta{ab}"] = n / (_ev_ms(stream, bg) / 1e3)
+    zx, zy = torch.empty_like(z), torch.empty_like(z)
+    for ab in ((2.0, 5.0),):
+        rp.rp_fill_beta_xy("xoshiro256pp", 7, rp.NO_STREAM, 0, ab[0], ab[1], z, zx, zy, stream)
+        bg = lambda: rp.rp_beta_grad_composed(zx, zy, ab[0], ab[1], g, dz, dz2, stream)
+        bg()
+        grads[f"beta_composed{ab}"] = n / (_ev_ms(stream, bg) / 1e3)
+    del zx, zy
     ex["gamma_beta_fill"] = {"unit": "variates/s", "n": n, **{k: round(v) for k, v in fwd.items()}}
     props = torch.cuda.get_device_properties(0)
     fp64_peak = props.multi_processor_count * FP64_FLOPS_PER_SM_CLK * 2.07e9
@@ -461,6 +464,21 @@ def run_extras(rp, stream):
             ph[key] = {"ms": round(ms, 4), "variates_per_s": round(n28 / (ms / 1e3))}
         ex[f"{eng}_fills"] = {"n": n28, **ph}
     del of
+    torch.cuda.empty_cache()
+    # float variants (suffix f), n = 2^28 floats (1 GiB), 4 B per output
+    ff = torch.empty(n28, dtype=torch.float32, device="cuda")
+    fl = {}
+    peaks, _ = _peaks()
+    for eng in ENGINES:
+        for key, fn in (("uniformf", rp.rp_fill_uniformf), ("normalf", rp.rp_fill_normalf), ("expf", rp.rp_fill_expf)):
+            f = lambda: fn(eng, SEED, rp.NO_STREAM, 0, ff, stream)
+            f()
+            ms = _ev_ms(stream, f, reps=3)
+            fl[f"{eng}/{key}"] = {"ms": round(ms, 4), "variates_per_s": round(n28 / (ms / 1e3)),
+                                  "write_gbs": round(4.0 * n28 / (ms / 1e3) / 1e9, 1),
+                                  "frac_hbm_copy_peak": round(4.0 * n28 / (ms / 1e3) / 1e9 / peaks["hbm_gbs"], 3)}
+    ex["float_fills"] = {"n": n28, **fl}
+    del ff
     torch.cuda.empty_cache()
     # batched substreams (config 4)
     reqs = inputs.batch_workload()

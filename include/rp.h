@@ -250,6 +250,20 @@ typedef enum {
   RP_DIST_UNIFORM52 = 7  /* 52-bit U[0,1), the paper's default (rp_fill_uniform52) */
 } rp_dist;
 
+/* A fill into host memory, the end-to-end form of rp_fill_state's
+ * distributions (dist, p0, p1, m as there): the library fills one of two
+ * device staging slots on cuda_stream and copies it to h_out (n 8-byte
+ * elements) on its own copy stream, so that a fill overlaps the previous
+ * call's copy.  With h_out in pinned memory the call returns once the work
+ * is enqueued and h_out is complete after the device is synchronised
+ * (cudaDeviceSynchronize, or rp_async_status(NULL)); synchronising
+ * cuda_stream alone does not cover the copy.  With h_out in pageable memory
+ * the copy completes before the call returns.  *pos as for the fills
+ * (written asynchronously when pinned).  Library convenience: the paper's
+ * fills write host memory directly. */
+rp_status rp_fill_to_host(rp_engine engine, uint64_t seed, uint64_t stream, uint64_t* pos, int dist, size_t n,
+                          double p0, double p1, uint64_t m, void* h_out, void* cuda_stream);
+
 /* Fill n variates of `dist` from a stream given by its state words (the
  * engine before word 0, layout of rp_seed_state), starting at word *pos;
  * *pos is set to the next unused word.  Same values as the seeded fills of

@@ -77,6 +77,7 @@ def lib():
             "rp_async_status": [vp],
             "rp_fill_uniformf": [i32, u64, u64, pu64, sz, vp, vp],
             "rp_fill_beta_xy": [i32, u64, u64, pu64, sz, dbl, dbl, vp, vp, vp, vp],
+            "rp_fill_to_host": [i32, u64, u64, pu64, i32, sz, dbl, dbl, u64, vp, vp],
             "rp_beta_grad_composed": [vp, vp, dbl, dbl, vp, sz, vp, vp, ctypes.POINTER(dbl), ctypes.POINTER(dbl), vp],
             "rp_fill_normalf": [i32, u64, u64, pu64, sz, vp, vp],
             "rp_fill_expf": [i32, u64, u64, pu64, sz, vp, vp],
@@ -280,6 +281,24 @@ def rp_beta_grad(z, a, b, g=None, dzda=None, dzdb=None, cuda_stream=None):
     _check(lib().rp_beta_grad(_ptr_or_null(z, n), float(a), float(b), _ptr_or_null(g, n), n, _ptr_or_null(dzda, n),
                               _ptr_or_null(dzdb, n), ctypes.byref(ga), ctypes.byref(gb), _stream_handle(cuda_stream)))
     return (ga.value, gb.value) if g is not None else None
+
+
+def rp_fill_to_host(engine, seed, stream, pos, dist, out, p0=0.0, p1=0.0, m=0, cuda_stream=None):
+    """rp_fill_state's distribution `dist` (a DIST name or code), seeded, into
+    `out`, a CPU tensor of 8-byte elements (pinned: asynchronous, complete
+    after torch.cuda.synchronize()).  pos: an int (returns the new position)
+    or a pinned 1-element tensor (written asynchronously; returns None)."""
+    if out.is_cuda or out.element_size() != 8 or not out.is_contiguous():
+        raise TypeError("out must be a contiguous CPU tensor of 8-byte elements")
+    d = DISTS[dist] if isinstance(dist, str) else int(dist)
+    args = (_engine(engine), seed, stream)
+    tail = (d, out.numel(), float(p0), float(p1), int(m), ctypes.c_void_p(out.data_ptr()), _stream_handle(cuda_stream))
+    if isinstance(pos, torch.Tensor):
+        _check(lib().rp_fill_to_host(*args, _pinned_pos(pos), *tail))
+        return None
+    cpos = ctypes.c_uint64(pos)
+    _check(lib().rp_fill_to_host(*args, ctypes.byref(cpos), *tail))
+    return cpos.value
 
 
 def rp_fill_beta_xy(engine, seed, stream, pos, a, b, z, x, y, cuda_stream=None):

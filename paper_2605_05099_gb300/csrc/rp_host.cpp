@@ -1577,6 +1577,75 @@ extern "C" rp_status rp_fill_state(rp_engine engine, const uint64_t* words, uint
   return run_fill_state_locked(engine, s, (u64*)pos, n, kd, sp, d_out, cuda_stream);
 }
 
+namespace {
+// Staging of rp_fill_to_host: two device slots, filled in turn on the
+// caller's stream and copied out on the library's copy stream, so that a
+// fill overlaps the previous call's copy.
+struct HostStage {
+  void* slot[2] = {nullptr, nullptr};
+  size_t cap = 0;
+  cudaEvent_t copied[2] = {nullptr, nullptr};   // the slot's last copy is done
+  cudaEvent_t filled = nullptr;
+  cudaStream_t copy_stream = nullptr;
+  int next = 0;
+};
+HostStage g_hs;
+
+int host_stage_ensure(size_t bytes) {
+  int e = 0;
+  if (!g_hs.copy_stream) {
+    e = (int)cudaStreamCreateWithFlags(&g_hs.copy_stream, cudaStreamNonBlocking);
+    for (int i = 0; i < 2 && !e; ++i) e = (int)cudaEventCreateWithFlags(&g_hs.copied[i], cudaEventDisableTiming);
+    if (!e) e = (int)cudaEventCreateWithFlags(&g_hs.filled, cudaEventDisableTiming);
+    if (e) return e;
+  }
+  if (bytes > g_hs.cap) {
+    for (int i = 0; i < 2; ++i)
+      if (g_hs.slot[i]) cudaFree(g_hs.slot[i]);   // waits for the device (earlier copies) first
+    g_hs.slot[0] = g_hs.slot[1] = nullptr;
+    g_hs.cap = 0;
+    for (int i = 0; i < 2 && !e; ++i) e = (int)cudaMalloc(&g_hs.slot[i], bytes);
+    if (e) return e;
+    g_hs.cap = bytes;
+  }
+  return 0;
+}
+}  // namespace
+
+extern "C" rp_status rp_fill_to_host(rp_engine engine, uint64_t seed, uint64_t stream, uint64_t* pos, int dist, size_t n,
+                                     double p0, double p1, uint64_t m, void* h_out, void* cuda_stream) {
+  if (!pos) return fail(RP_ERR_NULL, "pos is NULL");
+  if (n == 0) return RP_OK;
+  if (!h_out) return fail(RP_ERR_NULL, "h_out is NULL");
+  if (engine < 1 || engine > 5) return fail(RP_ERR_ENGINE, "unknown engine id " + std::to_string((int)engine));
+  rp::SampArgs sp;
+  int kd = 0;
+  rp_status st = make_samp(dist, p0, p1, m, sp, &kd);
+  if (st) return st;
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (rp_status dg = device_guard()) return dg;
+  u64 s[4] = {0, 0, 0, 0};
+  st = seed_state(engine, seed, stream, s);
+  if (st) return st;
+  const size_t bytes = n * 8;
+  int e = host_stage_ensure(bytes);
+  if (e) return fail(RP_ERR_NOMEM, "host staging allocation failed");
+  const int k = g_hs.next;
+  g_hs.next ^= 1;
+  cudaStream_t cs = (cudaStream_t)cuda_stream;
+  e = (int)cudaStreamWaitEvent(cs, g_hs.copied[k], 0);   // the slot's previous copy has left it
+  if (e) return cuda_fail(e, "staging order");
+  if (dist == RP_DIST_BETA && p0 == p1) st = beta_equal_state_locked(engine, s, (u64*)pos, n, sp, (double*)g_hs.slot[k], cuda_stream);
+  else st = run_fill_state_locked(engine, s, (u64*)pos, n, kd, sp, g_hs.slot[k], cuda_stream);
+  if (st) return st;
+  e = (int)cudaEventRecord(g_hs.filled, cs);
+  if (!e) e = (int)cudaStreamWaitEvent(g_hs.copy_stream, g_hs.filled, 0);
+  if (!e) e = (int)cudaMemcpyAsync(h_out, g_hs.slot[k], bytes, cudaMemcpyDeviceToHost, g_hs.copy_stream);
+  if (!e) e = (int)cudaEventRecord(g_hs.copied[k], g_hs.copy_stream);
+  if (e) return cuda_fail(e, "copy to host");
+  return RP_OK;
+}
+
 extern "C" rp_status rp_substream_state(rp_engine engine, uint64_t base_seed, uint64_t s, uint64_t* words, int* nw) {
   if (!words || !nw) return fail(RP_ERR_NULL, "words/nw is NULL");
   if (engine < 1 || engine > 5) return fail(RP_ERR_ENGINE, "unknown engine id " + std::to_string((int)engine));

@@ -170,3 +170,32 @@ def test_failures_are_reported_after_the_sync():
     torch.cuda.synchronize()
     rp.rp_async_status()
     assert int(pp[0]) == pos and np.array_equal(_bits(out), _bits(ref))
+
+
+@pytest.mark.parametrize("dist,params", [("normal", ()), ("bounded", (6,)), ("gamma", (2.5,)), ("u64", ())])
+@pytest.mark.parametrize("pinned", [True, False])
+def test_fill_to_host(dist, params, pinned):
+    """rp_fill_to_host: the same values and position as the device fill, in
+    pinned (asynchronous) and pageable host memory; consecutive calls
+    alternate staging slots, so three calls in a row must all land."""
+    n = 300_001
+    kw = {"p0": params[0]} if dist == "gamma" else ({"m": params[0]} if dist == "bounded" else {})
+    refs, outs, poss = [], [], []
+    pos = 0
+    for k in range(3):
+        r = _new(dist if dist != "bounded" else "bounded6", n)
+        pos = FILLS[{"normal": "normal", "bounded": "bounded6", "gamma": "gamma", "u64": "u64"}[dist]](
+            "philox4x32_10", 77, pos, r, None)
+        refs.append(r)
+    p = 0
+    for k in range(3):
+        h = torch.empty(n, dtype=torch.int64)
+        if pinned:
+            h = h.pin_memory()
+        p = rp.rp_fill_to_host("philox4x32_10", 77, rp.NO_STREAM, p, dist, h, **kw)
+        outs.append(h)
+    torch.cuda.synchronize()
+    rp.rp_async_status(None)
+    assert p == pos
+    for h, r in zip(outs, refs):
+        assert np.array_equal(h.numpy(), _bits(r))
