@@ -59,7 +59,7 @@ ENGINE_OPS = {"xoshiro256pp": 20, "pcg64dxsm": 42, "philox4x32_10": 42}
 # counted by ncu on n = 2^24 samples of the same workloads
 # (profiles/k_gamma_grad_n2e24.md, profiles/k_beta_grad_a2_b5_n2e24.md); the
 # kernels are bound by the FP64 pipe: 2 DFMA per SM per clock.
-GRAD_FLOPS = {"gamma(2.5)": 252.5, "gamma(30.0)": 371.9, "beta(2.0, 5.0)": 483.1}
+GRAD_FLOPS = {"gamma(2.5)": 252.5, "gamma(30.0)": 371.9, "beta(2.0, 5.0)": 442.3}
 FP64_FLOPS_PER_SM_CLK = 4
 ISSUE_LANES_PER_SM = 128
 
