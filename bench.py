@@ -532,7 +532,7 @@ def run_extras(rp, stream):
 def run_profile(args):
     """One workload alone, for ncu (--profile KIND; not a bench line):
     gamma:ALPHA, beta:A:B, grad:ALPHA (gamma gradient), bgrad:A:B (beta
-    gradient), mvn:D (forward and
+    gradient), normalf|expf|uniformf[:ENGINE] (float fills), mvn:D (forward and
     backward, n = 2^20) or batch:ENGINE (4096 requests; --log2n scales the
     request sizes' upper end).  Runs --warmup untimed and --steps timed
     repetitions and prints their mean time."""
@@ -564,6 +564,12 @@ def run_profile(args):
                 g = torch.tensor(inputs.upstream_grads(n), device="cuda")
                 dz = torch.empty_like(z)
                 f = lambda: rp.rp_gamma_grad(z, a_, g, dz, stream)
+    elif kind in ("normalf", "expf", "uniformf"):
+        n = 1 << args.log2n
+        ff = torch.empty(n, dtype=torch.float32, device="cuda")
+        fn = {"normalf": rp.rp_fill_normalf, "expf": rp.rp_fill_expf, "uniformf": rp.rp_fill_uniformf}[kind]
+        eng = vals[0] if vals else "xoshiro256pp"
+        f = lambda: fn(eng, SEED, rp.NO_STREAM, 0, ff, stream)
     elif kind == "mvn":
         d, n = int(vals[0]), 1 << 20
         mu_h, L_h = inputs.mvn_inputs(d)

@@ -25,7 +25,8 @@ __device__ __noinline__ bool wedge_nl(u64 r, int i, u64 u2, const ZigDev& z) { r
 
 struct LeanTab {
   unsigned khi[256];   // top 32 bits of the 52/53-bit fast-accept bound k_i
-  double w[256];       // w_i
+  double w[256];       // w_i; the float samplers keep their float w_i's bits in the low word
+                       // (read as a float with no conversion on the FP64 pipe)
 };
 
 // RN(r w) for 0 <= r < 2^53 with one fused multiply-add: D = 2^52 + (r mod
@@ -202,7 +203,10 @@ __device__ __noinline__ bool tail_pair_f(u64 w1, u64 w2, const ZigDev& z) {
     return tail_pair_f(w1, w2, z);                                                                    \
   }                                                                                                   \
   __device__ static __forceinline__ double tab_w(double w) {                                          \
-    return (double)__fmul_rn(__double2float_rn(w), 0x1.0p29f);                                        \
+    return __longlong_as_double((long long)__float_as_uint(__fmul_rn(__double2float_rn(w), 0x1.0p29f))); \
+  }                                                                                                   \
+  __device__ static __forceinline__ float wf_of(const LeanTab& tb, u64 u) {                           \
+    return __uint_as_float((unsigned)__double_as_longlong(tb.w[u & 0xff]));                           \
   }
 
 struct LeanNormalF {
@@ -215,7 +219,7 @@ struct LeanNormalF {
   __device__ static __forceinline__ unsigned r_of(u64 u) { return ((unsigned)u >> 9) & 0x7fffffu; }
   LEAN_HALF_HOOKS
   __device__ static __forceinline__ float value(u64 u, const LeanTab& tb, const SampArgs&) {
-    const float x = __fmul_rn((float)r_of(u), (float)tb.w[u & 0xff]);
+    const float x = __fmul_rn((float)r_of(u), wf_of(tb, u));
     return ((u >> 8) & 1) ? -x : x;
   }
   __device__ static __forceinline__ bool wedge(u64 u0, u64 u1, const ZigDev& z) {
@@ -244,7 +248,7 @@ struct LeanExpF {
   __device__ static __forceinline__ unsigned r_of(u64 u) { return (unsigned)u >> 8; }
   LEAN_HALF_HOOKS
   __device__ static __forceinline__ float value(u64 u, const LeanTab& tb, const SampArgs&) {
-    return __fmul_rn((float)r_of(u), (float)tb.w[u & 0xff]);
+    return __fmul_rn((float)r_of(u), wf_of(tb, u));
   }
   __device__ static __forceinline__ bool wedge(u64 u0, u64 u1, const ZigDev& z) {
     return wedge_f<false>(r_of(u0), (int)(u0 & 0xff), (unsigned)u1, z);
