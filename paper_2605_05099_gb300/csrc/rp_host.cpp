@@ -877,6 +877,7 @@ rp_status pairs_fill(int engine, u64 seed, u64 stream, u64* pos, size_t n, int b
     st = run_fill(engine, seed, stream, &p, 2 * m, base, sb, tmp, cuda_stream);
     if (st) break;
     e = rp::launch_pairs(tmp, d_out + done, m, mode, q, cuda_stream);
+    if (!e) g_launches.fetch_add(1);
     if (!e) e = (int)cudaStreamSynchronize((cudaStream_t)cuda_stream);
     if (e) st = cuda_fail(e, "pairwise outputs");
   }
@@ -1061,6 +1062,7 @@ rp_status rp_fill_beta_xy(rp_engine engine, uint64_t seed, uint64_t stream, uint
     st = run_fill(engine, seed, stream, &p, 2 * m, rp::D_GAMMA, sg, tmp, cuda_stream);
     if (st) break;
     e = rp::launch_pairs_xy(tmp, d_z + done, d_x + done, d_y + done, m, cuda_stream);
+    if (!e) g_launches.fetch_add(1);
     if (!e) e = (int)cudaStreamSynchronize((cudaStream_t)cuda_stream);
     if (e) st = cuda_fail(e, "beta pairs");
   }
@@ -1535,6 +1537,7 @@ rp_status beta_equal_state_locked(int engine, const u64 s[4], u64* pos, size_t n
     st = run_fill_state_locked(engine, s, &p, 2 * m, rp::D_GAMMA, sg, tmp, cstream);
     if (st) break;
     e = rp::launch_pairs(tmp, d_out + done, m, 0, nullptr, cstream);
+    if (!e) g_launches.fetch_add(1);
     if (!e) e = (int)cudaStreamSynchronize((cudaStream_t)cstream);
     if (e) st = cuda_fail(e, "beta pairs");
   }
