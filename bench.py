@@ -280,6 +280,18 @@ def run_gpu(args):
         hbuf = [torch.empty(N_FILL, dtype=torch.int64, pin_memory=True) for _ in range(2)]
         hpos = torch.zeros(e_steps * len(fills), dtype=torch.int64, pin_memory=True)
         codes = {"normal": 3, "exp": 4, "bounded": 2}
+        # the link's own rate: a plain 2 GiB device-to-host copy into the same
+        # pinned buffer, the ceiling of this leg (8 bytes per variate cross it)
+        dsrc = torch.zeros(N_FILL, dtype=torch.int64, device="cuda")
+        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        link = 0.0
+        for _ in range(3):
+            c0.record()
+            hbuf[0].copy_(dsrc, non_blocking=True)
+            c1.record()
+            c1.synchronize()
+            link = max(link, N_FILL * 8 / (c0.elapsed_time(c1) * 1e-3) / 1e9)
+        del dsrc
         # untimed: staging slots and tables in place
         rp.rp_fill_to_host(fills[0][0], SEED, spawn, 0, codes[fills[0][1]], hbuf[0],
                            m=fills[0][2][0] if fills[0][2] else 0, cuda_stream=stream)
@@ -296,7 +308,9 @@ def run_gpu(args):
         rp.rp_async_status(None)
         e2e = {"value": len(fills) * N_FILL * e_steps / esec, "unit": "variates/s",
                "h2d_bytes_per_step": 0, "d2h_bytes_per_step": len(fills) * N_FILL * 8,
-               "api": "rp_fill_to_host (C ABI, host buffers; copies inside the library)"}
+               "api": "rp_fill_to_host (C ABI, host buffers; copies inside the library)",
+               "d2h_copy_gbs": round(link, 1),
+               "frac_of_d2h_copy": round(len(fills) * N_FILL * e_steps * 8 / esec / 1e9 / link, 3)}
         del hbuf
 
     cpu = None
