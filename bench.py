@@ -34,7 +34,7 @@ WORKLOAD = "single-stream fills: engines {xoshiro256++, PCG64-DXSM, Philox4x32-1
 # one ncu capture at n = 2^26 scaled by outputs (profiles/*_n2e26.md), by fill
 # key.  Only kernels whose current version was captured are listed.
 TRAFFIC = {
-    "philox4x32_10/bounded:9223372036854775809": 4 * 1579835928,
+    "philox4x32_10/bounded:9223372036854775809": 4 * 1580355904,
 }
 
 
@@ -280,22 +280,28 @@ def run_gpu(args):
         hbuf = [torch.empty(N_FILL, dtype=torch.int64, pin_memory=True) for _ in range(2)]
         hpos = torch.zeros(e_steps * len(fills), dtype=torch.int64, pin_memory=True)
         codes = {"normal": 3, "exp": 4, "bounded": 2}
-        # the link's own rate: a plain 2 GiB device-to-host copy into the same
-        # pinned buffer, the ceiling of this leg (8 bytes per variate cross it)
+        # the link's own rate, the ceiling of this leg (8 bytes per variate
+        # cross it): plain 2 GiB device-to-host copies into the same pinned
+        # buffers, one step's worth back to back, before and after the leg
         dsrc = torch.zeros(N_FILL, dtype=torch.int64, device="cuda")
-        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        link = 0.0
-        for _ in range(3):
+
+        def link_gbs():
+            c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             c0.record()
-            hbuf[0].copy_(dsrc, non_blocking=True)
+            for j in range(len(fills)):
+                hbuf[j % 2].copy_(dsrc, non_blocking=True)
             c1.record()
             c1.synchronize()
-            link = max(link, N_FILL * 8 / (c0.elapsed_time(c1) * 1e-3) / 1e9)
-        del dsrc
-        # untimed: staging slots and tables in place
-        rp.rp_fill_to_host(fills[0][0], SEED, spawn, 0, codes[fills[0][1]], hbuf[0],
-                           m=fills[0][2][0] if fills[0][2] else 0, cuda_stream=stream)
+            return len(fills) * N_FILL * 8 / (c0.elapsed_time(c1) * 1e-3) / 1e9
+        link = link_gbs()
+        # untimed: one step of the same calls puts the staging slots and every
+        # fill's tables in place
+        wpos = torch.zeros(len(fills), dtype=torch.int64, pin_memory=True)
+        for j, (e, d, p) in enumerate(fills):
+            rp.rp_fill_to_host(e, SEED, spawn, wpos[j:j + 1], codes[d], hbuf[j % 2], m=p[0] if p else 0,
+                               cuda_stream=stream)
         torch.cuda.synchronize()
+        rp.rp_async_status(None)
         h0 = time.perf_counter()
         i = 0
         for _ in range(e_steps):
@@ -306,10 +312,12 @@ def run_gpu(args):
         torch.cuda.synchronize()
         esec = time.perf_counter() - h0
         rp.rp_async_status(None)
+        link_after = link_gbs()
+        del dsrc
         e2e = {"value": len(fills) * N_FILL * e_steps / esec, "unit": "variates/s",
                "h2d_bytes_per_step": 0, "d2h_bytes_per_step": len(fills) * N_FILL * 8,
                "api": "rp_fill_to_host (C ABI, host buffers; copies inside the library)",
-               "d2h_copy_gbs": round(link, 1),
+               "d2h_copy_gbs": round(link, 1), "d2h_copy_gbs_after": round(link_after, 1),
                "frac_of_d2h_copy": round(len(fills) * N_FILL * e_steps * 8 / esec / 1e9 / link, 3)}
         del hbuf
 
@@ -399,16 +407,34 @@ def run_extras(rp, stream):
     w = torch.empty(1 << 20, dtype=torch.uint64, device="cuda")
     u = torch.empty(1 << 20, dtype=torch.float64, device="cuda")
 
-    def c1():
-        p = rp.rp_fill_u64("xoshiro256pp", 12345, rp.NO_STREAM, 0, w, stream)
-        rp.rp_fill_uniform("xoshiro256pp", 12345, rp.NO_STREAM, p, u, stream)
+    def c1(cs=stream):
+        p = rp.rp_fill_u64("xoshiro256pp", 12345, rp.NO_STREAM, 0, w, cs)
+        rp.rp_fill_uniform("xoshiro256pp", 12345, rp.NO_STREAM, p, u, cs)
     c1()
-    # one-word fills do not wait for their kernels: 100 back-to-back pairs
-    # between the events time the device work, not host round trips
+    # one-word fills do not wait for their kernels: 100 back-to-back pairs of
+    # calls between the events (host launch rate included) ...
     ms = _ev_ms(stream, lambda: [c1() for _ in range(100)], reps=3) / 100
-    ex["config1_words_then_uniforms"] = {"variates_per_s": 2 * (1 << 20) / (ms / 1e3), "ms": ms,
-                                         "replays": 100}
-    del w, u
+    # ... and the same 100 pairs captured once into a CUDA graph and replayed
+    # (device time alone); the replayed outputs are checked against the calls'
+    ref_w, ref_u = w.clone(), u.clone()
+    cap = torch.cuda.Stream()
+    cap.wait_stream(stream)
+    with torch.cuda.stream(cap):
+        c1(cap)                                   # tables and jump tables in place on this stream
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=cap, capture_error_mode="relaxed"):
+        for _ in range(100):
+            c1(cap)
+    w.zero_()
+    u.zero_()
+    ms_g = _ev_ms(stream, graph.replay, reps=3) / 100
+    torch.cuda.synchronize()
+    same = bool(torch.equal(w.view(torch.int64), ref_w.view(torch.int64)) and torch.equal(u, ref_u))
+    ex["config1_words_then_uniforms"] = {"variates_per_s": 2 * (1 << 20) / (ms_g / 1e3), "ms": ms_g,
+                                         "form": "CUDA graph of 100 fill pairs, replayed", "replays": 100,
+                                         "replay_outputs_identical": same,
+                                         "variates_per_s_calls": 2 * (1 << 20) / (ms / 1e3), "ms_calls": ms}
+    del graph, w, u, ref_w, ref_u
     # gamma / beta forward and gradients (config 3)
     n = 1 << 26
     z = torch.empty(n, dtype=torch.float64, device="cuda")

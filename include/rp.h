@@ -30,8 +30,12 @@
  *   Fill calls enqueue their kernels on it.  When they return depends on
  *   the fill and on *pos:
  *   - one-word fills (rp_fill_u64, rp_fill_uniform, rp_fill_uniform52,
- *     rp_engine_fold) consume exactly n words: *pos is set on the host and
- *     the call returns without waiting for the kernel;
+ *     rp_engine_fold, and rp_fill_uniformf with an even n) consume exactly
+ *     n words: *pos is set on the host and the call returns without waiting
+ *     for the kernel.  Their only stream operation is the kernel, so once a
+ *     call with the same engine and size has set up the jump tables they
+ *     can be captured into a CUDA graph (stream capture in relaxed mode)
+ *     and replayed;
  *   - the other fills of rp_fill_u64's family and rp_fill_state, when pos
  *     points to host-pinned memory (cudaMallocHost, cudaHostRegister, a
  *     pinned torch tensor), enqueue their kernels, a one-thread kernel that

@@ -4,15 +4,17 @@
 // bitmap kernel's second pass would only regenerate words to evaluate the
 // accepted ones: with half the words rejected that doubles the engine work,
 // which is what bounds this fill.  Here every word is generated once:
-//   pass 1 tests each word and compacts the accepted values of each lane
-//          through the warp's staging rows into the lane's run in the CTA's
-//          parking area (global memory that every tile of the CTA reuses, so
-//          the runs are written and read back within L2);
+//   pass 1 tests each word (the low half of its product with m) and
+//          compacts the accepted words of each lane through the warp's
+//          staging rows into the lane's run in the CTA's parking area
+//          (global memory that every tile of the CTA reuses);
 //   the block scan and the look-back over tile counts give each lane its
 //          first output;
-//   pass 2 copies each lane's run to its final place, the whole warp on one
-//          run at a time, so every store instruction writes consecutive
-//          outputs.
+//   pass 2 turns each lane's run into values (the high half of the
+//          product, taken on the parked words) at its final place, the
+//          whole warp on one run at a time, so every store instruction
+//          writes consecutive outputs; the next run's loads are issued
+//          before the current run's stores.
 //
 // Fragment of rp_fill_impl.cuh, included inside its namespace after the
 // scans and staging helpers.
@@ -44,7 +46,7 @@ __device__ bool rej_tile(const FillArgs& a, u64 k, const E& e, RejSmem<NT>& sm, 
   u64* const pw = park + (u64)wid * 32 * C;   // this warp's runs
   const u64 m = a.sp.m, thr = a.sp.thresh;
   const int half = lane >> 4, col = lane & 15;
-  // ---------------- pass 1: test, evaluate, compact, park
+  // ---------------- pass 1: test, compact, park
   E g = e;
   int cnt = 0;
   for (int hb = 0; hb < C / kStage; ++hb) {
@@ -53,11 +55,11 @@ __device__ bool rej_tile(const FillArgs& a, u64 k, const E& e, RejSmem<NT>& sm, 
     for (int j = 0; j < kStage; j += E::kStep) {
       u64 u[E::kStep];
       g.next_step(u);
-      // branch-free: every word's value lands in the next free slot (ns <= j
-      // < kRow), which advances only for accepted words
+      // branch-free: every word lands in the next free slot (ns <= j <
+      // kRow), which advances only for accepted words
 #pragma unroll
       for (int i = 0; i < E::kStep; ++i) {
-        stage[lane * kRow + ns] = __umul64hi(u[i], m);
+        stage[lane * kRow + ns] = u[i];
         ns += (int)(u[i] * m >= thr);
       }
     }
@@ -111,28 +113,43 @@ __device__ bool rej_tile(const FillArgs& a, u64 k, const E& e, RejSmem<NT>& sm, 
     a.ctrl->next_pos = chunk0 + (u64)(p + 1);
     atomicMin(&a.ctrl->done_tile, k);
   }
-  // ---------------- pass 2: parked runs -> output
+  // ---------------- pass 2: parked runs -> values at the output
   if (base < a.n) {
     u64* outb = (u64*)a.out + base;
     const u64 room = a.n - base;
     const int lim = room < (u64)0x7fffffff ? (int)room : 0x7fffffff;
+    constexpr int Q = C / 32;   // a whole run (at most C words) in one pass of the warp
+    static_assert(C % 32 == 0 && C <= 256, "a run and the next one fit the warp's registers");
+    u64 v[Q];
+    int o = __shfl_sync(0xffffffffu, off, 0);
+    int c = min(__shfl_sync(0xffffffffu, cnt, 0), lim - o);
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      const int i = q * 32 + lane;
+      v[q] = i < c ? __ldcg(pw + i) : 0ull;
+    }
     for (int r = 0; r < 32; ++r) {
-      const int o = __shfl_sync(0xffffffffu, off, r);
-      const int c = min(__shfl_sync(0xffffffffu, cnt, r), lim - o);
-      const u64* src = pw + r * C;
-      for (int i0 = 0; i0 < c; i0 += 128) {
-        u64 v[4];
+      u64 w[Q];
+      int o2 = 0, c2 = 0;
+      if (r + 1 < 32) {
+        o2 = __shfl_sync(0xffffffffu, off, r + 1);
+        c2 = min(__shfl_sync(0xffffffffu, cnt, r + 1), lim - o2);
+        const u64* src = pw + (r + 1) * C;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const int i = i0 + q * 32 + lane;
-          v[q] = i < c ? __ldcg(src + i) : 0ull;
-        }
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const int i = i0 + q * 32 + lane;
-          if (i < c) outb[o + i] = v[q];
+        for (int q = 0; q < Q; ++q) {
+          const int i = q * 32 + lane;
+          w[q] = i < c2 ? __ldcg(src + i) : 0ull;
         }
       }
+#pragma unroll
+      for (int q = 0; q < Q; ++q) {
+        const int i = q * 32 + lane;
+        if (i < c) outb[o + i] = __umul64hi(v[q], m);
+      }
+#pragma unroll
+      for (int q = 0; q < Q; ++q) v[q] = w[q];
+      o = o2;
+      c = c2;
     }
   }
   return true;

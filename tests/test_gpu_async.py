@@ -199,3 +199,37 @@ def test_fill_to_host(dist, params, pinned):
     assert p == pos
     for h, r in zip(outs, refs):
         assert np.array_equal(h.numpy(), _bits(r))
+
+
+@pytest.mark.parametrize("engine", ["xoshiro256pp", "pcg64dxsm", "philox4x32_10"])
+def test_one_word_fills_replay_from_a_cuda_graph(engine):
+    """One-word fills issue no host wait and no stream-ordered library call
+    besides their kernel, so once their tables are in place (one call with
+    the same engine and size) they can be captured into a CUDA graph: the
+    replay writes what the calls write."""
+    n = (1 << 18) + 77
+    w = torch.empty(n, dtype=torch.uint64, device="cuda")
+    u = torch.empty(n, dtype=torch.float64, device="cuda")
+    f = torch.empty(2 * n, dtype=torch.float32, device="cuda")
+
+    def fills(cs):
+        p = rp.rp_fill_u64(engine, 41, rp.NO_STREAM, 3, w, cs)
+        p = rp.rp_fill_uniform(engine, 41, rp.NO_STREAM, p, u, cs)
+        return rp.rp_fill_uniformf(engine, 41, rp.NO_STREAM, p, f, cs)
+
+    cap = torch.cuda.Stream()
+    cap.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(cap):
+        end = fills(cap)
+    torch.cuda.synchronize()
+    ref = (_bits(w).copy(), _bits(u).copy(), f.cpu().numpy().view(np.int32).copy())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=cap, capture_error_mode="relaxed"):
+        assert fills(cap) == end
+    for t in (w, u, f):
+        t.zero_()
+    g.replay()
+    g.replay()
+    torch.cuda.synchronize()
+    assert np.array_equal(_bits(w), ref[0]) and np.array_equal(_bits(u), ref[1])
+    assert np.array_equal(f.cpu().numpy().view(np.int32), ref[2])
