@@ -37,6 +37,8 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "rp_device.cuh"
 #include "rp_internal.h"
 
@@ -558,6 +560,53 @@ __global__ void __launch_bounds__(NT) k_onepw(FillArgs a) {
   E e;
   e.init_tile(a.eng, blockIdx.x, t, sh4);
   onepw_tile<NT, E, S>(a, blockIdx.x, e, stage[wid], (int)a.eng.chunk_words);
+}
+
+// One-word fill for Philox4x32-10, whose word p is half of the block at
+// counter + p / 2: no thread has to walk a range of its own, so consecutive
+// threads take consecutive blocks (grid-stride) and store their two outputs
+// straight to the output, 16 bytes per lane, with no staging.  Output i is
+// word w0 + i (w0 = the launch's first word), and every block's first output
+// index has the parity of w0, so whether the pairs are 16-byte aligned is
+// the same for the whole launch.
+template <int NT, class S>
+__global__ void __launch_bounds__(NT) k_onepw_ctr(FillArgs a) {
+  PhiloxDev e;
+  e.c_lo = a.eng.s[0];
+  e.c_hi = a.eng.s[1];
+  e.k0 = (unsigned)a.eng.s[2];
+  e.k1 = (unsigned)(a.eng.s[2] >> 32);
+  const u64 w0 = a.eng.word0, n = a.n;
+  if (n == 0) return;
+  u64* out = (u64*)a.out;
+  const u64 b_first = w0 >> 1;
+  const u64 nb = ((w0 + n - 1) >> 1) - b_first + 1;
+  const bool pairs = ((((unsigned long long)out >> 3) + w0) & 1) == 0;
+  const u64 G = (u64)gridDim.x * NT;
+  for (u64 j = (u64)blockIdx.x * NT + threadIdx.x; j < nb; j += G) {
+    u64 u[2];
+    e.block(b_first + j, u[0], u[1]);
+    const long long p0 = (long long)(2 * (b_first + j) - w0);   // -1 only for the first block of an odd w0
+    u64 v[2];
+    if constexpr (S::kCheckReject) {
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        u64 lo;
+        v[h] = S::value_lo(u[h], a.sp, lo);
+        const long long p = p0 + h;
+        if (lo < a.sp.thresh && p >= 0 && (u64)p < n) atomicMin(&a.ctrl->first_reject, (u64)p);
+      }
+    } else {
+      v[0] = as_bits(S::value1(u[0], a.sp));
+      v[1] = as_bits(S::value1(u[1], a.sp));
+    }
+    if (pairs && p0 >= 0 && (u64)p0 + 1 < n) {
+      *reinterpret_cast<ulonglong2*>(out + p0) = make_ulonglong2(v[0], v[1]);
+    } else {
+      if (p0 >= 0 && (u64)p0 < n) out[p0] = v[0];
+      if ((u64)(p0 + 1) < n) out[p0 + 1] = v[1];
+    }
+  }
 }
 
 // Engine alone: the xor of the launch's n words, one contiguous range per
@@ -1242,6 +1291,14 @@ int launch_merge(const FillArgs& a, int grid, cudaStream_t s, int* occ) {
 
 template <class E, class S>
 int launch_es(const FillArgs& a, int grid, cudaStream_t s, int* occ) {
+  if constexpr (std::is_same<E, PhiloxDev>::value) {
+    if (occ) {
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k_onepw_ctr<NT_, S>, NT_, 0);
+      return 0;
+    }
+    k_onepw_ctr<NT_, S><<<grid, NT_, 0, s>>>(a);
+    return (int)cudaGetLastError();
+  }
   if (occ) {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k_onepw<NT_, E, S>, NT_, 0);
     return 0;

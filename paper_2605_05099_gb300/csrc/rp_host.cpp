@@ -692,7 +692,8 @@ rp_status run_fill_state_locked(int engine, const u64 s_in[4], u64* pos, size_t 
     if (trivial) {
       // one tile per CTA: each thread streams one contiguous range of at
       // least 64 words (a multiple of 16; of 64 for xoshiro, whose per-thread
-      // jump tables are built per chunk length)
+      // jump tables are built per chunk length).  Philox4x32-10's kernel
+      // strides over blocks instead and uses only the grid.
       const u64 nt = (u64)tg.nt, q = xoshiro_engine(engine) ? 64 : 16;
       grid = std::max<u64>(1, std::min<u64>((u64)sm_count() * occ, (left + nt * 64 - 1) / (nt * 64)));
       C = ((left + grid * nt - 1) / (grid * nt) + q - 1) / q * q;
