@@ -113,8 +113,9 @@ rp_status rp_fill_u64(rp_engine engine, uint64_t seed, uint64_t stream, uint64_t
 
 /* The xor of words pos .. pos + n - 1 of the stream, written to d_fold (one
  * 64-bit device word, owned by the caller); *pos advances by n.  The words
- * are generated as a fill generates them (each thread one contiguous range
- * after one jump, Sec. 4.4 jump-ahead) and folded, and nothing else is
+ * are generated as the sequential-engine fills generate them (each thread
+ * one contiguous range after one jump, Sec. 4.4 jump-ahead; Philox4x32-10's
+ * one-word fills index its blocks directly instead) and folded, and nothing else is
  * computed or stored, so the call's words/s is the engine's throughput
  * ceiling for the fills (Table "engines" lists the paper's CPU rates of the
  * same engines).  Errors as for the fills; n = 0 leaves d_fold untouched. */
